@@ -1,0 +1,347 @@
+"""Pins of the oracle's multigrid pieces (Secs. 1, 3.1, 3.3-3.5, 4) against
+definitions and theorems: line-minimiser property of Kaczmarz, Thm. 3.1,
+exact recovery of a planted interpolation, dense Galerkin products, the
+two-grid error propagation formula, the GMRES minimal-residual property and
+dense solves."""
+import json
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+import scipy.sparse.linalg as spla
+
+from wl_inputs import metropolis_u1, cgauss, workload, rhs_batch
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def h32(O):
+    U = metropolis_u1(32, 6.0, 100, 21)
+    m = -0.05
+    p = O.setup_params([2], k_r=6, k_e=6, mu1=6, mu2=3, seed=5)
+    return O.Hierarchy.setup(32, U, m, p)
+
+
+@pytest.fixture(scope="module")
+def h64(O):
+    w = workload("T64")
+    p = O.setup_params(w["blocks"], k_r=w["k"], k_e=w["k"], seed=w["seed"])
+    return O.Hierarchy.setup(w["N"], w["U"], w["m"], p), w
+
+
+def _dense_kaczmarz(A, b, x, order):
+    x = x.copy()
+    r = b - A @ x
+    for i in order:
+        c = A[:, i]
+        s = np.vdot(c, r) / np.vdot(c, c).real
+        x[i] += s
+        r -= s * c
+    return x, r
+
+
+def test_kaczmarz_residual_and_line_minimiser(O, h32):
+    """Sec. 3.1: r is kept equal to f - A x, ||r|| does not grow, and after
+    the update of variable i the residual is orthogonal to A e_i (s_i is the
+    exact minimiser along e_i)."""
+    A = h32.dense(0)
+    n = A.shape[0]
+    f = cgauss(2, 3, n)
+    x0 = cgauss(2, 4, n) * 0.1
+    r0 = f - A @ x0
+    for order in (O.ORDER_LEX, O.ORDER_COLOUR):
+        x, r = h32.kaczmarz(0, x0, r0, order=order, sweeps=1)
+        assert np.abs(r - (f - A @ x)).max() <= 1e-12 * np.abs(f).max()
+        assert np.linalg.norm(r) < np.linalg.norm(r0)
+    x, r = h32.kaczmarz(0, x0, r0, order=O.ORDER_LEX, sweeps=1)
+    last = n - 1
+    assert abs(np.vdot(A[:, last], r)) <= 1e-12 * np.linalg.norm(A[:, last]) * np.linalg.norm(r0)
+
+
+def test_kaczmarz_colour_order_is_a_forward_sweep(O, h32):
+    """The multicolour sweep is the forward Kaczmarz sweep taken in colour
+    order (colour 0..15, sites ascending, spin 0 then 1); compared with a
+    dense textbook sweep in that order."""
+    A = h32.dense(0)
+    n = A.shape[0] // 2
+    f = cgauss(5, 1, 2 * n)
+    order = []
+    for k in range(16):
+        for h in range(n):
+            if O.colour(32, h) == k:
+                order += [2 * h, 2 * h + 1]
+    xr, rr = _dense_kaczmarz(A, f, np.zeros(2 * n, complex), order)
+    x, r = h32.kaczmarz(0, np.zeros(2 * n), f, order=O.ORDER_COLOUR)
+    assert np.abs(x - xr).max() <= 1e-13 * np.abs(xr).max()
+
+
+def test_kaczmarz_within_colour_permutation(O, h32):
+    """Updates inside one colour commute (disjoint supports): any site order
+    within the colours gives the same sweep up to rounding."""
+    n = 32 * 32 // 2
+    f = cgauss(6, 1, 2 * n)
+    x1, _ = h32.kaczmarz(0, np.zeros(2 * n), f, order=O.ORDER_COLOUR, sweeps=2)
+    perm = np.random.default_rng(3).permutation(n)
+    x2, _ = h32.kaczmarz(0, np.zeros(2 * n), f, order=O.ORDER_COLOUR, sweeps=2, perm=perm)
+    assert np.abs(x1 - x2).max() <= 1e-15 * np.abs(x1).max() * 10
+
+
+def test_theorem_kaczmarz_on_Z(O, h32):
+    """Thm. 3.1 (ii): Kaczmarz on D x = b and on Z x = Gamma5 b (Z = Gamma5 D)
+    produce the same iterates."""
+    A = h32.dense(0)
+    n = A.shape[0]
+    g5 = np.tile([1.0, -1.0], n // 2)
+    Z = g5[:, None] * A
+    f = cgauss(7, 1, n)
+    xz, _ = _dense_kaczmarz(Z, g5 * f, np.zeros(n, complex), range(n))
+    x, _ = h32.kaczmarz(0, np.zeros(n), f, order=O.ORDER_LEX)
+    assert np.abs(x - xz).max() <= 1e-12 * np.abs(x).max()
+
+
+def test_interpolation_structure(O, h32):
+    """Eqs. 3.13-3.15: P is block diagonal in spin (Gamma5 P = P Gamma5c), a
+    fine variable interpolates from <= 4 coarse variables and, for 2x2 cells,
+    exactly from the same-spin coarse neighbours in the graph of Dhat; C rows
+    are the identity."""
+    gold = json.load(open(os.path.join(GOLDEN, "paper_structure.json")))
+    P = h32.dense(0, which=1)
+    A = h32.dense(0)
+    nf, nc = P.shape
+    g5f, g5c = np.tile([1.0, -1.0], nf // 2), np.tile([1.0, -1.0], nc // 2)
+    assert np.abs(g5f[:, None] * P - P * g5c[None, :]).max() == 0.0
+    nnz = (np.abs(P) > 0).sum(axis=1)
+    assert nnz.max() <= gold["max_interpolation_points"]
+    # coarse points: fine unknowns that are identity rows
+    crow = {}
+    for i in range(nf):
+        js = np.nonzero(np.abs(P[i]) > 0)[0]
+        if len(js) == 1 and abs(P[i, js[0]] - 1) < 1e-14:
+            crow[js[0]] = i
+    assert len(crow) == nc
+    for i in range(nf):
+        if i in crow.values():
+            continue
+        graph = {j for j in range(nc) if j % 2 == i % 2 and abs(A[i, crow[j]]) > 0}
+        assert set(np.nonzero(np.abs(P[i]) > 0)[0]) == graph
+
+
+def test_galerkin_dense(O, h64):
+    """Sec. 3.5: D_{l+1} = P^H D_l P; the coarse operator is gamma5-Hermitian
+    and keeps the 9-point pattern with at most 18 non-zeros per row."""
+    h, _ = h64
+    gold = json.load(open(os.path.join(GOLDEN, "paper_structure.json")))
+    for l in range(h.L - 1):
+        A, P, Ac = h.dense(l), h.dense(l, 1), h.dense(l + 1)
+        ref = P.conj().T @ A @ P
+        assert np.abs(Ac - ref).max() <= 1e-13 * np.abs(ref).max()
+        g5 = np.tile([1.0, -1.0], Ac.shape[0] // 2)
+        assert np.abs(g5[:, None] * Ac - (g5[:, None] * Ac).conj().T).max() == 0.0
+        assert (np.abs(Ac) > 0).sum(axis=1).max() <= gold["max_coarse_nnz_per_row"]
+
+
+def test_petrov_galerkin_equals_galerkin(O, h32):
+    """Sec. 3.5: with R = (Gamma5 P)^H, P (R D P)^-1 R = P (P^H D P)^-1 P^H."""
+    A, P = h32.dense(0), h32.dense(0, 1)
+    g5 = np.tile([1.0, -1.0], A.shape[0] // 2)
+    R = (g5[:, None] * P).conj().T
+    lhs = P @ np.linalg.solve(R @ A @ P, R)
+    rhs = P @ np.linalg.solve(P.conj().T @ A @ P, P.conj().T)
+    assert np.abs(lhs - rhs).max() <= 1e-10 * np.abs(rhs).max()
+
+
+def test_ls_fit_exact_recovery_and_optimality(O, h32):
+    """Eq. 3.4: test vectors that lie in range(P_true) are fitted exactly
+    (P_true is recovered); perturbing a fitted row increases the functional."""
+    N, B = 32, 2
+    nf = N * N // 2
+    rng = np.random.default_rng(11)
+    Pw_true = h32.export()[0][0].copy()
+    mask = np.abs(Pw_true) > 0
+    Pw_true[mask] = rng.standard_normal(mask.sum()) + 1j * rng.standard_normal(mask.sum())
+    # C rows stay the identity
+    for hf in range(nf):
+        for s in range(2):
+            if mask[hf, s].sum() == 1:
+                Pw_true[hf, s] = 0
+                Pw_true[hf, s, 0] = 1.0
+    _, As = h32.export()
+    hp = O.Hierarchy.from_arrays(N, h32.U, h32.m, h32.Nl, h32.Bl, [Pw_true], As)
+    P = hp.dense(0, 1)
+    k = 7
+    Vc = rng.standard_normal((k, P.shape[1])) + 1j * rng.standard_normal((k, P.shape[1]))
+    V = Vc @ P.T
+    w = rng.random(k) + 0.5
+    Pw = O.ls_fit(N, B, V, w)
+    assert np.abs(Pw - Pw_true).max() <= 1e-10
+    # optimality of a fit of noisy vectors
+    Vn = V + 0.3 * (rng.standard_normal(V.shape) + 1j * rng.standard_normal(V.shape))
+    Pn = O.ls_fit(N, B, Vn, w)
+    hn = O.Hierarchy.from_arrays(N, h32.U, h32.m, h32.Nl, h32.Bl, [Pn], As)
+    Pd = hn.dense(0, 1)
+    cidx = [np.nonzero(np.abs(Pd[:, j]) == 1)[0] for j in range(Pd.shape[1])]
+    cpos = np.array([c[0] for c in cidx])
+    for i in rng.choice(Pd.shape[0], 20, replace=False):
+        js = np.nonzero(np.abs(Pd[i]) > 0)[0]
+        if len(js) < 2:
+            continue
+        def L(p):
+            resid = Vn[:, i] - Vn[:, cpos[js]] @ p
+            return float(np.sum(w * np.abs(resid) ** 2))
+        p0 = Pd[i, js]
+        for _ in range(5):
+            dp = 1e-3 * (rng.standard_normal(len(js)) + 1j * rng.standard_normal(len(js)))
+            assert L(p0 + dp) >= L(p0)
+
+
+def test_generalised_eigensolver(O):
+    """Thm. 3.1 (i): Z V = T V Lambda against LAPACK's generalised Hermitian
+    solver (scipy.linalg.eigh)."""
+    rng = np.random.default_rng(2)
+    n = 40
+    Zr = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    Z = Zr + Zr.conj().T
+    Tr = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    T = Tr @ Tr.conj().T + n * np.eye(n)
+    lam, V = O.gen_eig(Z, T)
+    ref = sla.eigh(Z, T, eigvals_only=True)
+    assert np.abs(lam - ref).max() <= 1e-12 * np.abs(ref).max()
+    for k in range(n):
+        v = V[k]
+        assert np.linalg.norm(Z @ v - lam[k] * (T @ v)) <= 1e-11 * np.linalg.norm(Z)
+        assert abs(np.vdot(v, T @ v) - 1) <= 1e-12
+
+
+def test_theorem_singular_triplets(O, h64):
+    """Thm. 3.1 (i), (iii): an eigenpair Z_L v = lambda T_L v gives the
+    generalised singular triplet D_L v = |lambda| T_L u, D_L^H u = |lambda|
+    T_L v with u = sign(lambda) Gamma5 v (Q_L = T_L)."""
+    h, w = h64
+    O_ = O
+    p = O_.setup_params(w["blocks"], k_r=4, k_e=4, mu1=3, mu2=2, seed=3)
+    hh = O_.Hierarchy.setup(w["N"], w["U"], w["m"], p)
+    L = hh.L - 1
+    A = hh.dense(L)
+    T = hh.dense(L, which=2)
+    g5 = np.tile([1.0, -1.0], A.shape[0] // 2)
+    lam, V = O_.gen_eig(g5[:, None] * A, T)
+    for k in range(0, A.shape[0], 17):
+        v = V[k]
+        u = np.sign(lam[k]) * g5 * v
+        sig = abs(lam[k])
+        assert np.linalg.norm(A @ v - sig * (T @ u)) <= 1e-10 * np.linalg.norm(A)
+        assert np.linalg.norm(A.conj().T @ u - sig * (T @ v)) <= 1e-10 * np.linalg.norm(A)
+
+
+def test_two_grid_error_propagation(O, h32):
+    """Sec. 1: one pre-smoothing step and the Galerkin correction give
+    x = x_s + P A_c^-1 P^H (f - A x_s), x_s the smoothed iterate from 0."""
+    A, P = h32.dense(0), h32.dense(0, 1)
+    n = A.shape[0]
+    f = cgauss(9, 2, n)
+    xs, _ = h32.kaczmarz(0, np.zeros(n), f, order=O.ORDER_COLOUR, sweeps=1)
+    Ac = P.conj().T @ A @ P
+    ref = xs + P @ np.linalg.solve(Ac, P.conj().T @ (f - A @ xs))
+    x = h32.cycle(f, nu1=1, nu2=0)
+    assert np.abs(x - ref).max() <= 1e-11 * np.abs(ref).max()
+
+
+def test_cycle_linear(O, h64):
+    """The V- and W-cycles are linear maps of f."""
+    h, _ = h64
+    n = h.n(0)
+    f, g = cgauss(1, 5, n), cgauss(1, 6, n)
+    a = 0.7 - 0.3j
+    for gamma in (1, 2):
+        lhs = h.cycle(a * f + g, gamma=gamma)
+        rhs = a * h.cycle(f, gamma=gamma) + h.cycle(g, gamma=gamma)
+        assert np.abs(lhs - rhs).max() <= 1e-12 * np.abs(lhs).max()
+
+
+def test_gmres_minimal_residual(O, h32):
+    """Unpreconditioned GMRES after k steps minimises ||b - A x|| over the
+    Krylov space span{b, Ab, ..., A^{k-1} b} (dense least squares)."""
+    A = h32.dense(0)
+    n = A.shape[0]
+    b = cgauss(4, 4, n)
+    k = 6
+    x, info = h32.fgmres(b, tol=0.0, m=k, max_restarts=1, precond=0)
+    K = np.empty((n, k), complex)
+    v = b.copy()
+    for j in range(k):
+        K[:, j] = v
+        v = A @ v
+    Q, _ = np.linalg.qr(K)
+    y = np.linalg.lstsq(A @ Q, b, rcond=None)[0]
+    ref = Q @ y
+    assert info["iters"] == k
+    assert np.abs(x - ref).max() <= 1e-9 * np.abs(ref).max()
+
+
+def test_solve_dense_8x8(O):
+    """Whole solve (reduce, FGMRES + V-cycle, reconstruct) against the dense
+    solution of D psi = b on an 8x8 lattice."""
+    N, m = 8, 0.05
+    U = metropolis_u1(N, 3.0, 30, 77)
+    p = O.setup_params([2], k_r=4, k_e=4, mu1=4, mu2=2, seed=1)
+    h = O.Hierarchy.setup(N, U, m, p)
+    b = cgauss(8, 8, 2 * N * N).reshape(N, N, 2)
+    psi, info = h.solve(b, tol=1e-13)
+    D = O.wilson_csr(N, U, m).toarray()
+    ref = np.linalg.solve(D, b.reshape(-1)).reshape(N, N, 2)
+    assert info["status"] == 0
+    assert np.linalg.norm(psi - ref) <= 1e-11 * np.linalg.norm(ref)
+
+
+def test_solve_sparse_direct_64(O, h64):
+    """Whole solve on the 64x64 workload against SciPy's sparse LU of D."""
+    h, w = h64
+    N = w["N"]
+    b = rhs_batch(N, 1, 5)[0]
+    psi, info = h.solve(b, tol=1e-13)
+    D = O.wilson_csr(N, w["U"], w["m"]).tocsc()
+    ref = spla.spsolve(D, b.reshape(-1)).reshape(N, N, 2)
+    assert info["status"] == 0
+    assert np.linalg.norm(psi - ref) <= 1e-10 * np.linalg.norm(ref)
+
+
+def test_setup_quality_band(O, h64):
+    """Sec. 4.1 (quality, not parity): the preconditioned Krylov solve needs
+    far fewer iterations than plain GMRES and the stand-alone W(4,4) cycle
+    converges with rate rho well below 1."""
+    h, w = h64
+    bh = O.eo_reduce(w["N"], w["U"], w["m"], rhs_batch(w["N"], 1, 6)[0])
+    _, info = h.fgmres(bh, tol=1e-10, m=20, max_restarts=20)
+    assert info["status"] == 0 and info["iters"] <= 40
+    A = h.dense(0)
+    x = cgauss(3, 9, h.n(0))
+    e_prev = np.linalg.norm(x)
+    for _ in range(12):
+        x = x - h.cycle(A @ x, nu1=4, nu2=4, gamma=2)  # error iteration on A x = 0
+        e = np.linalg.norm(x)
+        rho, e_prev = e / e_prev, e
+    assert rho <= 0.8
+
+
+def test_hierarchy_roundtrip(O, h64):
+    """Export to (P weights, coarse stencils) and import gives the same
+    operators and the same cycle."""
+    h, w = h64
+    Pw, As = h.export()
+    h2 = O.Hierarchy.from_arrays(w["N"], w["U"], w["m"], h.Nl, h.Bl[:-1], Pw, As)
+    f = cgauss(12, 1, h.n(0))
+    assert np.abs(h.cycle(f) - h2.cycle(f)).max() == 0.0
+    for l in range(h.L):
+        assert np.abs(h.dense(l) - h2.dense(l)).max() == 0.0
+
+
+def test_rng_reference_values(O):
+    """SplitMix64 published test vector: state 0 -> 0xE220A8397B1DCDAF,
+    0x6E789E6AA1B965F4 (first two outputs); u64(seed,stream,i) composes it."""
+    from wl_inputs import rng as R
+    assert R._sm_scalar(0) == 0xE220A8397B1DCDAF
+    assert R._sm_scalar(0x9E3779B97F4A7C15) == 0x6E789E6AA1B965F4
+    for s, st, i in [(0, 0, 0), (123, 7, 99), (2**63 + 5, 3, 2**40)]:
+        assert int(R.rng_u64(s, st, [i])[0]) == O.rng_u64(s, st, i)

@@ -1,0 +1,87 @@
+"""Seeded synthetic workloads.
+
+Each workload names a lattice, a gauge ensemble recipe (beta, Metropolis
+sweeps, seed), the target smallest |eigenvalue| of D and the hierarchy shape.
+The shift m that realises the target for the seeded gauge field is stored in
+shifts.json, which oracle/make_shifts.py writes from the oracle's operator.
+
+C1..C4 follow the four single-configuration workloads; SERVE lists the 16
+resident configurations of the serving mix (sizes cycled over 64..1024,
+beta alternating 6 / 10, target 1e-2 / 1e-3).
+"""
+import json
+import os
+
+import numpy as np
+
+from .gauge import metropolis_u1
+from .rng import cgauss
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def _levels(N: int):
+    """cells of 4x4 while the next level keeps >= 16 sites per side, then 2x2,
+    down to the N = 16 coarsest grid."""
+    blocks, n = [], N
+    while n > 16:
+        b = 4 if n // 4 >= 16 else 2
+        blocks.append(b)
+        n //= b
+    return blocks
+
+
+WORKLOADS = {
+    "C1": dict(N=32, beta=6.0, sweeps=200, target=1e-2, seed=1001, blocks=[2], k=8,
+               precision="fp64", nrhs=1),
+    "C2": dict(N=128, beta=6.0, sweeps=500, target=1e-3, seed=2001, blocks=[4, 2], k=8,
+               precision="fp64", nrhs=1),
+    "C3": dict(N=512, beta=10.0, sweeps=500, target=1e-3, seed=3001, blocks=[4, 4, 2], k=12,
+               precision="fp32", nrhs=1),
+    "C4": dict(N=512, beta=10.0, sweeps=500, target=1e-3, seed=3001, blocks=[4, 4, 2], k=12,
+               precision="fp32", nrhs=64),
+}
+
+_SERVE_SIZES = [64, 128, 256, 512, 1024]
+for _i in range(16):
+    _N = _SERVE_SIZES[_i % 5]
+    WORKLOADS["S%02d" % _i] = dict(
+        N=_N, beta=6.0 if _i % 2 == 0 else 10.0, sweeps=200, target=1e-2 if (_i // 2) % 2 == 0 else 1e-3,
+        seed=5000 + _i, blocks=_levels(_N), k=8, precision="fp32", nrhs=0)
+
+# tiny cases for parity tests (targets are loose; shifts computed the same way)
+WORKLOADS["T16"] = dict(N=16, beta=6.0, sweeps=50, target=5e-2, seed=11, blocks=[], k=4,
+                        precision="fp64", nrhs=1)
+WORKLOADS["T32"] = dict(N=32, beta=3.0, sweeps=50, target=2e-2, seed=12, blocks=[2], k=6,
+                        precision="fp64", nrhs=1)
+WORKLOADS["T64"] = dict(N=64, beta=6.0, sweeps=100, target=1e-2, seed=13, blocks=[2, 2], k=8,
+                        precision="fp64", nrhs=1)
+
+
+def _shifts():
+    path = os.path.join(_HERE, "shifts.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f)
+    return {}
+
+
+def workload(name: str, with_gauge: bool = True):
+    """Return a dict with the workload parameters, its shift m (if computed)
+    and, optionally, the gauge field U[2][N][N]."""
+    w = dict(WORKLOADS[name])
+    w["name"] = name
+    w["levels"] = len(w["blocks"]) + 1
+    sh = _shifts().get(name)
+    w["m"] = None if sh is None else float(sh["m"])
+    if with_gauge:
+        w["U"] = metropolis_u1(w["N"], w["beta"], w["sweeps"], w["seed"])
+    return w
+
+
+def rhs_batch(N: int, nrhs: int, seed: int, first: int = 0) -> np.ndarray:
+    """Complex Gaussian right-hand sides, [nrhs][N][N][2] (y, x, spin)."""
+    out = np.empty((nrhs, N, N, 2), dtype=np.complex128)
+    for r in range(nrhs):
+        out[r] = cgauss(seed, 2000 + first + r, 2 * N * N).reshape(N, N, 2)
+    return out
