@@ -1,0 +1,170 @@
+/*
+ * wilson_amg.h -- C ABI of the GB300 (sm_103a) bootstrap-AMG solver for the
+ * odd-even reduced 2D Wilson-Dirac system.
+ *
+ * Method: J. Brannick and K. Kahl, "Bootstrap Algebraic Multigrid for the 2D
+ * Wilson Dirac system".  The problem is D psi = b (Sec. 1, Eq. 1.1) with the
+ * 2D Wilson matrix D = D_0 + m I (Sec. 2, Eq. 2.1; N_s = 2 spins, U(1)
+ * links).  The library reduces it to the even-site Schur complement
+ * Dhat = I - D_eo D_oe (Sec. 3.2, Eq. 3.2), solves Dhat psi_e = bhat with
+ * FGMRES preconditioned by an AMG cycle (Kaczmarz smoothing, Sec. 3.1;
+ * least-squares interpolation P and Galerkin restriction P^H, Secs. 3.3 and
+ * 3.5; a direct coarsest solve, Sec. 4), and reconstructs psi_o.
+ *
+ * Conventions (every pointer is a DEVICE pointer unless it says "host"):
+ *   complex numbers are complex128 (two doubles, re then im) at this ABI;
+ *   lattice side L (= N): L >= 16, L a power of two (so L/16 is one);
+ *   gauge  U[2][L][L]  (mu, y, x): U_mu(x, y) on the edge (x,y) -> (x,y)+e_mu,
+ *          mu = 0 is x, mu = 1 is y; gauge links are periodic;
+ *   D acts as (D psi)(z) = (m+2) psi(z) - 1/2 sum_mu [(1 - s_mu) U_mu(z)
+ *          psi(z+mu) + (1 + s_mu) conj(U_mu(z-mu)) psi(z-mu)], s_mu the
+ *          Pauli matrices, with an extra factor -1 on hops across the y
+ *          boundary (antiperiodic fermions in y);
+ *   full fields  [nrhs][L][L][2]  (rhs, y, x, spin);
+ *   level vectors [nrhs][n_l][2] with n_l = N_l^2/2 sites of the even
+ *          sublattice of an N_l x N_l torus, site h <-> y = h / (N_l/2),
+ *          x = 2 (h mod N_l/2) + (y mod 2);  level 0 is the fine even grid.
+ *   Interpolation weights [n_l][2][4] (site, spin, cell corner k = ka+2kb)
+ *   and coarse stencils [n_l][9][2][2] (site, offset d = 3(da+1)+(db+1) in
+ *   rotated coordinates a = (x+y)/2, b = (x-y)/2, row spin, column spin)
+ *   are the layouts of the hierarchy file (see amg_export).
+ *
+ * Ownership: the caller owns every array it passes; the library copies the
+ * gauge in wilson_create and owns its hierarchy and workspace.  All work is
+ * enqueued on the stream given to wilson_create; calls that return results
+ * to the host (amg_solve's info, amg_fgmres) synchronise that stream.
+ *
+ * Errors: 0 = OK, 1 = WL_NOT_CONVERGED (x holds the best iterate), negative
+ * values are errors; wl_last_error() returns a message for the calling
+ * thread.  No call faults the device on bad arguments: sizes, levels and
+ * pointers are checked on the host first (WL_EINVAL).
+ */
+#ifndef WILSON_AMG_H
+#define WILSON_AMG_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct wl_op wl_op;   /* Wilson operator for one gauge field          */
+typedef struct wl_amg wl_amg; /* AMG hierarchy (cached setup) for one wl_op   */
+
+enum {
+  WL_OK = 0,
+  WL_NOT_CONVERGED = 1,
+  WL_EINVAL = -1,
+  WL_OOM = -2,
+  WL_ECUDA = -3,
+  WL_TIMEOUT = -4,
+  WL_NAN = -5,
+  WL_BAD_HIERARCHY = -6
+};
+
+enum { WL_FP64 = 0, WL_FP32 = 1, WL_FP32_BF16 = 2 }; /* cycle precision */
+enum { WL_OP_D = 0, WL_OP_DHAT = 1 };                 /* wl_apply        */
+enum { WL_CYCLE_V = 0, WL_CYCLE_W = 1 };
+
+typedef struct {
+  int levels;             /* number of grids, >= 2; the coarsest is solved directly */
+  int block[8];           /* cell size (2 or 4) of coarsening step l -> l+1          */
+  int k_r, k_e;           /* relaxation / eigenvector test vectors (Sec. 3.4)        */
+  int setup_mu[2];        /* Kaczmarz sweeps per visit, setup cycles 1 and 2 (Sec. 4.1) */
+  int nu_pre, nu_post;    /* solve-cycle smoothing sweeps                           */
+  double omega;           /* Kaczmarz relaxation weight (1 = the paper's)           */
+  int cycle;              /* WL_CYCLE_V or WL_CYCLE_W                                */
+  int fgmres_m;           /* FGMRES restart length (<= 32)                          */
+  int max_restarts;
+  int precision;          /* WL_FP64, WL_FP32 or WL_FP32_BF16 (cycle arithmetic)    */
+  unsigned long long seed;/* seed of the setup's random test vectors                */
+  int gs_passes;          /* Gram-Schmidt passes (1 = CGS, 2 = CGS with one reorth.) */
+  int zero_guess;         /* 1: amg_solve ignores the contents of x                 */
+} amg_params;
+
+typedef struct {
+  int status;             /* WL_OK or WL_NOT_CONVERGED for this right-hand side     */
+  int restarts;           /* FGMRES cycles run                                       */
+  int iters;              /* FGMRES iterations (preconditioner applications)         */
+  double true_relres;     /* ||bhat - Dhat x|| / ||bhat|| recomputed in FP64         */
+} wl_info;
+
+/* Fill *p with the defaults: V(2,2) cycle, FGMRES(20), k_r = k_e = 8, setup
+ * relaxation 10 then 5 (Sec. 4.1), FP64, CGS with one reorthogonalisation. */
+void amg_params_default(amg_params *p);
+
+/* Create the Wilson operator D = D_0 + m I of Eq. 2.1 for the gauge field
+ * `gauge` (device, complex128 [2][L][L], copied).  cuda_stream is a
+ * cudaStream_t (NULL = default stream).  m must satisfy m + 2 != 0.
+ * Errors: WL_EINVAL (L not a power of two >= 16, NULL pointers), WL_OOM,
+ * WL_ECUDA. */
+int wilson_create(const void *gauge, int L, double m, void *cuda_stream, wl_op **out);
+void wl_destroy(wl_op *op);
+
+/* y = D x (which = WL_OP_D; x, y full fields [nrhs][L][L][2]) or
+ * y = Dhat x (which = WL_OP_DHAT, Eq. 3.2 with the 1/c scaling of Sec. 3.2;
+ * x, y level-0 vectors [nrhs][L^2/2][2]), computed matrix-free from the
+ * links in precision prec (WL_FP64 or WL_FP32; FP32 rounds x and the links
+ * to float and accumulates in float).  Errors: WL_EINVAL. */
+int wl_apply(wl_op *op, int which, const void *x, void *y, int nrhs, int prec);
+
+/* Sec. 3.2, two-step solve: bhat = b_e/c - (D_eo/c)(b_o/c) with c = m + 2
+ * (b full fields, bhat level-0 vectors), and psi_e = x_e,
+ * psi_o = b_o/c - (D_oe/c) x_e.  Errors: WL_EINVAL. */
+int wl_eo_reduce(wl_op *op, const void *b, void *bhat, int nrhs);
+int wl_eo_reconstruct(wl_op *op, const void *b, const void *xe, void *psi, int nrhs);
+
+/* Bootstrap setup (Secs. 3.4-3.5, 4.1) on the GPU: W-cycle setup with
+ * setup_mu[0] sweeps, an adaptive step, a second W-cycle with setup_mu[1]
+ * sweeps; least-squares interpolation (Eq. 3.4) and Galerkin coarse
+ * operators P^H D P on every level; coarsest operator inverted in FP64.
+ * Errors: WL_EINVAL (levels / blocks incompatible with L), WL_OOM, WL_ECUDA. */
+int amg_setup(wl_op *op, const amg_params *params, wl_amg **out);
+
+/* Solve D psi = b for nrhs right-hand sides (b, x full fields
+ * [nrhs][L][L][2], device).  x is the initial guess unless
+ * params.zero_guess.  Stops each right-hand side when its FP64 relative
+ * residual of the reduced system is <= tol.  info: host array [nrhs].
+ * Returns WL_OK if every right-hand side converged, WL_NOT_CONVERGED
+ * otherwise, or an error (WL_NAN if a residual became non-finite). */
+int amg_solve(wl_amg *amg, const void *b, void *x, int nrhs, double tol, wl_info *info);
+
+/* Hierarchy file: header "WLAMGH01", version, levels, N_l, B_l, m, gauge
+ * checksum, interpolation weights of every non-coarsest level and coarse
+ * stencils of levels >= 1 (complex128, layouts above), FNV-1a 64 checksum.
+ * amg_import rebuilds a hierarchy for `op` from such a file (its solve
+ * parameters from *params, NULL = defaults); WL_BAD_HIERARCHY if the file
+ * is corrupt or belongs to another gauge field / mass. */
+int amg_export(wl_amg *amg, const char *path);
+int amg_import(wl_op *op, const char *path, const amg_params *params, wl_amg **out);
+void amg_destroy(wl_amg *amg);
+
+/* Number of levels and the lattice side of level l (host outputs). */
+int amg_levels(wl_amg *amg, int *N_out /* host [levels] */);
+
+/* ---- per-step entry points of the solve phase (used by the parity tests) ----
+ * Vectors are level-l vectors [nrhs][n_l][2] in FP64 at this ABI; prec
+ * selects the arithmetic of the step (WL_FP64, WL_FP32, WL_FP32_BF16).     */
+
+/* y = A_l x, A_0 = Dhat (explicit 9-point stencil), A_l = P^H A_{l-1} P. */
+int amg_level_apply(wl_amg *amg, int level, const void *x, void *y, int nrhs, int prec);
+/* `sweeps` multicolour Kaczmarz sweeps (Sec. 3.1) on A_l x = f with the
+ * residual r = f - A_l x carried along; x, r updated in place. */
+int amg_kaczmarz(wl_amg *amg, int level, void *x, void *r, int nrhs, int sweeps, int prec);
+/* fc = P_l^H r (level l -> l+1) and x += P_l e (level l+1 -> l). */
+int amg_restrict(wl_amg *amg, int level, const void *r, void *fc, int nrhs, int prec);
+int amg_prolong(wl_amg *amg, int level, const void *e, void *x, int nrhs, int prec);
+/* x = A_L^{-1} f on the coarsest level (FP64 inverse). */
+int amg_coarsest(wl_amg *amg, const void *f, void *x, int nrhs);
+/* One preconditioning cycle x = M(f) on level 0 from x = 0 (the
+ * configured V or W cycle, nu_pre / nu_post sweeps). */
+int amg_cycle(wl_amg *amg, const void *f, void *x, int nrhs, int prec);
+/* FGMRES on Dhat x = bhat (level-0 vectors, x = initial guess); info host
+ * array [nrhs]. */
+int amg_fgmres(wl_amg *amg, const void *bhat, void *x, int nrhs, double tol, wl_info *info);
+
+/* Last error message of the calling thread ("" if none). */
+const char *wl_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,50 @@
+"""Writer of the hierarchy file format for hierarchies built by the oracle
+(TEST INFRASTRUCTURE).  Format, little endian:
+
+  "WLAMGH01" | int32 version = 1 | int32 L | int32 N[L] | int32 B[L] |
+  float64 m | uint64 FNV-1a-64 of the gauge bytes (complex128 [2][N][N]) |
+  complex128 P weights [n_l][2][4] for l = 0 .. L-2 |
+  complex128 coarse stencils [n_l][9][2][2] for l = 1 .. L-1 |
+  uint64 FNV-1a-64 of all preceding bytes
+"""
+import struct
+
+import numpy as np
+
+_FNV_OFF = 1469598103934665603
+_FNV_PRIME = 1099511628211
+
+
+def fnv1a64(data: bytes, h: int = _FNV_OFF) -> int:
+    # vectorised in blocks: h = (h ^ byte) * prime mod 2^64 is sequential, so
+    # process bytes in a plain loop over a memoryview (fast enough for MBs)
+    mask = (1 << 64) - 1
+    for b in memoryview(data):
+        h = ((h ^ b) * _FNV_PRIME) & mask
+    return h
+
+
+def gauge_hash(U) -> int:
+    return fnv1a64(np.ascontiguousarray(U, dtype=np.complex128).tobytes())
+
+
+def write(path, U, m, Nl, Bl, Pw, As):
+    L = len(Nl)
+    Bfull = list(Bl[: L - 1]) + [0]
+    parts = [b"WLAMGH01", struct.pack("<ii", 1, L), struct.pack("<%di" % L, *Nl),
+             struct.pack("<%di" % L, *Bfull), struct.pack("<d", float(m)),
+             struct.pack("<Q", gauge_hash(U))]
+    for l in range(L - 1):
+        parts.append(np.ascontiguousarray(Pw[l], dtype=np.complex128).tobytes())
+    for l in range(1, L):
+        parts.append(np.ascontiguousarray(As[l - 1], dtype=np.complex128).tobytes())
+    body = b"".join(parts)
+    with open(path, "wb") as f:
+        f.write(body)
+        f.write(struct.pack("<Q", fnv1a64(body)))
+
+
+def write_hierarchy(path, h):
+    """h: oracle.Hierarchy"""
+    Pw, As = h.export()
+    write(path, h.U, h.m, h.Nl, h.Bl, Pw, As)

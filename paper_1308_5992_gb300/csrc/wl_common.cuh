@@ -1,0 +1,228 @@
+// wl_common.cuh -- internal types, complex helpers, lattice geometry and the
+// host-side objects of the sm_103a solver.  Included by every .cu file.
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+#include <string>
+#include <vector>
+
+#include "../../include/wilson_amg.h"
+
+// ------------------------------------------------------------------ complex
+template <typename T>
+struct alignas(2 * sizeof(T)) cx {
+  T re, im;
+};
+typedef cx<double> zd;
+typedef cx<float> zf;
+
+template <typename T>
+__host__ __device__ __forceinline__ cx<T> mk(T r, T i) {
+  cx<T> z;
+  z.re = r;
+  z.im = i;
+  return z;
+}
+template <typename T>
+__host__ __device__ __forceinline__ cx<T> operator+(cx<T> a, cx<T> b) { return mk(a.re + b.re, a.im + b.im); }
+template <typename T>
+__host__ __device__ __forceinline__ cx<T> operator-(cx<T> a, cx<T> b) { return mk(a.re - b.re, a.im - b.im); }
+template <typename T>
+__host__ __device__ __forceinline__ cx<T> operator*(cx<T> a, cx<T> b) {
+  return mk(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re);
+}
+template <typename T>
+__host__ __device__ __forceinline__ cx<T> operator*(T s, cx<T> a) { return mk(s * a.re, s * a.im); }
+template <typename T>
+__host__ __device__ __forceinline__ cx<T> cconj(cx<T> a) { return mk(a.re, -a.im); }
+// conj(a) * b
+template <typename T>
+__host__ __device__ __forceinline__ cx<T> cmulc(cx<T> a, cx<T> b) {
+  return mk(a.re * b.re + a.im * b.im, a.re * b.im - a.im * b.re);
+}
+// i * a
+template <typename T>
+__host__ __device__ __forceinline__ cx<T> ci(cx<T> a) { return mk(-a.im, a.re); }
+template <typename T>
+__host__ __device__ __forceinline__ T cnorm2(cx<T> a) { return a.re * a.re + a.im * a.im; }
+// accumulate a * b into acc
+template <typename T>
+__host__ __device__ __forceinline__ void cfma(cx<T> &acc, cx<T> a, cx<T> b) {
+  acc.re = fma(a.re, b.re, acc.re);
+  acc.re = fma(-a.im, b.im, acc.re);
+  acc.im = fma(a.re, b.im, acc.im);
+  acc.im = fma(a.im, b.re, acc.im);
+}
+// accumulate conj(a) * b into acc
+template <typename T>
+__host__ __device__ __forceinline__ void cfmac(cx<T> &acc, cx<T> a, cx<T> b) {
+  acc.re = fma(a.re, b.re, acc.re);
+  acc.re = fma(a.im, b.im, acc.re);
+  acc.im = fma(a.re, b.im, acc.im);
+  acc.im = fma(-a.im, b.re, acc.im);
+}
+
+template <typename To, typename From>
+__host__ __device__ __forceinline__ cx<To> ccast(cx<From> a) {
+  return mk((To)a.re, (To)a.im);
+}
+
+// storage of operator coefficients: complex double, complex float or bf16 pair
+struct zb {
+  __nv_bfloat162 v;
+};
+template <typename T>
+__device__ __forceinline__ cx<T> ld(const zd *p) { return ccast<T>(*p); }
+template <typename T>
+__device__ __forceinline__ cx<T> ld(const zf *p) { return ccast<T>(*p); }
+template <typename T>
+__device__ __forceinline__ cx<T> ld(const zb *p) {
+  float2 f = __bfloat1622float2(p->v);
+  return mk((T)f.x, (T)f.y);
+}
+
+// ----------------------------------------------------------------- geometry
+// Level l is the even sublattice of an N x N torus (N a power of two).
+// site h <-> (x, y): y = h / (N/2), x = 2 (h mod N/2) + (y mod 2).
+// Rotated coordinates a = (x+y)/2, b = (x-y)/2; stencil offset
+// d = 3 (da+1) + (db+1), (dx, dy) = (da+db, da-db).
+struct Geo {
+  int N, lg;  // N = 1 << lg
+  __host__ __device__ __forceinline__ int half() const { return N >> 1; }
+  __host__ __device__ __forceinline__ int nsites() const { return (N * N) >> 1; }
+  __host__ __device__ __forceinline__ void xy(int h, int &x, int &y) const {
+    y = h >> (lg - 1);
+    x = ((h & (half() - 1)) << 1) | (y & 1);
+  }
+  // index of the site (x, y) (any parity-consistent integers; wrapped)
+  __host__ __device__ __forceinline__ int idx(int x, int y) const {
+    x &= N - 1;
+    y &= N - 1;
+    return (y << (lg - 1)) | (x >> 1);
+  }
+  __host__ __device__ __forceinline__ int nb(int x, int y, int d) const {
+    int da = d / 3 - 1, db = d % 3 - 1;
+    return idx(x + da + db, y + da - db);
+  }
+};
+
+static inline int ilog2(int v) {
+  int l = 0;
+  while ((1 << l) < v) ++l;
+  return l;
+}
+static inline Geo make_geo(int N) {
+  Geo g;
+  g.N = N;
+  g.lg = ilog2(N);
+  return g;
+}
+
+// -------------------------------------------------------------- error state
+void wl_set_error(const char *fmt, ...);
+#define WL_CUDA(call)                                                        \
+  do {                                                                       \
+    cudaError_t _e = (call);                                                 \
+    if (_e != cudaSuccess) {                                                 \
+      wl_set_error("%s:%d %s: %s", __FILE__, __LINE__, #call,                \
+                   cudaGetErrorString(_e));                                  \
+      return WL_ECUDA;                                                       \
+    }                                                                        \
+  } while (0)
+#define WL_TRY(expr)          \
+  do {                        \
+    int _rc = (expr);         \
+    if (_rc < 0) return _rc;  \
+  } while (0)
+
+// ------------------------------------------------------------ device buffer
+struct DBuf {
+  void *p = nullptr;
+  size_t bytes = 0;
+  int alloc(size_t b);
+  void release();
+  template <typename T>
+  T *as() const { return (T *)p; }
+};
+
+// ------------------------------------------------------------ host objects
+struct wl_op {
+  int N;
+  double m, c;
+  cudaStream_t stream;  // the library's own non-blocking work stream
+  cudaStream_t user;    // the caller's stream given to wilson_create
+  cudaEvent_t ev;       // orders the work stream after the caller's stream
+  Geo geo;
+  DBuf Uf64, Uf32;  // folded links V_mu(z) = sign * U_mu(z) / (2c), [2][N][N]
+  uint64_t gauge_hash;
+  DBuf scratch;     // small generic scratch for the per-step entry points
+};
+
+// one precision copy of a level's operator data
+struct LevelOps {
+  DBuf A;    // stencil [n][9][2][2]
+  DBuf den;  // Kaczmarz denominators ||A e_i||^2, [n][2] (real, T)
+  DBuf P;    // interpolation weights to the next level [n][2][4]
+};
+
+struct Level {
+  int N, B, n;  // lattice side, cell size to the next level (0 at coarsest), sites
+  Geo geo;
+  LevelOps op64, op32, opbf;  // FP64 master, FP32 copy, BF16 copy (den in FP32)
+  // cycle work vectors, [n][2][nrhs_cap] in the cycle precision
+  DBuf x, r, f, t;
+};
+
+struct wl_amg {
+  wl_op *op;
+  amg_params prm;
+  int L;
+  Level lev[8];
+  DBuf Ainv;      // coarsest inverse, complex double [nc][nc]
+  DBuf Ainv32;    // float copy
+  int nc;         // coarsest dimension 2 n_{L-1}
+  // Krylov workspace (level-0, [n][2][nrhs_cap])
+  int cap;        // right-hand sides the workspace holds
+  int cap_prec;   // precision the cycle buffers were sized for
+  DBuf V, Z, w, bh, xh, rr;
+  DBuf red;       // reduction partials
+  DBuf small;     // per-rhs scalars (Hessenberg, Givens, flags)
+  DBuf pinned_small;  // host-pinned mirror of flags
+  void *h_small;
+  // captured cycle graphs, one per (nrhs, precision)
+  struct G {
+    int nrhs, prec;
+    cudaGraphExec_t exec;
+  };
+  std::vector<G> graphs;
+};
+
+// --------------------------------------------------------- internal C++ API
+namespace wl {
+int enter(wl_op *op);  // work stream waits for everything queued on the caller's stream
+int ensure_workspace(wl_amg *a, int nrhs, int prec);
+int level_ops_build_copies(wl_amg *a);
+int coarsest_invert(wl_amg *a);
+int cycle_run(wl_amg *a, int nrhs, int prec, cudaStream_t s);  // lev[0].f -> lev[0].x
+int cycle_direct(wl_amg *a, int nrhs, int prec, cudaStream_t s);
+int dhat_apply_dev(wl_op *op, const void *x, int x_is_f32, zd *y, int nrhs, cudaStream_t s);
+int stencil_apply(wl_amg *a, int l, int prec, const void *x, void *y, const void *f, int nrhs,
+                  cudaStream_t s);
+int kaczmarz_sweeps(wl_amg *a, int l, int prec, void *x, void *r, int nrhs, int sweeps,
+                    cudaStream_t s);
+int restrict_op(wl_amg *a, int l, int prec, const void *r, void *fc, int nrhs, cudaStream_t s);
+int prolong_op(wl_amg *a, int l, int prec, const void *e, void *x, int nrhs, cudaStream_t s);
+int coarsest_apply(wl_amg *a, int prec, const void *f, void *x, int nrhs, cudaStream_t s);
+int fgmres_run(wl_amg *a, const zd *bh, zd *xh, int nrhs, double tol, wl_info *info);
+int build_dhat_stencil(wl_op *op, zd *A, cudaStream_t s);
+int symmetrise_stencil(int N, zd *A, cudaStream_t s);
+int compute_den64(int N, const zd *A, double *den, cudaStream_t s);
+// layout transposes between the ABI [nrhs][n][2] (FP64) and the internal
+// [n][2][nrhs] in precision prec (0 = double, 1 = float)
+int to_internal(const zd *src, void *dst, int n2, int nrhs, int prec, cudaStream_t s);
+int from_internal(const void *src, zd *dst, int n2, int nrhs, int prec, cudaStream_t s);
+size_t prec_bytes(int prec);  // bytes of one complex element of the cycle precision
+}  // namespace wl
+
+#define WL_GRID(n, b) ((unsigned)(((n) + (b)-1) / (b)))

@@ -1,0 +1,443 @@
+// wl_krylov.cu -- FP64 flexible GMRES(m) (Saad 1993) around the AMG cycle,
+// batched over right-hand sides in lock step: right preconditioning
+// z_j = M(v_j) (Sec. 4 uses GMRES(32) with a W(4,4) cycle), classical
+// Gram-Schmidt with optional reorthogonalisation, per right-hand-side
+// Givens rotations, restarts that recompute the true residual in FP64
+// (iterative refinement when the cycle runs in FP32), and the two-step
+// Schur solve of Sec. 3.2 around it (amg_solve).
+#include <math.h>
+#include <cmath>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "wl_common.cuh"
+
+namespace wl {
+int eo_reduce_internal(wl_op *op, const zd *b, zd *bh, int nrhs, cudaStream_t s);
+int eo_reconstruct_internal(wl_op *op, const zd *b, const zd *xe, zd *psi, int nrhs, cudaStream_t s);
+int take_even_internal(wl_op *op, const zd *psi, zd *xe, int nrhs, cudaStream_t s);
+int resolve_levels(int N, amg_params *p, int *Nl);
+}
+
+// per right-hand-side Krylov scalars
+struct KS {
+  int m, nrhs;
+  zd *hcol;    // [nrhs][m+1] accumulated column of H
+  zd *hpass;   // [nrhs][m+1] coefficients of the current Gram-Schmidt pass
+  zd *H;       // [nrhs][m+1][m]
+  zd *g;       // [nrhs][m+1]
+  zd *cs;      // [nrhs][m]
+  double *cc;  // [nrhs][m]
+  zd *y;       // [nrhs][m]
+  double *bnorm, *beta, *nrm2, *inv;  // [nrhs]
+  int *active, *stop, *jend, *iters;  // [nrhs]
+  int *running;                       // [1]
+};
+
+static KS ks_layout(void *base, int m, int nrhs) {
+  KS k;
+  k.m = m;
+  k.nrhs = nrhs;
+  char *p = (char *)base;
+  auto take = [&](size_t bytes) {
+    char *q = p;
+    p += (bytes + 255) & ~(size_t)255;
+    return q;
+  };
+  k.hcol = (zd *)take(sizeof(zd) * nrhs * (m + 1));
+  k.hpass = (zd *)take(sizeof(zd) * nrhs * (m + 1));
+  k.H = (zd *)take(sizeof(zd) * nrhs * (m + 1) * m);
+  k.g = (zd *)take(sizeof(zd) * nrhs * (m + 1));
+  k.cs = (zd *)take(sizeof(zd) * nrhs * m);
+  k.cc = (double *)take(sizeof(double) * nrhs * m);
+  k.y = (zd *)take(sizeof(zd) * nrhs * m);
+  k.bnorm = (double *)take(sizeof(double) * nrhs);
+  k.beta = (double *)take(sizeof(double) * nrhs);
+  k.nrm2 = (double *)take(sizeof(double) * nrhs);
+  k.inv = (double *)take(sizeof(double) * nrhs);
+  k.active = (int *)take(sizeof(int) * nrhs);
+  k.stop = (int *)take(sizeof(int) * nrhs);
+  k.jend = (int *)take(sizeof(int) * nrhs);
+  k.iters = (int *)take(sizeof(int) * nrhs);
+  k.running = (int *)take(sizeof(int) * 4);
+  return k;
+}
+
+// ------------------------------------------------------------- reductions
+// Block layout: blockDim = R * G with R = nrhs (<= 256) and G a power of two;
+// thread t handles right-hand side t % R, so element e of a vector
+// ([n][2][nrhs] flattened) always belongs to rhs e % R.
+#define KCH 8  // dots per launch
+template <typename Tv>
+__global__ void k_mdot(const cx<Tv> *__restrict__ V, long vstride, int kc, const zd *__restrict__ w,
+                       long E, int R, zd *__restrict__ part) {
+  extern __shared__ unsigned char sm_raw[];
+  zd *sm = (zd *)sm_raw;  // [KCH][blockDim]
+  int t = threadIdx.x, nt = blockDim.x;
+  int G = nt / R, q = t / R;
+  zd acc[KCH];
+#pragma unroll
+  for (int k = 0; k < KCH; ++k) acc[k] = mk(0.0, 0.0);
+  long stride = (long)gridDim.x * nt;
+  for (long e = (long)blockIdx.x * nt + t; e < E; e += stride) {
+    zd we = w[e];
+#pragma unroll
+    for (int k = 0; k < KCH; ++k)
+      if (k < kc) cfmac(acc[k], ccast<double>(V[k * vstride + e]), we);
+  }
+#pragma unroll
+  for (int k = 0; k < KCH; ++k) sm[k * nt + t] = acc[k];
+  __syncthreads();
+  for (int s = G >> 1; s > 0; s >>= 1) {
+    if (q < s)
+      for (int k = 0; k < kc; ++k) sm[k * nt + t] = sm[k * nt + t] + sm[k * nt + t + s * R];
+    __syncthreads();
+  }
+  if (q == 0)
+    for (int k = 0; k < kc; ++k) part[((long)blockIdx.x * kc + k) * R + t] = sm[k * nt + t];
+}
+
+// out[r][k0 + k] (= or +=) sum over blocks of part[b][k][r], fixed order
+__global__ void k_mdot_final(const zd *__restrict__ part, int nblk, int kc, int R, zd *out, int ostride,
+                             int k0, int accumulate, zd *copy_to) {
+  int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= kc * R) return;
+  int k = tid / R, r = tid % R;
+  zd s = mk(0.0, 0.0);
+  for (int b = 0; b < nblk; ++b) s = s + part[((long)b * kc + k) * R + r];
+  zd *o = out + (long)r * ostride + k0 + k;
+  if (copy_to) copy_to[(long)r * ostride + k0 + k] = s;
+  *o = accumulate ? (*o + s) : s;
+}
+
+// w -= sum_k V_k * coef[r][k]   (coef row stride cstride)
+template <typename Tv>
+__global__ void k_maxpy(const cx<Tv> *__restrict__ V, long vstride, int kc, const zd *__restrict__ coef,
+                        int cstride, double sign, zd *__restrict__ w, long E, int R) {
+  long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= E) return;
+  int r = (int)(e % R);
+  zd acc = w[e];
+  for (int k = 0; k < kc; ++k) {
+    zd c = coef[(long)r * cstride + k];
+    zd v = ccast<double>(V[k * vstride + e]);
+    zd p = c * v;
+    acc.re = fma(sign, p.re, acc.re);
+    acc.im = fma(sign, p.im, acc.im);
+  }
+  w[e] = acc;
+}
+
+__global__ void k_scale_rhs(const zd *__restrict__ in, zd *__restrict__ out, const double *__restrict__ f,
+                            long E, int R) {
+  long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= E) return;
+  out[e] = f[e % R] * in[e];
+}
+
+__global__ void k_sub(const zd *__restrict__ a, const zd *__restrict__ b, zd *__restrict__ c, long E) {
+  long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < E) c[e] = a[e] - b[e];
+}
+
+template <typename To, typename Ti>
+__global__ void k_cast(const cx<Ti> *__restrict__ a, cx<To> *__restrict__ b, long E) {
+  long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < E) b[e] = ccast<To>(a[e]);
+}
+
+// ------------------------------------------------------------------ Givens
+// column j of the Arnoldi process for every active right-hand side
+__global__ void k_givens(KS k, int j, double tol) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= k.nrhs) return;
+  int m = k.m;
+  if (!k.active[r] || k.stop[r]) {
+    k.inv[r] = 0.0;
+    return;
+  }
+  zd *hc = k.hcol + (long)r * (m + 1);
+  double hn = sqrt(fmax(k.nrm2[r], 0.0));
+  hc[j + 1] = mk(hn, 0.0);
+  zd *cs = k.cs + (long)r * m;
+  double *cc = k.cc + (long)r * m;
+  for (int i = 0; i < j; ++i) {
+    zd a = hc[i], b = hc[i + 1];
+    zd t = cc[i] * a + cs[i] * b;
+    hc[i + 1] = mk(0.0, 0.0) - cconj(cs[i]) * a + cc[i] * b;
+    hc[i] = t;
+  }
+  double aa = sqrt(cnorm2(hc[j])), bb = hn;
+  double den = sqrt(aa * aa + bb * bb);
+  zd *g = k.g + (long)r * (m + 1);
+  if (den == 0.0) {
+    cc[j] = 1.0;
+    cs[j] = mk(0.0, 0.0);
+  } else if (aa == 0.0) {
+    cc[j] = 0.0;
+    cs[j] = mk(1.0, 0.0);
+  } else {
+    cc[j] = aa / den;
+    zd ph = mk(hc[j].re / aa, hc[j].im / aa);
+    cs[j] = (bb / den) * ph;  // conj(h_{j+1}) = h_{j+1} (real)
+  }
+  hc[j] = cc[j] * hc[j] + cs[j] * hc[j + 1];
+  hc[j + 1] = mk(0.0, 0.0);
+  zd gj = g[j];
+  g[j + 1] = mk(0.0, 0.0) - cconj(cs[j]) * gj;
+  g[j] = cc[j] * gj;
+  zd *H = k.H + (long)r * (m + 1) * m;
+  for (int i = 0; i <= j; ++i) H[i * m + j] = hc[i];
+  k.iters[r] += 1;
+  k.jend[r] = j + 1;
+  double res = sqrt(cnorm2(g[j + 1]));
+  bool done = !(res > tol * k.bnorm[r]) || hn == 0.0 || !isfinite(res);
+  if (!isfinite(res)) k.running[1] = 1;  // NaN / Inf seen
+  k.inv[r] = (done || hn == 0.0) ? 0.0 : 1.0 / hn;
+  if (done) k.stop[r] = 1;
+  else atomicAdd(k.running, 1);
+}
+
+// y = H^-1 g (upper triangular, jend columns), zero beyond jend / inactive
+__global__ void k_trisolve(KS k) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= k.nrhs) return;
+  int m = k.m, je = k.active[r] ? k.jend[r] : 0;
+  const zd *H = k.H + (long)r * (m + 1) * m;
+  const zd *g = k.g + (long)r * (m + 1);
+  zd *y = k.y + (long)r * m;
+  for (int i = m - 1; i >= 0; --i) {
+    if (i >= je) {
+      y[i] = mk(0.0, 0.0);
+      continue;
+    }
+    zd s = g[i];
+    for (int q = i + 1; q < je; ++q) s = s - H[i * m + q] * y[q];
+    zd d = H[i * m + i];
+    double dn = cnorm2(d);
+    y[i] = (dn > 0) ? mk((s.re * d.re + s.im * d.im) / dn, (s.im * d.re - s.re * d.im) / dn) : mk(0.0, 0.0);
+  }
+}
+
+// start of a cycle: beta = ||r||, inv = active ? 1/beta : 0, g = (beta, 0..)
+__global__ void k_cycle_start(KS k) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= k.nrhs) return;
+  int m = k.m;
+  double beta = sqrt(fmax(k.nrm2[r], 0.0));
+  k.beta[r] = beta;
+  bool act = k.active[r] && beta > 0.0;
+  k.inv[r] = act ? 1.0 / beta : 0.0;
+  for (int i = 0; i <= m; ++i) k.g[(long)r * (m + 1) + i] = mk(0.0, 0.0);
+  k.g[(long)r * (m + 1)] = mk(act ? beta : 0.0, 0.0);
+  k.stop[r] = act ? 0 : 1;
+  k.jend[r] = 0;
+  for (int i = 0; i <= m; ++i) k.hcol[(long)r * (m + 1) + i] = mk(0.0, 0.0);
+}
+
+__global__ void k_zero_hcol(KS k) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= k.nrhs) return;
+  for (int i = 0; i <= k.m; ++i) k.hcol[(long)r * (k.m + 1) + i] = mk(0.0, 0.0);
+}
+
+__global__ void k_re_of(const zd *a, double *b, int n) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = a[i].re;
+}
+
+namespace wl {
+
+struct RedCfg {
+  int R, nt, nblk;
+};
+static RedCfg red_cfg(long E, int R) {
+  RedCfg c;
+  c.R = R;
+  int G = 1;
+  while (R * G * 2 <= 256) G *= 2;
+  c.nt = R * G;
+  long want = (E + c.nt - 1) / c.nt;
+  c.nblk = (int)std::max(1L, std::min(want, 1024L));
+  return c;
+}
+
+// out[r][k0+k] (=|+=) V_k^H w for k < kc, chunks of KCH
+template <typename Tv>
+static int mdots(wl_amg *a, const cx<Tv> *V, long vstride, int kc, const zd *w, long E, int R, zd *out,
+                 int ostride, int accumulate, zd *copy_to, cudaStream_t s) {
+  RedCfg c = red_cfg(E, R);
+  size_t sm = sizeof(zd) * KCH * c.nt;
+  for (int k0 = 0; k0 < kc; k0 += KCH) {
+    int kk = std::min(KCH, kc - k0);
+    k_mdot<Tv><<<c.nblk, c.nt, sm, s>>>(V + k0 * vstride, vstride, kk, w, E, R, a->red.as<zd>());
+    k_mdot_final<<<WL_GRID(kk * R, 128), 128, 0, s>>>(a->red.as<zd>(), c.nblk, kk, R, out, ostride, k0,
+                                                      accumulate, copy_to);
+  }
+  WL_CUDA(cudaGetLastError());
+  return WL_OK;
+}
+
+static int norms2(wl_amg *a, const zd *w, long E, int R, zd *tmp, double *out, cudaStream_t s) {
+  WL_TRY(mdots<double>(a, w, 0, 1, w, E, R, tmp, 1, 0, nullptr, s));
+  k_re_of<<<WL_GRID(R, 128), 128, 0, s>>>(tmp, out, R);
+  WL_CUDA(cudaGetLastError());
+  return WL_OK;
+}
+
+int fgmres_run(wl_amg *a, const zd *bh, zd *xh, int nrhs, double tol, wl_info *info) {
+  wl_op *op = a->op;
+  cudaStream_t s = op->stream;
+  int prec = a->prm.precision, m = a->prm.fgmres_m;
+  int pcyc = prec;  // cycle precision
+  long n2 = (long)a->lev[0].n * 2;
+  long E = n2 * nrhs;
+  long vs = E;  // stride between Krylov vectors
+  KS k = ks_layout(a->small.p, m, nrhs);
+  zd *V = a->V.as<zd>(), *w = a->w.as<zd>(), *rr = a->rr.as<zd>();
+  size_t zb_ = prec_bytes(pcyc);
+  char *Zb = (char *)a->Z.p;
+  unsigned gE = WL_GRID(E, 256);
+  zd *tmpc = a->small.as<zd>() + (a->small.bytes / sizeof(zd)) - 2 * (size_t)nrhs - 8;
+
+  std::vector<int> active(nrhs, 1), iters(nrhs, 0), restarts(nrhs, 0);
+  std::vector<double> relres(nrhs, 0.0), bnorm(nrhs, 0.0);
+  double *h_d = (double *)a->h_small;
+
+  // ||bhat||
+  WL_TRY(norms2(a, bh, E, nrhs, tmpc, k.nrm2, s));
+  WL_CUDA(cudaMemcpyAsync(h_d, k.nrm2, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s));
+  WL_CUDA(cudaStreamSynchronize(s));
+  for (int r = 0; r < nrhs; ++r) bnorm[r] = sqrt(h_d[r]) > 0 ? sqrt(h_d[r]) : 1.0;
+  WL_CUDA(cudaMemcpyAsync(k.bnorm, bnorm.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, s));
+  WL_CUDA(cudaMemsetAsync(k.iters, 0, sizeof(int) * nrhs, s));
+  int status = WL_OK;
+  for (int cyc = 0;; ++cyc) {
+    // true residual in FP64: rr = bhat - Dhat x
+    WL_TRY(dhat_apply_dev(op, xh, 0, w, nrhs, s));
+    k_sub<<<gE, 256, 0, s>>>(bh, w, rr, E);
+    WL_TRY(norms2(a, rr, E, nrhs, tmpc, k.nrm2, s));
+    WL_CUDA(cudaMemcpyAsync(h_d, k.nrm2, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s));
+    WL_CUDA(cudaStreamSynchronize(s));
+    int any = 0;
+    for (int r = 0; r < nrhs; ++r) {
+      double rn = sqrt(h_d[r]);
+      if (!std::isfinite(rn)) {
+        wl_set_error("non-finite residual for right-hand side %d", r);
+        return WL_NAN;
+      }
+      relres[r] = rn / bnorm[r];
+      active[r] = active[r] && relres[r] > tol && cyc < a->prm.max_restarts;
+      any |= active[r];
+    }
+    if (!any) break;
+    WL_CUDA(cudaMemcpyAsync(k.active, active.data(), sizeof(int) * nrhs, cudaMemcpyHostToDevice, s));
+    k_cycle_start<<<WL_GRID(nrhs, 128), 128, 0, s>>>(k);
+    k_scale_rhs<<<gE, 256, 0, s>>>(rr, V, k.inv, E, nrhs);
+    int jdone = 0;
+    for (int j = 0; j < m; ++j) {
+      zd *vj = V + j * vs;
+      void *zj = Zb + (size_t)j * vs * zb_;
+      // z_j = M(v_j) in the cycle precision
+      if (pcyc == WL_FP64) WL_CUDA(cudaMemcpyAsync(a->lev[0].f.p, vj, sizeof(zd) * E, cudaMemcpyDeviceToDevice, s));
+      else k_cast<float, double><<<gE, 256, 0, s>>>(vj, a->lev[0].f.as<zf>(), E);
+      WL_TRY(cycle_run(a, nrhs, pcyc, s));
+      WL_CUDA(cudaMemcpyAsync(zj, a->lev[0].x.p, zb_ * E, cudaMemcpyDeviceToDevice, s));
+      // w = Dhat z_j (FP64)
+      WL_TRY(dhat_apply_dev(op, zj, pcyc != WL_FP64, w, nrhs, s));
+      // Gram-Schmidt against v_0 .. v_j
+      k_zero_hcol<<<WL_GRID(nrhs, 128), 128, 0, s>>>(k);
+      for (int pass = 0; pass < a->prm.gs_passes; ++pass) {
+        WL_TRY(mdots<double>(a, V, vs, j + 1, w, E, nrhs, k.hcol, m + 1, 1, k.hpass, s));
+        k_maxpy<double><<<gE, 256, 0, s>>>(V, vs, j + 1, k.hpass, m + 1, -1.0, w, E, nrhs);
+      }
+      WL_TRY(norms2(a, w, E, nrhs, tmpc, k.nrm2, s));
+      WL_CUDA(cudaMemsetAsync(k.running, 0, sizeof(int) * 2, s));
+      k_givens<<<WL_GRID(nrhs, 128), 128, 0, s>>>(k, j, tol);
+      if (j + 1 < m) k_scale_rhs<<<gE, 256, 0, s>>>(w, V + (j + 1) * vs, k.inv, E, nrhs);
+      WL_CUDA(cudaGetLastError());
+      int run[2];
+      WL_CUDA(cudaMemcpyAsync(h_d + nrhs, k.running, sizeof(int) * 2, cudaMemcpyDeviceToHost, s));
+      WL_CUDA(cudaStreamSynchronize(s));
+      memcpy(run, h_d + nrhs, sizeof(int) * 2);
+      jdone = j + 1;
+      if (run[1]) {
+        wl_set_error("non-finite Arnoldi residual");
+        return WL_NAN;
+      }
+      if (run[0] == 0) break;
+    }
+    k_trisolve<<<WL_GRID(nrhs, 128), 128, 0, s>>>(k);
+    if (pcyc == WL_FP64) k_maxpy<double><<<gE, 256, 0, s>>>(a->Z.as<zd>(), vs, jdone, k.y, m, 1.0, xh, E, nrhs);
+    else k_maxpy<float><<<gE, 256, 0, s>>>(a->Z.as<zf>(), vs, jdone, k.y, m, 1.0, xh, E, nrhs);
+    WL_CUDA(cudaGetLastError());
+    for (int r = 0; r < nrhs; ++r)
+      if (active[r]) restarts[r]++;
+  }
+  WL_CUDA(cudaMemcpyAsync(iters.data(), k.iters, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, s));
+  WL_CUDA(cudaStreamSynchronize(s));
+  for (int r = 0; r < nrhs; ++r) {
+    bool ok = relres[r] <= tol;
+    if (!ok) status = WL_NOT_CONVERGED;
+    if (info) {
+      info[r].status = ok ? WL_OK : WL_NOT_CONVERGED;
+      info[r].restarts = restarts[r];
+      info[r].iters = iters[r];
+      info[r].true_relres = relres[r];
+    }
+  }
+  return status;
+}
+
+}  // namespace wl
+
+#define MAX_BATCH 256
+
+extern "C" int amg_fgmres(wl_amg *a, const void *bhat, void *x, int nrhs, double tol, wl_info *info) {
+  if (!a || !bhat || !x || nrhs < 1 || nrhs > MAX_BATCH || !(tol > 0)) {
+    wl_set_error("amg_fgmres: invalid argument (1 <= nrhs <= %d, tol > 0)", MAX_BATCH);
+    return WL_EINVAL;
+  }
+  WL_TRY(wl::enter(a->op));
+  WL_TRY(wl::ensure_workspace(a, nrhs, a->prm.precision));
+  cudaStream_t s = a->op->stream;
+  int n2 = a->lev[0].n * 2;
+  WL_TRY(wl::to_internal((const zd *)bhat, a->bh.p, n2, nrhs, WL_FP64, s));
+  WL_TRY(wl::to_internal((const zd *)x, a->xh.p, n2, nrhs, WL_FP64, s));
+  int rc = wl::fgmres_run(a, a->bh.as<zd>(), a->xh.as<zd>(), nrhs, tol, info);
+  if (rc < 0) return rc;
+  WL_TRY(wl::from_internal(a->xh.p, (zd *)x, n2, nrhs, WL_FP64, s));
+  WL_CUDA(cudaStreamSynchronize(s));
+  return rc;
+}
+
+extern "C" int amg_solve(wl_amg *a, const void *b, void *x, int nrhs, double tol, wl_info *info) {
+  if (!a || !b || !x || nrhs < 1 || !(tol > 0)) {
+    wl_set_error("amg_solve: invalid argument");
+    return WL_EINVAL;
+  }
+  wl_op *op = a->op;
+  WL_TRY(wl::enter(op));
+  cudaStream_t s = op->stream;
+  int N = op->N;
+  int status = WL_OK;
+  for (int r0 = 0; r0 < nrhs; r0 += MAX_BATCH) {
+    int nb = std::min(MAX_BATCH, nrhs - r0);
+    WL_TRY(wl::ensure_workspace(a, nb, a->prm.precision));
+    const zd *bb = (const zd *)b + (size_t)r0 * N * N * 2;
+    zd *xx = (zd *)x + (size_t)r0 * N * N * 2;
+    WL_TRY(wl::eo_reduce_internal(op, bb, a->bh.as<zd>(), nb, s));
+    if (a->prm.zero_guess)
+      WL_CUDA(cudaMemsetAsync(a->xh.p, 0, sizeof(zd) * (size_t)a->lev[0].n * 2 * nb, s));
+    else
+      WL_TRY(wl::take_even_internal(op, xx, a->xh.as<zd>(), nb, s));
+    int rc = wl::fgmres_run(a, a->bh.as<zd>(), a->xh.as<zd>(), nb, tol, info ? info + r0 : nullptr);
+    if (rc < 0) return rc;
+    if (rc) status = rc;
+    WL_TRY(wl::eo_reconstruct_internal(op, bb, a->xh.as<zd>(), xx, nb, s));
+  }
+  WL_CUDA(cudaStreamSynchronize(s));
+  return status;
+}

@@ -1,0 +1,464 @@
+// wl_mg.cu -- solve-phase multigrid kernels on the GB300: block-stencil
+// apply, multicolour Kaczmarz (Sec. 3.1), Galerkin transfers P^H / P
+// (Secs. 3.3, 3.5), the dense coarsest solve (Sec. 4), and the cycle driver
+// (Sec. 1 two-grid correction applied recursively).
+//
+// Vectors use the internal layout [n][2][nrhs] (site, spin, right-hand
+// side innermost) so that a warp covers consecutive right-hand sides of one
+// site and shares that site's stencil coefficients.
+#include "wl_common.cuh"
+
+
+// ------------------------------------------------------------ stencil apply
+// y = A x, or y = f - A x when f != nullptr (y may alias f).
+template <typename T, typename S>
+__global__ void __launch_bounds__(256) k_stencil(Geo g, const S *__restrict__ A, const cx<T> *__restrict__ x,
+                                                 const cx<T> *f, cx<T> *y, int nrhs) {
+  long tid = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  int n = g.nsites();
+  if (tid >= (long)n * nrhs) return;
+  int h = (int)(tid / nrhs), r = (int)(tid - (long)h * nrhs);
+  int px, py;
+  g.xy(h, px, py);
+  const S *Ah = A + (long)h * 36;
+  cx<T> y0 = mk<T>(0, 0), y1 = mk<T>(0, 0);
+#pragma unroll
+  for (int d = 0; d < 9; ++d) {
+    long j = (long)g.nb(px, py, d) * 2 * nrhs + r;
+    cx<T> x0 = x[j], x1 = x[j + nrhs];
+    cfma(y0, ld<T>(Ah + d * 4 + 0), x0);
+    cfma(y0, ld<T>(Ah + d * 4 + 1), x1);
+    cfma(y1, ld<T>(Ah + d * 4 + 2), x0);
+    cfma(y1, ld<T>(Ah + d * 4 + 3), x1);
+  }
+  long o = (long)h * 2 * nrhs + r;
+  if (f) {
+    y0 = f[o] - y0;
+    y1 = f[o + nrhs] - y1;
+  }
+  y[o] = y0;
+  y[o + nrhs] = y1;
+}
+
+// ---------------------------------------------------------------- Kaczmarz
+// One colour of the multicolour sweep.  Colour k = 4 (a mod 4) + (b mod 4);
+// thread q enumerates a = ka + 4 (q / (N/8)), b = kb + 4 (q mod N/8).
+// Column (h, t) of a gamma5-Hermitian A has the entries
+//   A_{(j,s),(h,t)} = g_s g_t conj(A[h][d][t][s]),  j = nb(h, d),
+// so s = <r, A e> / ||A e||^2 = g_t sum_{d,s} A[h][d][t][s] g_s r_{j,s} / den
+// reads only row h of the stencil; then x_(h,t) += omega s and
+// r_(j,s) -= omega s g_s g_t conj(A[h][d][t][s]).  Spin 0 precedes spin 1.
+template <typename T, typename S>
+__global__ void __launch_bounds__(128) k_kacz(Geo g, int colour, const S *__restrict__ A,
+                                              const T *__restrict__ den, cx<T> *__restrict__ x,
+                                              cx<T> *__restrict__ r, int nrhs, T omega) {
+  long tid = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  int n16 = g.nsites() >> 4;
+  if (tid >= (long)n16 * nrhs) return;
+  int q = (int)(tid / nrhs), rh = (int)(tid - (long)q * nrhs);
+  int nb8 = g.N >> 3;
+  int a = (colour >> 2) + 4 * (q / nb8);
+  int b = (colour & 3) + 4 * (q % nb8);
+  int px = (a + b) & (g.N - 1), py = (a - b) & (g.N - 1);
+  int h = g.idx(px, py);
+  long jj[9];
+  cx<T> rv[9][2];
+#pragma unroll
+  for (int d = 0; d < 9; ++d) {
+    jj[d] = (long)g.nb(px, py, d) * 2 * nrhs + rh;
+    rv[d][0] = r[jj[d]];
+    rv[d][1] = r[jj[d] + nrhs];
+  }
+  const S *Ah = A + (long)h * 36;
+  cx<T> xs[2];
+  long xo = (long)h * 2 * nrhs + rh;
+  xs[0] = x[xo];
+  xs[1] = x[xo + nrhs];
+#pragma unroll
+  for (int t = 0; t < 2; ++t) {
+    cx<T> num = mk<T>(0, 0);
+#pragma unroll
+    for (int d = 0; d < 9; ++d) {
+      cfma(num, ld<T>(Ah + d * 4 + t * 2 + 0), rv[d][0]);
+      cx<T> m1 = ld<T>(Ah + d * 4 + t * 2 + 1);
+      cfma(num, mk<T>(-m1.re, -m1.im), rv[d][1]);
+    }
+    T sc = omega / den[2 * h + t];
+    if (t) sc = -sc;
+    cx<T> sv = sc * num;
+    xs[t] = xs[t] + sv;
+#pragma unroll
+    for (int d = 0; d < 9; ++d) {
+#pragma unroll
+      for (int s = 0; s < 2; ++s) {
+        cx<T> a_ = ld<T>(Ah + d * 4 + t * 2 + s);
+        // rv -= sv * g_s g_t conj(a)
+        T gg = (s == t) ? (T)1 : (T)-1;
+        cx<T> c = cconj(a_);
+        cx<T> p = sv * c;
+        rv[d][s] = mk<T>(rv[d][s].re - gg * p.re, rv[d][s].im - gg * p.im);
+      }
+    }
+  }
+  x[xo] = xs[0];
+  x[xo + nrhs] = xs[1];
+#pragma unroll
+  for (int d = 0; d < 9; ++d) {
+    r[jj[d]] = rv[d][0];
+    r[jj[d] + nrhs] = rv[d][1];
+  }
+}
+
+// ---------------------------------------------------------------- transfers
+// fc = P^H r: coarse site hc gathers the fine points of the (2B-1)^2 box
+// around its C point; a fine point at offset (da, db) sees hc as its cell
+// corner k = [da < 0] + 2 [db < 0].
+template <typename T, typename S>
+__global__ void k_restrict(Geo gf, Geo gc, int lgB, const S *__restrict__ P,
+                           const cx<T> *__restrict__ r, cx<T> *__restrict__ fc, int nrhs) {
+  long tid = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  int nc = gc.nsites();
+  if (tid >= (long)nc * nrhs) return;
+  int hc = (int)(tid / nrhs), rh = (int)(tid - (long)hc * nrhs);
+  int xc, yc;
+  gc.xy(hc, xc, yc);
+  int B = 1 << lgB;
+  int X = xc << lgB, Y = yc << lgB;
+  cx<T> a0 = mk<T>(0, 0), a1 = mk<T>(0, 0);
+  for (int da = -(B - 1); da <= B - 1; ++da)
+    for (int db = -(B - 1); db <= B - 1; ++db) {
+      int hf = gf.idx(X + da + db, Y + da - db);
+      int k = (da < 0 ? 1 : 0) + (db < 0 ? 2 : 0);
+      long j = (long)hf * 2 * nrhs + rh;
+      cfmac(a0, ld<T>(P + (long)hf * 8 + k), r[j]);
+      cfmac(a1, ld<T>(P + (long)hf * 8 + 4 + k), r[j + nrhs]);
+    }
+  long o = (long)hc * 2 * nrhs + rh;
+  fc[o] = a0;
+  fc[o + nrhs] = a1;
+}
+
+// x += P e: fine site (a, b) with cell origin (a0, b0) = B floor((a, b)/B)
+// interpolates from the existing corners (a0 + ka B, b0 + kb B).
+template <typename T, typename S>
+__global__ void k_prolong(Geo gf, Geo gc, int lgB, const S *__restrict__ P,
+                          const cx<T> *__restrict__ e, cx<T> *__restrict__ x, int nrhs) {
+  long tid = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  int nf = gf.nsites();
+  if (tid >= (long)nf * nrhs) return;
+  int hf = (int)(tid / nrhs), rh = (int)(tid - (long)hf * nrhs);
+  int px, py;
+  gf.xy(hf, px, py);
+  int B = 1 << lgB;
+  int a = (px + py) >> 1, b = (px - py) >> 1;
+  int a0 = a & ~(B - 1), b0 = b & ~(B - 1);
+  int ra = a - a0, rb = b - b0;
+  long o = (long)hf * 2 * nrhs + rh;
+  cx<T> x0 = x[o], x1 = x[o + nrhs];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    int ka = k & 1, kb = k >> 1;
+    if ((ka && !ra) || (kb && !rb)) continue;
+    int ac = a0 + ka * B, bc = b0 + kb * B;
+    int xf = (ac + bc) & (gf.N - 1), yf = (ac - bc) & (gf.N - 1);
+    long j = (long)gc.idx(xf >> lgB, yf >> lgB) * 2 * nrhs + rh;
+    cfma(x0, ld<T>(P + (long)hf * 8 + k), e[j]);
+    cfma(x1, ld<T>(P + (long)hf * 8 + 4 + k), e[j + nrhs]);
+  }
+  x[o] = x0;
+  x[o + nrhs] = x1;
+}
+
+// x = Ainv f on the coarsest level, FP64 arithmetic: 8 rows per block, one
+// warp per row, lanes stride the columns, shuffle reduction.
+template <typename T>
+__global__ void __launch_bounds__(256) k_coarsest(int nc, const zd *__restrict__ Ainv,
+                                                  const cx<T> *__restrict__ f, cx<T> *__restrict__ x,
+                                                  int nrhs) {
+  int row = blockIdx.x * 8 + (threadIdx.x >> 5);
+  int lane = threadIdx.x & 31;
+  int rh = blockIdx.y;
+  if (row >= nc) return;
+  zd acc = mk(0.0, 0.0);
+  const zd *Ar = Ainv + (long)row * nc;
+  for (int j = lane; j < nc; j += 32) cfma(acc, Ar[j], ccast<double>(f[(long)j * nrhs + rh]));
+#pragma unroll
+  for (int off = 16; off; off >>= 1) {
+    acc.re += __shfl_down_sync(0xffffffffu, acc.re, off);
+    acc.im += __shfl_down_sync(0xffffffffu, acc.im, off);
+  }
+  if (lane == 0) x[(long)row * nrhs + rh] = ccast<T>(acc);
+}
+
+template <typename T>
+__global__ void k_axpy_inplace(cx<T> *__restrict__ y, const cx<T> *__restrict__ x, long n) {
+  long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = y[i] + x[i];
+}
+
+namespace wl {
+
+static const LevelOps &ops_of(const Level &L, int prec) {
+  return prec == WL_FP64 ? L.op64 : prec == WL_FP32 ? L.op32 : L.opbf;
+}
+
+int stencil_apply(wl_amg *a, int l, int prec, const void *x, void *y, const void *f, int nrhs,
+                  cudaStream_t s) {
+  const Level &L = a->lev[l];
+  const LevelOps &o = ops_of(L, prec);
+  long tot = (long)L.n * nrhs;
+  unsigned grid = WL_GRID(tot, 256);
+  if (prec == WL_FP64)
+    k_stencil<double, zd><<<grid, 256, 0, s>>>(L.geo, o.A.as<zd>(), (const zd *)x, (const zd *)f, (zd *)y, nrhs);
+  else if (prec == WL_FP32)
+    k_stencil<float, zf><<<grid, 256, 0, s>>>(L.geo, o.A.as<zf>(), (const zf *)x, (const zf *)f, (zf *)y, nrhs);
+  else
+    k_stencil<float, zb><<<grid, 256, 0, s>>>(L.geo, o.A.as<zb>(), (const zf *)x, (const zf *)f, (zf *)y, nrhs);
+  WL_CUDA(cudaGetLastError());
+  return WL_OK;
+}
+
+int kaczmarz_sweeps(wl_amg *a, int l, int prec, void *x, void *r, int nrhs, int sweeps,
+                    cudaStream_t s) {
+  const Level &L = a->lev[l];
+  const LevelOps &o = ops_of(L, prec);
+  long tot = (long)(L.n >> 4) * nrhs;
+  unsigned grid = WL_GRID(tot, 128);
+  for (int sw = 0; sw < sweeps; ++sw)
+    for (int c = 0; c < 16; ++c) {
+      if (prec == WL_FP64)
+        k_kacz<double, zd><<<grid, 128, 0, s>>>(L.geo, c, o.A.as<zd>(), o.den.as<double>(), (zd *)x, (zd *)r, nrhs, a->prm.omega);
+      else if (prec == WL_FP32)
+        k_kacz<float, zf><<<grid, 128, 0, s>>>(L.geo, c, o.A.as<zf>(), o.den.as<float>(), (zf *)x, (zf *)r, nrhs, (float)a->prm.omega);
+      else
+        k_kacz<float, zb><<<grid, 128, 0, s>>>(L.geo, c, o.A.as<zb>(), o.den.as<float>(), (zf *)x, (zf *)r, nrhs, (float)a->prm.omega);
+    }
+  WL_CUDA(cudaGetLastError());
+  return WL_OK;
+}
+
+int restrict_op(wl_amg *a, int l, int prec, const void *r, void *fc, int nrhs, cudaStream_t s) {
+  const Level &F = a->lev[l], &Cl = a->lev[l + 1];
+  const LevelOps &o = ops_of(F, prec);
+  int lgB = ilog2(F.B);
+  long tot = (long)Cl.n * nrhs;
+  unsigned grid = WL_GRID(tot, 128);
+  if (prec == WL_FP64)
+    k_restrict<double, zd><<<grid, 128, 0, s>>>(F.geo, Cl.geo, lgB, o.P.as<zd>(), (const zd *)r, (zd *)fc, nrhs);
+  else if (prec == WL_FP32)
+    k_restrict<float, zf><<<grid, 128, 0, s>>>(F.geo, Cl.geo, lgB, o.P.as<zf>(), (const zf *)r, (zf *)fc, nrhs);
+  else
+    k_restrict<float, zb><<<grid, 128, 0, s>>>(F.geo, Cl.geo, lgB, o.P.as<zb>(), (const zf *)r, (zf *)fc, nrhs);
+  WL_CUDA(cudaGetLastError());
+  return WL_OK;
+}
+
+int prolong_op(wl_amg *a, int l, int prec, const void *e, void *x, int nrhs, cudaStream_t s) {
+  const Level &F = a->lev[l], &Cl = a->lev[l + 1];
+  const LevelOps &o = ops_of(F, prec);
+  int lgB = ilog2(F.B);
+  long tot = (long)F.n * nrhs;
+  unsigned grid = WL_GRID(tot, 256);
+  if (prec == WL_FP64)
+    k_prolong<double, zd><<<grid, 256, 0, s>>>(F.geo, Cl.geo, lgB, o.P.as<zd>(), (const zd *)e, (zd *)x, nrhs);
+  else if (prec == WL_FP32)
+    k_prolong<float, zf><<<grid, 256, 0, s>>>(F.geo, Cl.geo, lgB, o.P.as<zf>(), (const zf *)e, (zf *)x, nrhs);
+  else
+    k_prolong<float, zb><<<grid, 256, 0, s>>>(F.geo, Cl.geo, lgB, o.P.as<zb>(), (const zf *)e, (zf *)x, nrhs);
+  WL_CUDA(cudaGetLastError());
+  return WL_OK;
+}
+
+int coarsest_apply(wl_amg *a, int prec, const void *f, void *x, int nrhs, cudaStream_t s) {
+  dim3 grid(WL_GRID(a->nc, 8), nrhs);
+  if (prec == WL_FP64)
+    k_coarsest<double><<<grid, 256, 0, s>>>(a->nc, a->Ainv.as<zd>(), (const zd *)f, (zd *)x, nrhs);
+  else
+    k_coarsest<float><<<grid, 256, 0, s>>>(a->nc, a->Ainv.as<zd>(), (const zf *)f, (zf *)x, nrhs);
+  WL_CUDA(cudaGetLastError());
+  return WL_OK;
+}
+
+// recursive cycle on level l: lev[l].x = M(lev[l].f) starting from x = 0
+static int cycle_level(wl_amg *a, int l, int nrhs, int prec, cudaStream_t s) {
+  Level &L = a->lev[l];
+  size_t eb = prec_bytes(prec);
+  size_t vb = eb * (size_t)L.n * 2 * nrhs;
+  if (l == a->L - 1) return coarsest_apply(a, prec, L.f.p, L.x.p, nrhs, s);
+  WL_CUDA(cudaMemsetAsync(L.x.p, 0, vb, s));
+  WL_CUDA(cudaMemcpyAsync(L.r.p, L.f.p, vb, cudaMemcpyDeviceToDevice, s));
+  WL_TRY(kaczmarz_sweeps(a, l, prec, L.x.p, L.r.p, nrhs, a->prm.nu_pre, s));
+  Level &C = a->lev[l + 1];
+  WL_TRY(restrict_op(a, l, prec, L.r.p, C.f.p, nrhs, s));
+  int gamma = (a->prm.cycle == WL_CYCLE_W) ? 2 : 1;
+  size_t cb = eb * (size_t)C.n * 2 * nrhs;
+  for (int g = 0; g < gamma; ++g) {
+    if (g > 0) {
+      // coarse residual of the correction so far, then one more cycle
+      WL_CUDA(cudaMemcpyAsync(C.t.p, C.x.p, cb, cudaMemcpyDeviceToDevice, s));
+      WL_TRY(stencil_apply(a, l + 1, prec, C.t.p, C.f.p, C.f.p, nrhs, s));
+    }
+    WL_TRY(cycle_level(a, l + 1, nrhs, prec, s));
+    if (g > 0) {
+      long ne = (long)C.n * 2 * nrhs;
+      if (prec == WL_FP64) k_axpy_inplace<double><<<WL_GRID(ne, 256), 256, 0, s>>>(C.x.as<zd>(), C.t.as<zd>(), ne);
+      else k_axpy_inplace<float><<<WL_GRID(ne, 256), 256, 0, s>>>(C.x.as<zf>(), C.t.as<zf>(), ne);
+      WL_CUDA(cudaGetLastError());
+    }
+  }
+  WL_TRY(prolong_op(a, l, prec, C.x.p, L.x.p, nrhs, s));
+  WL_TRY(stencil_apply(a, l, prec, L.x.p, L.r.p, L.f.p, nrhs, s));
+  WL_TRY(kaczmarz_sweeps(a, l, prec, L.x.p, L.r.p, nrhs, a->prm.nu_post, s));
+  return WL_OK;
+}
+
+// lev[0].x = M(lev[0].f) without graph capture (setup's adaptive step)
+int cycle_direct(wl_amg *a, int nrhs, int prec, cudaStream_t s) { return cycle_level(a, 0, nrhs, prec, s); }
+
+// lev[0].x = M(lev[0].f); captured once per (nrhs, precision) as a CUDA graph
+int cycle_run(wl_amg *a, int nrhs, int prec, cudaStream_t s) {
+  for (auto &g : a->graphs)
+    if (g.nrhs == nrhs && g.prec == prec) {
+      WL_CUDA(cudaGraphLaunch(g.exec, s));
+      return WL_OK;
+    }
+  cudaGraph_t graph;
+  WL_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  int rc = cycle_level(a, 0, nrhs, prec, s);
+  cudaError_t e = cudaStreamEndCapture(s, &graph);
+  if (rc) {
+    if (e == cudaSuccess) cudaGraphDestroy(graph);
+    return rc;
+  }
+  WL_CUDA(e);
+  wl_amg::G gg;
+  gg.nrhs = nrhs;
+  gg.prec = prec;
+  e = cudaGraphInstantiate(&gg.exec, graph, 0);
+  cudaGraphDestroy(graph);
+  WL_CUDA(e);
+  a->graphs.push_back(gg);
+  WL_CUDA(cudaGraphLaunch(gg.exec, s));
+  return WL_OK;
+}
+
+}  // namespace wl
+
+// ------------------------------------------------------ per-step entry points
+static int check_amg(wl_amg *a, int level, int nrhs, int prec, const char *who) {
+  if (!a || nrhs < 1 || level < 0 || level >= a->L ||
+      (prec != WL_FP64 && prec != WL_FP32 && prec != WL_FP32_BF16)) {
+    wl_set_error("%s: invalid argument", who);
+    return WL_EINVAL;
+  }
+  return wl::enter(a->op);
+}
+
+struct StepBufs {
+  DBuf b[3];
+  ~StepBufs() {
+    for (auto &x : b) x.release();
+  }
+};
+
+extern "C" int amg_level_apply(wl_amg *a, int level, const void *x, void *y, int nrhs, int prec) {
+  WL_TRY(check_amg(a, level, nrhs, prec, "amg_level_apply"));
+  if (!x || !y) return WL_EINVAL;
+  cudaStream_t s = a->op->stream;
+  int n2 = a->lev[level].n * 2;
+  size_t vb = wl::prec_bytes(prec) * (size_t)n2 * nrhs;
+  int pin = prec == WL_FP64 ? WL_FP64 : WL_FP32;
+  StepBufs sb;
+  WL_TRY(sb.b[0].alloc(vb));
+  WL_TRY(sb.b[1].alloc(vb));
+  WL_TRY(wl::to_internal((const zd *)x, sb.b[0].p, n2, nrhs, pin, s));
+  WL_TRY(wl::stencil_apply(a, level, prec, sb.b[0].p, sb.b[1].p, nullptr, nrhs, s));
+  WL_TRY(wl::from_internal(sb.b[1].p, (zd *)y, n2, nrhs, pin, s));
+  WL_CUDA(cudaStreamSynchronize(s));
+  return WL_OK;
+}
+
+extern "C" int amg_kaczmarz(wl_amg *a, int level, void *x, void *r, int nrhs, int sweeps, int prec) {
+  WL_TRY(check_amg(a, level, nrhs, prec, "amg_kaczmarz"));
+  if (!x || !r || sweeps < 0 || level == a->L - 1) {
+    wl_set_error("amg_kaczmarz: invalid argument (the coarsest level is not relaxed)");
+    return WL_EINVAL;
+  }
+  cudaStream_t s = a->op->stream;
+  int n2 = a->lev[level].n * 2;
+  size_t vb = wl::prec_bytes(prec) * (size_t)n2 * nrhs;
+  int pin = prec == WL_FP64 ? WL_FP64 : WL_FP32;
+  StepBufs sb;
+  WL_TRY(sb.b[0].alloc(vb));
+  WL_TRY(sb.b[1].alloc(vb));
+  WL_TRY(wl::to_internal((const zd *)x, sb.b[0].p, n2, nrhs, pin, s));
+  WL_TRY(wl::to_internal((const zd *)r, sb.b[1].p, n2, nrhs, pin, s));
+  WL_TRY(wl::kaczmarz_sweeps(a, level, prec, sb.b[0].p, sb.b[1].p, nrhs, sweeps, s));
+  WL_TRY(wl::from_internal(sb.b[0].p, (zd *)x, n2, nrhs, pin, s));
+  WL_TRY(wl::from_internal(sb.b[1].p, (zd *)r, n2, nrhs, pin, s));
+  WL_CUDA(cudaStreamSynchronize(s));
+  return WL_OK;
+}
+
+extern "C" int amg_restrict(wl_amg *a, int level, const void *r, void *fc, int nrhs, int prec) {
+  WL_TRY(check_amg(a, level, nrhs, prec, "amg_restrict"));
+  if (!r || !fc || level == a->L - 1) return WL_EINVAL;
+  cudaStream_t s = a->op->stream;
+  int nf2 = a->lev[level].n * 2, nc2 = a->lev[level + 1].n * 2;
+  size_t eb = wl::prec_bytes(prec);
+  int pin = prec == WL_FP64 ? WL_FP64 : WL_FP32;
+  StepBufs sb;
+  WL_TRY(sb.b[0].alloc(eb * nf2 * nrhs));
+  WL_TRY(sb.b[1].alloc(eb * nc2 * nrhs));
+  WL_TRY(wl::to_internal((const zd *)r, sb.b[0].p, nf2, nrhs, pin, s));
+  WL_TRY(wl::restrict_op(a, level, prec, sb.b[0].p, sb.b[1].p, nrhs, s));
+  WL_TRY(wl::from_internal(sb.b[1].p, (zd *)fc, nc2, nrhs, pin, s));
+  WL_CUDA(cudaStreamSynchronize(s));
+  return WL_OK;
+}
+
+extern "C" int amg_prolong(wl_amg *a, int level, const void *e, void *x, int nrhs, int prec) {
+  WL_TRY(check_amg(a, level, nrhs, prec, "amg_prolong"));
+  if (!e || !x || level == a->L - 1) return WL_EINVAL;
+  cudaStream_t s = a->op->stream;
+  int nf2 = a->lev[level].n * 2, nc2 = a->lev[level + 1].n * 2;
+  size_t eb = wl::prec_bytes(prec);
+  int pin = prec == WL_FP64 ? WL_FP64 : WL_FP32;
+  StepBufs sb;
+  WL_TRY(sb.b[0].alloc(eb * nc2 * nrhs));
+  WL_TRY(sb.b[1].alloc(eb * nf2 * nrhs));
+  WL_TRY(wl::to_internal((const zd *)e, sb.b[0].p, nc2, nrhs, pin, s));
+  WL_TRY(wl::to_internal((const zd *)x, sb.b[1].p, nf2, nrhs, pin, s));
+  WL_TRY(wl::prolong_op(a, level, prec, sb.b[0].p, sb.b[1].p, nrhs, s));
+  WL_TRY(wl::from_internal(sb.b[1].p, (zd *)x, nf2, nrhs, pin, s));
+  WL_CUDA(cudaStreamSynchronize(s));
+  return WL_OK;
+}
+
+extern "C" int amg_coarsest(wl_amg *a, const void *f, void *x, int nrhs) {
+  WL_TRY(check_amg(a, 0, nrhs, WL_FP64, "amg_coarsest"));
+  if (!f || !x) return WL_EINVAL;
+  cudaStream_t s = a->op->stream;
+  StepBufs sb;
+  WL_TRY(sb.b[0].alloc(sizeof(zd) * a->nc * nrhs));
+  WL_TRY(sb.b[1].alloc(sizeof(zd) * a->nc * nrhs));
+  WL_TRY(wl::to_internal((const zd *)f, sb.b[0].p, a->nc, nrhs, WL_FP64, s));
+  WL_TRY(wl::coarsest_apply(a, WL_FP64, sb.b[0].p, sb.b[1].p, nrhs, s));
+  WL_TRY(wl::from_internal(sb.b[1].p, (zd *)x, a->nc, nrhs, WL_FP64, s));
+  WL_CUDA(cudaStreamSynchronize(s));
+  return WL_OK;
+}
+
+extern "C" int amg_cycle(wl_amg *a, const void *f, void *x, int nrhs, int prec) {
+  WL_TRY(check_amg(a, 0, nrhs, prec, "amg_cycle"));
+  if (!f || !x) return WL_EINVAL;
+  WL_TRY(wl::ensure_workspace(a, nrhs, prec));
+  cudaStream_t s = a->op->stream;
+  int n2 = a->lev[0].n * 2;
+  int pin = prec == WL_FP64 ? WL_FP64 : WL_FP32;
+  WL_TRY(wl::to_internal((const zd *)f, a->lev[0].f.p, n2, nrhs, pin, s));
+  WL_TRY(wl::cycle_run(a, nrhs, prec, s));
+  WL_TRY(wl::from_internal(a->lev[0].x.p, (zd *)x, n2, nrhs, pin, s));
+  WL_CUDA(cudaStreamSynchronize(s));
+  return WL_OK;
+}

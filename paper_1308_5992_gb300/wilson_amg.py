@@ -1,0 +1,267 @@
+"""Thin Python binding of libwilson_amg.so (C ABI in include/wilson_amg.h).
+
+Argument marshalling only: every step runs in the CUDA library.  Arrays are
+torch tensors on the GPU (complex128, contiguous); the binding passes their
+device pointers and the current torch stream.  Importing this module fails
+loudly if the library cannot be loaded: there is no CPU path.
+"""
+import ctypes as C
+import os
+
+from . import _build
+
+WL_OK, WL_NOT_CONVERGED = 0, 1
+WL_EINVAL, WL_OOM, WL_ECUDA, WL_TIMEOUT, WL_NAN, WL_BAD_HIERARCHY = -1, -2, -3, -4, -5, -6
+WL_FP64, WL_FP32, WL_FP32_BF16 = 0, 1, 2
+WL_OP_D, WL_OP_DHAT = 0, 1
+WL_CYCLE_V, WL_CYCLE_W = 0, 1
+
+
+class amg_params(C.Structure):
+    _fields_ = [("levels", C.c_int), ("block", C.c_int * 8), ("k_r", C.c_int), ("k_e", C.c_int),
+                ("setup_mu", C.c_int * 2), ("nu_pre", C.c_int), ("nu_post", C.c_int),
+                ("omega", C.c_double), ("cycle", C.c_int), ("fgmres_m", C.c_int),
+                ("max_restarts", C.c_int), ("precision", C.c_int), ("seed", C.c_ulonglong),
+                ("gs_passes", C.c_int), ("zero_guess", C.c_int)]
+
+
+class wl_info(C.Structure):
+    _fields_ = [("status", C.c_int), ("restarts", C.c_int), ("iters", C.c_int),
+                ("true_relres", C.c_double)]
+
+    def as_dict(self):
+        return dict(status=self.status, restarts=self.restarts, iters=self.iters,
+                    true_relres=self.true_relres)
+
+
+class WilsonAMGError(RuntimeError):
+    def __init__(self, what, code):
+        super().__init__("%s failed (%d): %s" % (what, code, last_error()))
+        self.code = code
+
+
+_lib = None
+
+
+def library_path():
+    return _build.LIB
+
+
+def lib():
+    """Load (building first if the sources are newer) the CUDA library."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError("libwilson_amg.so is missing; the CUDA build did not produce it")
+        L = C.CDLL(path)
+        P, i, d = C.c_void_p, C.c_int, C.c_double
+        sig = {
+            "amg_params_default": (None, [C.POINTER(amg_params)]),
+            "wilson_create": (i, [P, i, d, P, C.POINTER(P)]),
+            "wl_destroy": (None, [P]),
+            "wl_apply": (i, [P, i, P, P, i, i]),
+            "wl_eo_reduce": (i, [P, P, P, i]),
+            "wl_eo_reconstruct": (i, [P, P, P, P, i]),
+            "amg_setup": (i, [P, C.POINTER(amg_params), C.POINTER(P)]),
+            "amg_solve": (i, [P, P, P, i, d, C.POINTER(wl_info)]),
+            "amg_export": (i, [P, C.c_char_p]),
+            "amg_import": (i, [P, C.c_char_p, C.POINTER(amg_params), C.POINTER(P)]),
+            "amg_destroy": (None, [P]),
+            "amg_levels": (i, [P, P]),
+            "amg_level_apply": (i, [P, i, P, P, i, i]),
+            "amg_kaczmarz": (i, [P, i, P, P, i, i, i]),
+            "amg_restrict": (i, [P, i, P, P, i, i]),
+            "amg_prolong": (i, [P, i, P, P, i, i]),
+            "amg_coarsest": (i, [P, P, P, i]),
+            "amg_cycle": (i, [P, P, P, i, i]),
+            "amg_fgmres": (i, [P, P, P, i, d, C.POINTER(wl_info)]),
+            "wl_last_error": (C.c_char_p, []),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def last_error():
+    return lib().wl_last_error().decode()
+
+
+def _ptr(t):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("expected a CUDA tensor")
+    if t.dtype != torch.complex128 or not t.is_contiguous():
+        raise TypeError("expected a contiguous complex128 tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream():
+    import torch
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _chk(rc, what, ok=(WL_OK,)):
+    if rc not in ok:
+        raise WilsonAMGError(what, rc)
+    return rc
+
+
+def amg_params_default(**kw):
+    p = amg_params()
+    lib().amg_params_default(C.byref(p))
+    for k, v in kw.items():
+        if k == "block":
+            for j, b in enumerate(v):
+                p.block[j] = b
+        elif k == "setup_mu":
+            p.setup_mu[0], p.setup_mu[1] = v
+        else:
+            setattr(p, k, v)
+    return p
+
+
+# --------------------------------------------------------------- handles
+class wl_op:
+    """Owns a wl_op* (Wilson operator for one gauge field)."""
+
+    def __init__(self, ptr, L, m):
+        self._p = ptr
+        self.L, self.m = L, m
+
+    @property
+    def handle(self):
+        return self._p
+
+    def close(self):
+        if self._p:
+            lib().wl_destroy(self._p)
+            self._p = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class wl_amg:
+    """Owns a wl_amg* (hierarchy); keeps its wl_op alive."""
+
+    def __init__(self, ptr, op):
+        self._p = ptr
+        self.op = op
+
+    @property
+    def handle(self):
+        return self._p
+
+    def close(self):
+        if self._p:
+            lib().amg_destroy(self._p)
+            self._p = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------- C ABI mirrors
+def wilson_create(gauge, L, m):
+    out = C.c_void_p()
+    _chk(lib().wilson_create(_ptr(gauge), L, m, _stream(), C.byref(out)), "wilson_create")
+    return wl_op(out, L, m)
+
+
+def wl_apply(op, which, x, y, nrhs, prec=WL_FP64):
+    return _chk(lib().wl_apply(op.handle, which, _ptr(x), _ptr(y), nrhs, prec), "wl_apply")
+
+
+def wl_eo_reduce(op, b, bhat, nrhs):
+    return _chk(lib().wl_eo_reduce(op.handle, _ptr(b), _ptr(bhat), nrhs), "wl_eo_reduce")
+
+
+def wl_eo_reconstruct(op, b, xe, psi, nrhs):
+    return _chk(lib().wl_eo_reconstruct(op.handle, _ptr(b), _ptr(xe), _ptr(psi), nrhs),
+                "wl_eo_reconstruct")
+
+
+def amg_setup(op, params=None):
+    p = params or amg_params_default()
+    out = C.c_void_p()
+    _chk(lib().amg_setup(op.handle, C.byref(p), C.byref(out)), "amg_setup")
+    return wl_amg(out, op)
+
+
+def amg_import(op, path, params=None):
+    out = C.c_void_p()
+    pp = C.byref(params) if params is not None else None
+    _chk(lib().amg_import(op.handle, os.fsencode(path), pp, C.byref(out)), "amg_import")
+    return wl_amg(out, op)
+
+
+def amg_export(amg, path):
+    return _chk(lib().amg_export(amg.handle, os.fsencode(path)), "amg_export")
+
+
+def amg_levels(amg):
+    buf = (C.c_int * 8)()
+    L = lib().amg_levels(amg.handle, C.cast(buf, C.c_void_p))
+    return [buf[i] for i in range(L)]
+
+
+def amg_solve(amg, b, x, nrhs, tol):
+    info = (wl_info * nrhs)()
+    rc = _chk(lib().amg_solve(amg.handle, _ptr(b), _ptr(x), nrhs, tol, info), "amg_solve",
+              ok=(WL_OK, WL_NOT_CONVERGED))
+    return rc, [i.as_dict() for i in info]
+
+
+def amg_fgmres(amg, bhat, x, nrhs, tol):
+    info = (wl_info * nrhs)()
+    rc = _chk(lib().amg_fgmres(amg.handle, _ptr(bhat), _ptr(x), nrhs, tol, info), "amg_fgmres",
+              ok=(WL_OK, WL_NOT_CONVERGED))
+    return rc, [i.as_dict() for i in info]
+
+
+def amg_level_apply(amg, level, x, y, nrhs, prec=WL_FP64):
+    return _chk(lib().amg_level_apply(amg.handle, level, _ptr(x), _ptr(y), nrhs, prec),
+                "amg_level_apply")
+
+
+def amg_kaczmarz(amg, level, x, r, nrhs, sweeps=1, prec=WL_FP64):
+    return _chk(lib().amg_kaczmarz(amg.handle, level, _ptr(x), _ptr(r), nrhs, sweeps, prec),
+                "amg_kaczmarz")
+
+
+def amg_restrict(amg, level, r, fc, nrhs, prec=WL_FP64):
+    return _chk(lib().amg_restrict(amg.handle, level, _ptr(r), _ptr(fc), nrhs, prec), "amg_restrict")
+
+
+def amg_prolong(amg, level, e, x, nrhs, prec=WL_FP64):
+    return _chk(lib().amg_prolong(amg.handle, level, _ptr(e), _ptr(x), nrhs, prec), "amg_prolong")
+
+
+def amg_coarsest(amg, f, x, nrhs):
+    return _chk(lib().amg_coarsest(amg.handle, _ptr(f), _ptr(x), nrhs), "amg_coarsest")
+
+
+def amg_cycle(amg, f, x, nrhs, prec=WL_FP64):
+    return _chk(lib().amg_cycle(amg.handle, _ptr(f), _ptr(x), nrhs, prec), "amg_cycle")
+
+
+def wl_last_error():
+    return last_error()
+
+
+def wl_destroy(op):
+    op.close()
+
+
+def amg_destroy(amg):
+    amg.close()

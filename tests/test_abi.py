@@ -1,0 +1,46 @@
+"""CPU checks of the C ABI: the library builds for sm_103a, loads, and
+exports every function that include/wilson_amg.h declares (no compute call
+is made without a GPU)."""
+import ctypes
+import os
+import re
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    txt = open(os.path.join(ROOT, "include", "wilson_amg.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?(?:int|void|char)\s*\**\s*(\w+)\s*\(", txt, flags=re.M)
+    return sorted(set(names))
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_1308_5992_gb300 import _build
+    path = _build.build()
+    lib = ctypes.CDLL(path)
+    names = declared_functions()
+    assert len(names) >= 20
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_names_match_abi():
+    from paper_1308_5992_gb300 import wilson_amg as W
+    for n in declared_functions():
+        assert hasattr(W, n), n
+    W.lib()
+
+
+def test_params_defaults_and_errors():
+    """Host-side argument checks need no device."""
+    from paper_1308_5992_gb300 import wilson_amg as W
+    p = W.amg_params_default()
+    assert (p.k_r, p.k_e, p.nu_pre, p.nu_post, p.fgmres_m) == (8, 8, 2, 2, 20)
+    assert (p.setup_mu[0], p.setup_mu[1], p.omega, p.precision) == (10, 5, 1.0, W.WL_FP64)
+    out = ctypes.c_void_p()
+    # L not a power of two -> WL_EINVAL before any device work
+    rc = W.lib().wilson_create(ctypes.c_void_p(8), 24, 0.1, None, ctypes.byref(out))
+    assert rc == W.WL_EINVAL and "power of two" in W.last_error()
+    rc = W.lib().wilson_create(None, 32, 0.1, None, ctypes.byref(out))
+    assert rc == W.WL_EINVAL

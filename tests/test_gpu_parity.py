@@ -1,0 +1,254 @@
+"""GPU-versus-oracle parity of every solve-phase step, called through the C
+ABI (binding paper_1308_5992_gb300.wilson_amg).  Tolerances: FP64 matvec
+1e-14 relative, FP32 1e-6; one FP64 Kaczmarz sweep 1e-13; one FP64 cycle
+on a shared (oracle-built) hierarchy 1e-12; final solutions 1e-10 relative
+error against the oracle."""
+import os
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover - collected only on GPU machines
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_1308_5992_gb300 import wilson_amg as W  # noqa: E402
+from wl_inputs import workload, rhs_batch, cgauss  # noqa: E402
+
+DEV = torch.device("cuda:0")
+
+
+def T(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.complex128)).to(DEV)
+
+
+def H(t):
+    return t.cpu().numpy()
+
+
+def rel(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+@pytest.fixture(scope="module")
+def ops():
+    cache = {}
+
+    def get(name):
+        if name not in cache:
+            w = workload(name)
+            cache[name] = (w, W.wilson_create(T(w["U"]), w["N"], w["m"]))
+        return cache[name]
+    return get
+
+
+@pytest.fixture(scope="module")
+def shared(O, ops, tmp_path_factory):
+    """GPU hierarchies imported from oracle-built hierarchy files."""
+    from oracle.hierfile import write_hierarchy
+    cache = {}
+
+    def get(name):
+        if name not in cache:
+            w, op = ops(name)
+            p = O.setup_params(w["blocks"], k_r=w["k"], k_e=w["k"], seed=w["seed"])
+            h = O.Hierarchy.setup(w["N"], w["U"], w["m"], p)
+            path = str(tmp_path_factory.mktemp("h") / ("%s.wlh" % name))
+            write_hierarchy(path, h)
+            amg = W.amg_import(op, path, W.amg_params_default(zero_guess=1))
+            cache[name] = (w, op, h, amg, path)
+        return cache[name]
+    return get
+
+
+# ------------------------------------------------------------- operators
+@pytest.mark.parametrize("name,nrhs", [("T16", 1), ("T32", 3), ("T64", 5), ("C2", 2)])
+def test_dhat_and_d_apply(O, ops, name, nrhs):
+    w, op = ops(name)
+    N, U, m = w["N"], w["U"], w["m"]
+    x = np.stack([cgauss(10 + r, 1, N * N) for r in range(nrhs)])
+    ref = np.stack([O.dhat_apply(N, U, m, x[r]) for r in range(nrhs)])
+    for prec, tol in ((W.WL_FP64, 1e-14), (W.WL_FP32, 1e-6)):
+        y = torch.zeros_like(T(x))
+        W.wl_apply(op, W.WL_OP_DHAT, T(x), y, nrhs, prec)
+        assert rel(H(y), ref) <= tol, (prec, rel(H(y), ref))
+    psi = np.stack([cgauss(20 + r, 1, 2 * N * N).reshape(N, N, 2) for r in range(nrhs)])
+    refD = np.stack([O.wilson_apply(N, U, m, psi[r].reshape(-1)).reshape(N, N, 2) for r in range(nrhs)])
+    for prec, tol in ((W.WL_FP64, 1e-14), (W.WL_FP32, 1e-6)):
+        y = torch.zeros_like(T(psi))
+        W.wl_apply(op, W.WL_OP_D, T(psi), y, nrhs, prec)
+        assert rel(H(y), refD) <= tol
+
+
+@pytest.mark.parametrize("name,nrhs", [("T32", 1), ("T64", 3)])
+def test_eo_reduce_reconstruct(O, ops, name, nrhs):
+    w, op = ops(name)
+    N, U, m = w["N"], w["U"], w["m"]
+    b = rhs_batch(N, nrhs, 7)
+    bh = torch.zeros((nrhs, N * N), dtype=torch.complex128, device=DEV)
+    W.wl_eo_reduce(op, T(b), bh, nrhs)
+    ref = np.stack([O.eo_reduce(N, U, m, b[r]) for r in range(nrhs)])
+    assert rel(H(bh), ref) <= 1e-14
+    xe = np.stack([cgauss(30 + r, 2, N * N) for r in range(nrhs)])
+    psi = torch.zeros_like(T(b))
+    W.wl_eo_reconstruct(op, T(b), T(xe), psi, nrhs)
+    refp = np.stack([O.eo_reconstruct(N, U, m, b[r], xe[r]) for r in range(nrhs)])
+    assert rel(H(psi), refp) <= 1e-14
+
+
+# ------------------------------------------------- per-level cycle steps
+@pytest.mark.parametrize("name", ["T64", "C1"])
+def test_level_apply(shared, name):
+    w, op, h, amg, _ = shared(name)
+    for l in range(h.L):
+        n = h.n(l)
+        x = np.stack([cgauss(40 + l, r, n) for r in range(2)])
+        ref = np.stack([h.apply(l, x[r]) for r in range(2)])
+        for prec, tol in ((W.WL_FP64, 1e-14), (W.WL_FP32, 1e-6)):
+            y = torch.zeros_like(T(x))
+            W.amg_level_apply(amg, l, T(x), y, 2, prec)
+            assert rel(H(y), ref) <= tol, (l, prec, rel(H(y), ref))
+
+
+@pytest.mark.parametrize("name", ["T64", "C1"])
+def test_kaczmarz_sweep(O, shared, name):
+    """One multicolour sweep: GPU (row/gamma5 form) vs oracle (true columns)."""
+    w, op, h, amg, _ = shared(name)
+    for l in range(h.L - 1):
+        n = h.n(l)
+        nrhs = 3
+        f = np.stack([cgauss(50 + l, r, n) for r in range(nrhs)])
+        x0 = 0.1 * np.stack([cgauss(60 + l, r, n) for r in range(nrhs)])
+        r0 = np.stack([f[r] - h.apply(l, x0[r]) for r in range(nrhs)])
+        ref = [h.kaczmarz(l, x0[r], r0[r], order=O.ORDER_COLOUR, sweeps=1) for r in range(nrhs)]
+        xr, rr = np.stack([a for a, _ in ref]), np.stack([b for _, b in ref])
+        for prec, tol in ((W.WL_FP64, 1e-13), (W.WL_FP32, 1e-5)):
+            xg, rg = T(x0), T(r0)
+            W.amg_kaczmarz(amg, l, xg, rg, nrhs, 1, prec)
+            assert rel(H(xg), xr) <= tol, (l, prec, rel(H(xg), xr))
+            assert rel(H(rg), rr) <= tol, (l, prec, rel(H(rg), rr))
+
+
+@pytest.mark.parametrize("name", ["T64", "C1"])
+def test_transfers_and_coarsest(shared, name):
+    w, op, h, amg, _ = shared(name)
+    for l in range(h.L - 1):
+        nf, nc = h.n(l), h.n(l + 1)
+        r = np.stack([cgauss(70 + l, q, nf) for q in range(2)])
+        ref = np.stack([h.restrict(l, r[q]) for q in range(2)])
+        fc = torch.zeros((2, nc), dtype=torch.complex128, device=DEV)
+        W.amg_restrict(amg, l, T(r), fc, 2, W.WL_FP64)
+        assert rel(H(fc), ref) <= 1e-14
+        e = np.stack([cgauss(80 + l, q, nc) for q in range(2)])
+        x = np.stack([cgauss(90 + l, q, nf) for q in range(2)])
+        refp = np.stack([h.prolong(l, e[q], x[q]) for q in range(2)])
+        xg = T(x)
+        W.amg_prolong(amg, l, T(e), xg, 2, W.WL_FP64)
+        assert rel(H(xg), refp) <= 1e-14
+    nc = h.n(h.L - 1)
+    f = np.stack([cgauss(99, q, nc) for q in range(3)])
+    ref = np.stack([h.coarsest_solve(f[q]) for q in range(3)])
+    xg = torch.zeros_like(T(f))
+    W.amg_coarsest(amg, T(f), xg, 3)
+    assert rel(H(xg), ref) <= 1e-11
+
+
+@pytest.mark.parametrize("name", ["T64", "C1", "C2"])
+def test_cycle(O, shared, name):
+    """One V(2,2) cycle on the shared hierarchy, FP64 1e-12 (FP32 1e-5)."""
+    w, op, h, amg, _ = shared(name)
+    n = h.n(0)
+    f = np.stack([cgauss(123, q, n) for q in range(2)])
+    ref = np.stack([h.cycle(f[q], nu1=2, nu2=2, gamma=1) for q in range(2)])
+    for prec, tol in ((W.WL_FP64, 1e-12), (W.WL_FP32, 1e-5)):
+        xg = torch.zeros_like(T(f))
+        W.amg_cycle(amg, T(f), xg, 2, prec)
+        assert rel(H(xg), ref) <= tol, (prec, rel(H(xg), ref))
+
+
+# ---------------------------------------------------------- full solves
+@pytest.mark.parametrize("name", ["T64", "C1", "C2"])
+def test_fgmres_and_solve_match_oracle(shared, name):
+    w, op, h, amg, _ = shared(name)
+    N = w["N"]
+    b = rhs_batch(N, 2, 11)
+    psi = torch.zeros_like(T(b))
+    rc, info = W.amg_solve(amg, T(b), psi, 2, 1e-13)
+    assert rc == W.WL_OK, info
+    for q in range(2):
+        ref, oi = h.solve(b[q], tol=1e-13)
+        err = np.linalg.norm(H(psi[q]) - ref) / np.linalg.norm(ref)
+        assert err <= 1e-10, (q, err)
+        assert abs(info[q]["iters"] - oi["iters"]) <= 2, (info[q], oi)
+
+
+@pytest.mark.parametrize("prec", [W.WL_FP32, W.WL_FP32_BF16])
+def test_mixed_precision_solve(O, ops, shared, prec):
+    """FP32 (or BF16-stored) cycle inside FP64 FGMRES with iterative
+    refinement reaches the FP64 accuracy."""
+    w, op, h, _, path = shared("C2")
+    amg = W.amg_import(op, path, W.amg_params_default(zero_guess=1, precision=prec))
+    b = rhs_batch(w["N"], 1, 12)
+    psi = torch.zeros_like(T(b))
+    rc, info = W.amg_solve(amg, T(b), psi, 1, 1e-12)
+    assert rc == W.WL_OK and info[0]["true_relres"] <= 1e-12
+    ref, _ = h.solve(b[0], tol=1e-13)
+    assert np.linalg.norm(H(psi[0]) - ref) / np.linalg.norm(ref) <= 1e-9
+
+
+def test_batch_equals_alone(shared):
+    """Each right-hand side gives the same result alone and in a batch."""
+    w, op, h, amg, _ = shared("T64")
+    N = w["N"]
+    b = rhs_batch(N, 7, 13)
+    psi = torch.zeros_like(T(b))
+    rc, info = W.amg_solve(amg, T(b), psi, 7, 1e-12)
+    assert rc == W.WL_OK
+    for q in (0, 3, 6):
+        one = torch.zeros_like(T(b[q:q + 1]))
+        W.amg_solve(amg, T(b[q:q + 1]), one, 1, 1e-12)
+        assert np.linalg.norm(H(one[0]) - H(psi[q])) / np.linalg.norm(H(one[0])) <= 1e-10
+
+
+def test_gpu_setup_quality(O, ops):
+    """The GPU bootstrap setup gives a preconditioner of the same quality as
+    the oracle's (iterations within a band) and solutions to 1e-10."""
+    w, op = ops("T64")
+    p = W.amg_params_default(k_r=w["k"], k_e=w["k"], seed=w["seed"], zero_guess=1)
+    for l, b in enumerate(w["blocks"]):
+        p.block[l] = b
+    p.levels = len(w["blocks"]) + 1
+    amg = W.amg_setup(op, p)
+    b = rhs_batch(w["N"], 1, 14)
+    psi = torch.zeros_like(T(b))
+    rc, info = W.amg_solve(amg, T(b), psi, 1, 1e-12)
+    assert rc == W.WL_OK
+    ho = O.Hierarchy.setup(w["N"], w["U"], w["m"],
+                           O.setup_params(w["blocks"], k_r=w["k"], k_e=w["k"], seed=w["seed"]))
+    ref, oi = ho.solve(b[0], tol=1e-13)
+    assert np.linalg.norm(H(psi[0]) - ref) / np.linalg.norm(ref) <= 1e-9
+    assert info[0]["iters"] <= 2 * oi["iters"] + 5, (info, oi)
+
+
+def test_hierarchy_roundtrip_and_errors(shared, ops, tmp_path):
+    w, op, h, amg, path = shared("T64")
+    out = str(tmp_path / "x.wlh")
+    W.amg_export(amg, out)
+    amg2 = W.amg_import(op, out)
+    assert W.amg_levels(amg2) == h.Nl
+    data = bytearray(open(out, "rb").read())
+    data[100] ^= 1
+    bad = str(tmp_path / "bad.wlh")
+    open(bad, "wb").write(bytes(data))
+    with pytest.raises(W.WilsonAMGError) as e:
+        W.amg_import(op, bad)
+    assert e.value.code == W.WL_BAD_HIERARCHY
+    w2, op2 = ops("C1")
+    with pytest.raises(W.WilsonAMGError) as e:
+        W.amg_import(op2, out)  # another operator
+    assert e.value.code == W.WL_BAD_HIERARCHY
+    with pytest.raises(W.WilsonAMGError) as e:
+        W.amg_kaczmarz(amg, len(h.Nl) - 1, T(np.zeros(1)), T(np.zeros(1)), 1)
+    assert e.value.code == W.WL_EINVAL

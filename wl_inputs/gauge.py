@@ -25,45 +25,43 @@ def unit_gauge(N: int) -> np.ndarray:
 def metropolis_u1(N: int, beta: float, sweeps: int, seed: int, delta: float = 1.0) -> np.ndarray:
     if N % 2:
         raise ValueError("N must be even")
-    th = np.zeros((2, N, N), dtype=np.float64)
-    nlinks = N * N // 2
-    idx = np.arange(nlinks, dtype=np.uint64)
-    sel = [np.zeros((N, N), dtype=bool) for _ in range(4)]
-    sel[0][0::2, :] = True   # x-links, even y
-    sel[1][1::2, :] = True   # x-links, odd y
-    sel[2][:, 0::2] = True   # y-links, even x
-    sel[3][:, 1::2] = True   # y-links, odd x
+    tx = np.zeros((N, N), dtype=np.float64)   # theta_x[y, x]
+    ty = np.zeros((N, N), dtype=np.float64)   # theta_y[y, x]
+    idx = np.arange(N * N // 2, dtype=np.uint64)
+    two_pi = 2 * np.pi
+
+    def accept(t, b1, b2, sign, sw, cls):
+        base = 8 * (4 * sw + cls) + 1024
+        dlt = (delta * (2.0 * uniform01(seed, base + 0, idx) - 1.0)).reshape(t.shape)
+        acc = uniform01(seed, base + 1, idx).reshape(t.shape)
+        tn = t + dlt
+        ds = beta * (np.cos(sign * tn + b1) + np.cos(-sign * tn + b2)
+                     - np.cos(sign * t + b1) - np.cos(-sign * t + b2))
+        ok = acc < np.exp(np.minimum(ds, 0.0))
+        return np.remainder(np.where(ok, tn, t) + np.pi, two_pi) - np.pi
+
     for sw in range(sweeps):
-        for cls in range(4):
-            base = 8 * (4 * sw + cls) + 1024
-            dlt = delta * (2.0 * uniform01(seed, base + 0, idx) - 1.0)
-            acc = uniform01(seed, base + 1, idx)
-            tx, ty = th[0], th[1]
-            if cls < 2:
-                # P(x,y) = tx(x,y) + ty(x+1,y) - tx(x,y+1) - ty(x,y)
-                a1 = np.roll(ty, -1, axis=1) - np.roll(tx, -1, axis=0) - ty
-                # P(x,y-1) = tx(x,y-1) + ty(x+1,y-1) - tx(x,y) - ty(x,y-1)
-                a2 = np.roll(tx, 1, axis=0) + np.roll(np.roll(ty, -1, axis=1), 1, axis=0) - np.roll(ty, 1, axis=0)
-                t = tx[sel[cls]]
-                b1, b2 = a1[sel[cls]], a2[sel[cls]]
-                tn = t + dlt
-                ds = beta * (np.cos(tn + b1) + np.cos(-tn + b2) - np.cos(t + b1) - np.cos(-t + b2))
-                ok = acc < np.exp(np.minimum(ds, 0.0))
-                t = np.where(ok, tn, t)
-                tx[sel[cls]] = np.remainder(t + np.pi, 2 * np.pi) - np.pi
-            else:
-                # P(x,y) = tx(x,y) + ty(x+1,y) - tx(x,y+1) - ty(x,y)
-                c1 = tx + np.roll(ty, -1, axis=1) - np.roll(tx, -1, axis=0)
-                # P(x-1,y) = tx(x-1,y) + ty(x,y) - tx(x-1,y+1) - ty(x-1,y)
-                c2 = np.roll(tx, 1, axis=1) - np.roll(np.roll(tx, 1, axis=1), -1, axis=0) - np.roll(ty, 1, axis=1)
-                t = ty[sel[cls]]
-                b1, b2 = c1[sel[cls]], c2[sel[cls]]
-                tn = t + dlt
-                ds = beta * (np.cos(-tn + b1) + np.cos(tn + b2) - np.cos(-t + b1) - np.cos(t + b2))
-                ok = acc < np.exp(np.minimum(ds, 0.0))
-                t = np.where(ok, tn, t)
-                ty[sel[cls]] = np.remainder(t + np.pi, 2 * np.pi) - np.pi
-    return np.exp(1j * th)
+        for p in (0, 1):   # x-links on rows y = p (mod 2)
+            Y = np.arange(p, N, 2)
+            Yp, Ym = (Y + 1) % N, (Y - 1) % N
+            tyY = ty[Y]
+            # P(x,y)   = tx(x,y) + ty(x+1,y) - tx(x,y+1) - ty(x,y)
+            b1 = np.roll(tyY, -1, axis=1) - tx[Yp] - tyY
+            # P(x,y-1) = tx(x,y-1) + ty(x+1,y-1) - tx(x,y) - ty(x,y-1)
+            tyM = ty[Ym]
+            b2 = tx[Ym] + np.roll(tyM, -1, axis=1) - tyM
+            tx[Y] = accept(tx[Y], b1, b2, 1.0, sw, p)
+        for p in (0, 1):   # y-links on columns x = p (mod 2)
+            X = np.arange(p, N, 2)
+            Xp, Xm = (X + 1) % N, (X - 1) % N
+            # P(x,y)   = tx(x,y) + ty(x+1,y) - tx(x,y+1) - ty(x,y)   (ty enters with -)
+            txX = tx[:, X]
+            b1 = txX + ty[:, Xp] - np.roll(txX, -1, axis=0)
+            # P(x-1,y) = tx(x-1,y) + ty(x,y) - tx(x-1,y+1) - ty(x-1,y)  (ty enters with +)
+            txM = tx[:, Xm]
+            b2 = txM - np.roll(txM, -1, axis=0) - ty[:, Xm]
+            ty[:, X] = accept(ty[:, X], b1, b2, -1.0, sw, 2 + p)
+    return np.exp(1j * np.stack([tx, ty]))
 
 
 def random_gauge_transform(U: np.ndarray, seed: int):

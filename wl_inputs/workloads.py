@@ -66,6 +66,27 @@ def _shifts():
     return {}
 
 
+def cached_gauge(N, beta, sweeps, seed):
+    """metropolis_u1 with an on-disk cache (directory $WL_GAUGE_CACHE, default
+    ~/.cache/wl_inputs); the file name carries every parameter."""
+    d = os.environ.get("WL_GAUGE_CACHE", os.path.join(os.path.expanduser("~"), ".cache", "wl_inputs"))
+    path = os.path.join(d, "u1_N%d_b%g_s%d_seed%d.npy" % (N, beta, sweeps, seed))
+    if os.path.exists(path):
+        try:
+            return np.load(path)
+        except Exception:
+            pass
+    U = metropolis_u1(N, beta, sweeps, seed)
+    try:
+        os.makedirs(d, exist_ok=True)
+        tmp = path + ".%d.tmp.npy" % os.getpid()
+        np.save(tmp, U)
+        os.replace(tmp, path)
+    except OSError:
+        pass
+    return U
+
+
 def workload(name: str, with_gauge: bool = True):
     """Return a dict with the workload parameters, its shift m (if computed)
     and, optionally, the gauge field U[2][N][N]."""
@@ -75,7 +96,7 @@ def workload(name: str, with_gauge: bool = True):
     sh = _shifts().get(name)
     w["m"] = None if sh is None else float(sh["m"])
     if with_gauge:
-        w["U"] = metropolis_u1(w["N"], w["beta"], w["sweeps"], w["seed"])
+        w["U"] = cached_gauge(w["N"], w["beta"], w["sweeps"], w["seed"])
     return w
 
 
