@@ -1,0 +1,369 @@
+#!/usr/bin/env python3
+"""Benchmark: Wilson-AMG solves/s at 1e-10 relative residual on one GB300
+(and on N GPUs as independent replicas).
+
+A step is one call of the solver's public entry point amg_solve on one batch
+of right-hand sides: odd-even reduction, FP64 FGMRES(20) preconditioned by
+the V(2,2) multicolour-Kaczmarz AMG cycle, reconstruction.  The hierarchy is
+set up once before the timed region (the setup is cached per gauge field);
+its time is reported separately.
+
+Default workload (C4): 512x512 lattice, beta = 10 U(1) links from 500
+seeded Metropolis sweeps, m at smallest |eigenvalue| 1e-3, 4 grids (4x4,
+4x4, 2x2 cells), k = 12 test vectors, 64 complex Gaussian right-hand sides
+per step, FP32 cycle inside FP64 FGMRES.  The plain FP64 single-RHS solve of
+the same lattice is timed beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+import argparse
+import faulthandler
+import json
+import multiprocessing as mp
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Wilson-AMG solves/s at 1e-10 rel err (mixed+batched vs plain FP64); p99 ms"
+TOL = 1e-10
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="C4")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------- oracle (CPU)
+def _oracle_solves(name, nsolves, out_q):
+    """Runs in a spawned process: the oracle's own setup (untimed), then
+    `nsolves` timed single-RHS solves of the workload."""
+    try:
+        import numpy as np
+        from oracle import oracle as O
+        from wl_inputs import workload, rhs_batch
+        w = workload(name)
+        p = O.setup_params(w["blocks"], k_r=w["k"], k_e=w["k"], seed=w["seed"])
+        t0 = time.time()
+        h = O.Hierarchy.setup(w["N"], w["U"], w["m"], p)
+        setup_s = time.time() - t0
+        times, iters, sols = [], [], []
+        for i in range(nsolves):
+            b = rhs_batch(w["N"], 1, 100, first=i)[0]
+            t0 = time.perf_counter()
+            psi, info = h.solve(b, tol=TOL)
+            times.append(time.perf_counter() - t0)
+            iters.append(info["iters"])
+            if i == 0:
+                sols.append(psi)
+        out_q.put(dict(ok=True, setup_s=setup_s, times=times, iters=iters, psi0=sols[0]))
+    except Exception as e:  # reported, never silently replaced
+        out_q.put(dict(ok=False, error=repr(e)))
+
+
+def start_oracle(name, nsolves):
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    p = ctx.Process(target=_oracle_solves, args=(name, nsolves, q), daemon=True)
+    p.start()
+    return p, q
+
+
+# ------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples (200 ms) taken while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# --------------------------------------------------------------- main arm
+def run_gb300(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+    from paper_1308_5992_gb300 import wilson_amg as W
+    from wl_inputs import workload, rhs_batch
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    w = workload(args.workload)
+    if w["m"] is None:
+        raise SystemExit("no shift for workload %s (run oracle/make_shifts.py)" % args.workload)
+    N, nrhs = w["N"], max(1, w["nrhs"])
+    prec = {"fp64": W.WL_FP64, "fp32": W.WL_FP32, "bf16": W.WL_FP32_BF16}[w["precision"]]
+
+    # CPU baseline leg: the oracle, started before the first GPU call
+    oracle_proc = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        oracle_proc = start_oracle(args.workload, 3)
+
+    op = W.wilson_create(torch.from_numpy(w["U"]).to(dev), N, w["m"])
+
+    def params(precision):
+        p = W.amg_params_default(k_r=w["k"], k_e=w["k"], seed=w["seed"], zero_guess=1,
+                                 precision=precision)
+        p.levels = len(w["blocks"]) + 1
+        for l, b in enumerate(w["blocks"]):
+            p.block[l] = b
+        return p
+
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    amg = W.amg_setup(op, params(prec))
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    hier = os.path.join("/tmp", "wl_bench_%d_%d.wlh" % (os.getpid(), rank))
+    W.amg_export(amg, hier)
+    amg64 = W.amg_import(op, hier, params(W.WL_FP64))  # same hierarchy, plain FP64 cycle
+    os.remove(hier)
+
+    b_host = torch.from_numpy(rhs_batch(N, nrhs, 100 + 1000 * rank)).pin_memory()
+    b = b_host.to(dev)
+    x = torch.zeros_like(b)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
+
+    def step(amg_, bb, xx, n):
+        rc, info = W.amg_solve(amg_, bb, xx, n, TOL)
+        if rc != W.WL_OK:
+            raise RuntimeError("solve did not converge: %s" % info)
+        return info
+
+    for _ in range(args.warmup):
+        step(amg, b, x, nrhs)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    launches0 = W.wl_launch_count()
+    times, infos = [], []
+    barrier()
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        infos.append(step(amg, b, x, nrhs))
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    barrier()
+    launches = W.wl_launch_count() - launches0
+    clk = clocks.stop()
+    total_ms = sum(times)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = nrhs * args.steps * world / (total_ms / 1e3)
+    iters = [i["iters"] for inf in infos for i in inf]
+    relres = max(i["true_relres"] for inf in infos for i in inf)
+
+    # e2e: host buffers, copies inside the timed region
+    x_host = torch.empty_like(b_host).pin_memory()
+    e2e_ms = []
+    for _ in range(max(1, args.steps)):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        bd = b_host.to(dev, non_blocking=True)
+        xd = torch.zeros_like(bd)
+        step(amg, bd, xd, nrhs)
+        x_host.copy_(xd, non_blocking=True)
+        e1.record()
+        torch.cuda.synchronize()
+        e2e_ms.append(e0.elapsed_time(e1))
+    e2e = {"value": nrhs * len(e2e_ms) / (sum(e2e_ms) / 1e3), "unit": "solves/s",
+           "h2d_bytes_per_step": b_host.numel() * 16, "d2h_bytes_per_step": x_host.numel() * 16}
+
+    # plain FP64 single-RHS solve of the same lattice (the method's baseline)
+    b1, x1 = b[:1].contiguous(), torch.zeros_like(b[:1])
+    for _ in range(2):
+        step(amg64, b1, x1, 1)
+    p64 = []
+    for _ in range(3):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        inf64 = step(amg64, b1, x1, 1)
+        e1.record()
+        torch.cuda.synchronize()
+        p64.append(e0.elapsed_time(e1))
+
+    # roofline of the dominant kernel: the fine-level Kaczmarz colour pass
+    n0 = N * N // 2
+    eb = 16 if prec == W.WL_FP64 else 8          # bytes of one complex value of the cycle
+    sb = 16 if prec == W.WL_FP64 else (8 if prec == W.WL_FP32 else 4)  # stencil storage
+    kacz_ms = W.wl_time_kernel(amg, W.WL_K_KACZ, 0, nrhs, prec, 160)
+    # one colour pass: r read + written on 9/16 of the sites, x on 1/16, stencil row
+    # and denominators of 1/16 of the sites (per launch, each operand once)
+    kacz_bytes = n0 * nrhs * (9 / 16 * 2 * 2 * eb + 1 / 16 * 2 * 2 * eb) + n0 / 16 * (36 * sb + 2 * (eb // 2))
+    hbm, src = peaks()
+    achieved = kacz_bytes / (kacz_ms * 1e-3) / 1e9
+    roof = {"kernel": "k_kacz (fine level, one colour)", "bound": "hbm", "achieved": round(achieved, 1),
+            "peak": hbm, "peak_source": src, "unit": "GB/s", "frac": round(achieved / hbm, 4),
+            "traffic": None, "avg_launch_ms": round(kacz_ms, 5), "algorithmic_bytes": int(kacz_bytes)}
+
+    out = {
+        "metric": METRIC, "value": round(value, 3), "unit": "solves/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 cycle + f64 Krylov" if prec != W.WL_FP64 else "f64",
+        "data": "synthetic (seeded U(1) Metropolis gauge, complex Gaussian right-hand sides)",
+        "config": {"workload": "%s: %dx%d lattice, beta=%g, %d Metropolis sweeps, m=%.6f (smallest |eig| %g), "
+                               "%d grids, blocks %s, k=%d, %d RHS/step, V(2,2) Kaczmarz, FGMRES(20), tol %g"
+                               % (args.workload, N, N, w["beta"], w["sweeps"], w["m"], w["target"],
+                                  len(w["blocks"]) + 1, w["blocks"], w["k"], nrhs,
+                                  ["fp64", "fp32", "bf16"][prec], TOL),
+                   "nrhs": nrhs, "L": N, "precision": ["fp64", "fp32", "fp32_bf16"][prec],
+                   "l2": "flushed (256 MB write) between timed steps", "parallelism": "replicas"},
+        "iters_mean": round(sum(iters) / len(iters), 2), "iters_max": max(iters),
+        "true_relres_max": relres, "setup_s": round(setup_s, 3),
+        "step_ms_p50": sorted(times)[len(times) // 2], "step_ms_p99": sorted(times)[min(len(times) - 1,
+                                                                                         int(0.99 * len(times)))],
+        "plain_fp64_single_rhs": {"value": round(1e3 / (sorted(p64)[1]), 3), "unit": "solves/s",
+                                  "ms": sorted(p64)[1], "iters": inf64[0]["iters"]},
+        "e2e": e2e, "gpu_launches": int(launches), "roofline": roof, "clocks": clk,
+    }
+    if oracle_proc is not None:
+        proc, q = oracle_proc
+        res = q.get(timeout=1800)
+        proc.join(timeout=60)
+        if res.get("ok"):
+            ts = res["times"]
+            out["cpu_baseline"] = {"value": round(len(ts) / sum(ts), 4), "unit": "solves/s", "cores": 1,
+                                   "kind": "oracle",
+                                   "sample": "%d single-RHS solves of the same workload (the oracle's own setup, "
+                                             "untimed: %.1f s); iterations %s" % (len(ts), res["setup_s"],
+                                                                                 res["iters"])}
+            ref = res["psi0"]
+            one = torch.zeros_like(b[:1])
+            bref = torch.from_numpy(rhs_batch(N, 1, 100)).to(dev)
+            step(amg, bref, one, 1)
+            got = one[0].cpu().numpy()
+            out["rel_err_vs_oracle"] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+        else:
+            out["cpu_baseline"] = {"value": None, "error": res.get("error")}
+    return out
+
+
+def run_reference(args, rank, world):
+    """The oracle as it stands, on the host cores, same metric and workload."""
+    if rank != 0:
+        return None
+    from wl_inputs import workload
+    w = workload(args.workload, with_gauge=False)
+    proc, q = start_oracle(args.workload, args.warmup + args.steps)
+    res = q.get(timeout=3600)
+    proc.join(timeout=60)
+    if not res.get("ok"):
+        return {"impl": "reference", "unavailable": "oracle failed: %s" % res.get("error")}
+    ts = res["times"][args.warmup:]
+    value = len(ts) / sum(ts)
+    return {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "solves/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(1e3 * sum(ts) / len(ts), 2), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "L": w["N"], "nrhs_per_step": 1},
+            "cpu_baseline": {"value": round(value, 4), "unit": "solves/s", "cores": 1, "kind": "oracle",
+                             "sample": "one single-RHS solve per step (oracle setup untimed: %.1f s)"
+                                       % res["setup_s"]},
+            "e2e": {"value": round(value, 4), "unit": "solves/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    faulthandler.enable()
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+        if out is not None:
+            print(json.dumps(out))
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    out = run_gb300(args, rank, world, local_rank)
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

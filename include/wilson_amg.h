@@ -78,6 +78,9 @@ typedef struct {
   unsigned long long seed;/* seed of the setup's random test vectors                */
   int gs_passes;          /* Gram-Schmidt passes (1 = CGS, 2 = CGS with one reorth.) */
   int zero_guess;         /* 1: amg_solve ignores the contents of x                 */
+  int sweep_kernel;       /* Kaczmarz launch form: 0 = automatic, 1 = one launch
+                             per colour, 2 = one cooperative launch per level visit
+                             (same arithmetic and order; results agree to rounding) */
 } amg_params;
 
 typedef struct {
@@ -160,6 +163,28 @@ int amg_cycle(wl_amg *amg, const void *f, void *x, int nrhs, int prec);
 /* FGMRES on Dhat x = bhat (level-0 vectors, x = initial guess); info host
  * array [nrhs]. */
 int amg_fgmres(wl_amg *amg, const void *bhat, void *x, int nrhs, double tol, wl_info *info);
+
+/* ---- instrumentation (benchmarks, tests) ---- */
+enum {
+  WL_K_DHAT = 0,      /* matrix-free FP64 Dhat apply (two hop kernels)       */
+  WL_K_KACZ = 1,      /* one colour pass of the Kaczmarz sweep on `level`     */
+  WL_K_STENCIL = 2,   /* residual r = f - A_l x on `level`                    */
+  WL_K_RESTRICT = 3,  /* P^H from `level` to level + 1                        */
+  WL_K_PROLONG = 4,   /* P from level + 1 to `level`                          */
+  WL_K_COARSEST = 5,  /* dense FP64 coarsest solve                            */
+  WL_K_GS_DOT = 6,    /* FP64 multi-dot of 11 Krylov vectors (Gram-Schmidt)   */
+  WL_K_GS_AXPY = 7    /* FP64 multi-axpy of 11 Krylov vectors                 */
+};
+/* Average duration (host output, milliseconds) of one launch of kernel
+ * family `kind` in the launch configuration the solver uses for `nrhs`
+ * right-hand sides and cycle precision `prec`, timed with CUDA events on
+ * the library's work stream over `reps` back-to-back launches on the
+ * hierarchy's own work buffers (their contents are not preserved).
+ * Errors: WL_EINVAL. */
+int wl_time_kernel(wl_amg *amg, int kind, int level, int nrhs, int prec, int reps, double *avg_ms);
+/* Number of kernels this library has launched in this process (a captured
+ * graph counts each of its kernel nodes at every replay). */
+long long wl_launch_count(void);
 
 /* Last error message of the calling thread ("" if none). */
 const char *wl_last_error(void);

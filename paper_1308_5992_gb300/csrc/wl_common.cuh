@@ -121,6 +121,9 @@ static inline Geo make_geo(int N) {
 
 // -------------------------------------------------------------- error state
 void wl_set_error(const char *fmt, ...);
+// kernel launch accounting (wl_launch_count)
+void wl_count_launches(long long n);
+extern "C" long long wl_launch_count(void);
 #define WL_CUDA(call)                                                        \
   do {                                                                       \
     cudaError_t _e = (call);                                                 \
@@ -193,6 +196,7 @@ struct wl_amg {
   // captured cycle graphs, one per (nrhs, precision)
   struct G {
     int nrhs, prec;
+    long long kernels;  // kernel nodes of the graph
     cudaGraphExec_t exec;
   };
   std::vector<G> graphs;
@@ -211,6 +215,7 @@ int stencil_apply(wl_amg *a, int l, int prec, const void *x, void *y, const void
                   cudaStream_t s);
 int kaczmarz_sweeps(wl_amg *a, int l, int prec, void *x, void *r, int nrhs, int sweeps,
                     cudaStream_t s);
+int kaczmarz_colour(wl_amg *a, int l, int prec, void *x, void *r, int nrhs, int c, cudaStream_t s);
 int restrict_op(wl_amg *a, int l, int prec, const void *r, void *fc, int nrhs, cudaStream_t s);
 int prolong_op(wl_amg *a, int l, int prec, const void *e, void *x, int nrhs, cudaStream_t s);
 int coarsest_apply(wl_amg *a, int prec, const void *f, void *x, int nrhs, cudaStream_t s);

@@ -68,7 +68,7 @@ int resolve_levels(int N, amg_params *p, int *Nl) {
     return WL_EINVAL;
   }
   if (p->fgmres_m < 1 || p->fgmres_m > 32 || p->max_restarts < 1 || p->nu_pre < 0 ||
-      p->nu_post < 0 || p->gs_passes < 1 || p->gs_passes > 2 ||
+      p->nu_post < 0 || p->gs_passes < 1 || p->gs_passes > 2 || p->sweep_kernel < 0 || p->sweep_kernel > 2 ||
       (p->precision != WL_FP64 && p->precision != WL_FP32 && p->precision != WL_FP32_BF16) ||
       (p->cycle != WL_CYCLE_V && p->cycle != WL_CYCLE_W)) {
     wl_set_error("invalid solve parameters");
@@ -266,6 +266,8 @@ int ensure_workspace(wl_amg *a, int nrhs, int prec) {
     WL_TRY(L.r.alloc(vb));
     WL_TRY(L.f.alloc(vb));
     WL_TRY(L.t.alloc(vb));
+    DBuf *bs[4] = {&L.x, &L.r, &L.f, &L.t};
+    for (auto *b : bs) WL_CUDA(cudaMemsetAsync(b->p, 0, vb, a->op->stream));
   }
   int m = a->prm.fgmres_m;
   size_t vb0 = sizeof(zd) * (size_t)a->lev[0].n * 2 * cap;
@@ -275,6 +277,9 @@ int ensure_workspace(wl_amg *a, int nrhs, int prec) {
   WL_TRY(a->bh.alloc(vb0));
   WL_TRY(a->xh.alloc(vb0));
   WL_TRY(a->rr.alloc(vb0));
+  WL_CUDA(cudaMemsetAsync(a->V.p, 0, vb0 * (m + 1), a->op->stream));
+  WL_CUDA(cudaMemsetAsync(a->Z.p, 0, vb0 * m, a->op->stream));
+  WL_CUDA(cudaMemsetAsync(a->w.p, 0, vb0, a->op->stream));
   WL_TRY(a->red.alloc(sizeof(zd) * 1024 * (m + 2) * (size_t)cap));
   WL_TRY(a->small.alloc(sizeof(zd) * (size_t)cap * 8 * (m + 2) * (m + 2)));
   if (a->h_small) cudaFreeHost(a->h_small);

@@ -69,7 +69,7 @@ static KS ks_layout(void *base, int m, int nrhs) {
 // Block layout: blockDim = R * G with R = nrhs (<= 256) and G a power of two;
 // thread t handles right-hand side t % R, so element e of a vector
 // ([n][2][nrhs] flattened) always belongs to rhs e % R.
-#define KCH 8  // dots per launch
+#define KCH 12  // dots per launch
 template <typename Tv>
 __global__ void k_mdot(const cx<Tv> *__restrict__ V, long vstride, int kc, const zd *__restrict__ w,
                        long E, int R, zd *__restrict__ part) {
@@ -99,14 +99,21 @@ __global__ void k_mdot(const cx<Tv> *__restrict__ V, long vstride, int kc, const
     for (int k = 0; k < kc; ++k) part[((long)blockIdx.x * kc + k) * R + t] = sm[k * nt + t];
 }
 
-// out[r][k0 + k] (= or +=) sum over blocks of part[b][k][r], fixed order
+// out[r][k0 + k] (= or +=) sum over blocks of part[b][k][r]: one warp per
+// (k, r), lanes stride the blocks, shuffle tree (fixed order: deterministic)
 __global__ void k_mdot_final(const zd *__restrict__ part, int nblk, int kc, int R, zd *out, int ostride,
                              int k0, int accumulate, zd *copy_to) {
-  int tid = blockIdx.x * blockDim.x + threadIdx.x;
-  if (tid >= kc * R) return;
-  int k = tid / R, r = tid % R;
+  int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (wid >= kc * R) return;
+  int k = wid / R, r = wid % R;
   zd s = mk(0.0, 0.0);
-  for (int b = 0; b < nblk; ++b) s = s + part[((long)b * kc + k) * R + r];
+  for (int b = lane; b < nblk; b += 32) s = s + part[((long)b * kc + k) * R + r];
+#pragma unroll
+  for (int off = 16; off; off >>= 1) {
+    s.re += __shfl_down_sync(0xffffffffu, s.re, off);
+    s.im += __shfl_down_sync(0xffffffffu, s.im, off);
+  }
+  if (lane) return;
   zd *o = out + (long)r * ostride + k0 + k;
   if (copy_to) copy_to[(long)r * ostride + k0 + k] = s;
   *o = accumulate ? (*o + s) : s;
@@ -260,7 +267,7 @@ static RedCfg red_cfg(long E, int R) {
   while (R * G * 2 <= 256) G *= 2;
   c.nt = R * G;
   long want = (E + c.nt - 1) / c.nt;
-  c.nblk = (int)std::max(1L, std::min(want, 1024L));
+  c.nblk = (int)std::max(1L, std::min(want, 608L));  // 4 blocks per SM on 152 SMs
   return c;
 }
 
@@ -272,9 +279,10 @@ static int mdots(wl_amg *a, const cx<Tv> *V, long vstride, int kc, const zd *w, 
   size_t sm = sizeof(zd) * KCH * c.nt;
   for (int k0 = 0; k0 < kc; k0 += KCH) {
     int kk = std::min(KCH, kc - k0);
+    wl_count_launches(2);
     k_mdot<Tv><<<c.nblk, c.nt, sm, s>>>(V + k0 * vstride, vstride, kk, w, E, R, a->red.as<zd>());
-    k_mdot_final<<<WL_GRID(kk * R, 128), 128, 0, s>>>(a->red.as<zd>(), c.nblk, kk, R, out, ostride, k0,
-                                                      accumulate, copy_to);
+    k_mdot_final<<<WL_GRID(kk * R * 32, 256), 256, 0, s>>>(a->red.as<zd>(), c.nblk, kk, R, out, ostride, k0,
+                                                           accumulate, copy_to);
   }
   WL_CUDA(cudaGetLastError());
   return WL_OK;
@@ -283,6 +291,7 @@ static int mdots(wl_amg *a, const cx<Tv> *V, long vstride, int kc, const zd *w, 
 static int norms2(wl_amg *a, const zd *w, long E, int R, zd *tmp, double *out, cudaStream_t s) {
   WL_TRY(mdots<double>(a, w, 0, 1, w, E, R, tmp, 1, 0, nullptr, s));
   k_re_of<<<WL_GRID(R, 128), 128, 0, s>>>(tmp, out, R);
+  wl_count_launches(1);
   WL_CUDA(cudaGetLastError());
   return WL_OK;
 }
@@ -318,6 +327,7 @@ int fgmres_run(wl_amg *a, const zd *bh, zd *xh, int nrhs, double tol, wl_info *i
     // true residual in FP64: rr = bhat - Dhat x
     WL_TRY(dhat_apply_dev(op, xh, 0, w, nrhs, s));
     k_sub<<<gE, 256, 0, s>>>(bh, w, rr, E);
+    wl_count_launches(1);
     WL_TRY(norms2(a, rr, E, nrhs, tmpc, k.nrm2, s));
     WL_CUDA(cudaMemcpyAsync(h_d, k.nrm2, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s));
     WL_CUDA(cudaStreamSynchronize(s));
@@ -336,27 +346,37 @@ int fgmres_run(wl_amg *a, const zd *bh, zd *xh, int nrhs, double tol, wl_info *i
     WL_CUDA(cudaMemcpyAsync(k.active, active.data(), sizeof(int) * nrhs, cudaMemcpyHostToDevice, s));
     k_cycle_start<<<WL_GRID(nrhs, 128), 128, 0, s>>>(k);
     k_scale_rhs<<<gE, 256, 0, s>>>(rr, V, k.inv, E, nrhs);
+    wl_count_launches(2);
     int jdone = 0;
     for (int j = 0; j < m; ++j) {
       zd *vj = V + j * vs;
       void *zj = Zb + (size_t)j * vs * zb_;
       // z_j = M(v_j) in the cycle precision
       if (pcyc == WL_FP64) WL_CUDA(cudaMemcpyAsync(a->lev[0].f.p, vj, sizeof(zd) * E, cudaMemcpyDeviceToDevice, s));
-      else k_cast<float, double><<<gE, 256, 0, s>>>(vj, a->lev[0].f.as<zf>(), E);
+      else {
+        k_cast<float, double><<<gE, 256, 0, s>>>(vj, a->lev[0].f.as<zf>(), E);
+        wl_count_launches(1);
+      }
       WL_TRY(cycle_run(a, nrhs, pcyc, s));
       WL_CUDA(cudaMemcpyAsync(zj, a->lev[0].x.p, zb_ * E, cudaMemcpyDeviceToDevice, s));
       // w = Dhat z_j (FP64)
       WL_TRY(dhat_apply_dev(op, zj, pcyc != WL_FP64, w, nrhs, s));
       // Gram-Schmidt against v_0 .. v_j
       k_zero_hcol<<<WL_GRID(nrhs, 128), 128, 0, s>>>(k);
+      wl_count_launches(1);
       for (int pass = 0; pass < a->prm.gs_passes; ++pass) {
         WL_TRY(mdots<double>(a, V, vs, j + 1, w, E, nrhs, k.hcol, m + 1, 1, k.hpass, s));
         k_maxpy<double><<<gE, 256, 0, s>>>(V, vs, j + 1, k.hpass, m + 1, -1.0, w, E, nrhs);
+        wl_count_launches(1);
       }
       WL_TRY(norms2(a, w, E, nrhs, tmpc, k.nrm2, s));
       WL_CUDA(cudaMemsetAsync(k.running, 0, sizeof(int) * 2, s));
       k_givens<<<WL_GRID(nrhs, 128), 128, 0, s>>>(k, j, tol);
-      if (j + 1 < m) k_scale_rhs<<<gE, 256, 0, s>>>(w, V + (j + 1) * vs, k.inv, E, nrhs);
+      wl_count_launches(1);
+      if (j + 1 < m) {
+        k_scale_rhs<<<gE, 256, 0, s>>>(w, V + (j + 1) * vs, k.inv, E, nrhs);
+        wl_count_launches(1);
+      }
       WL_CUDA(cudaGetLastError());
       int run[2];
       WL_CUDA(cudaMemcpyAsync(h_d + nrhs, k.running, sizeof(int) * 2, cudaMemcpyDeviceToHost, s));
@@ -370,6 +390,7 @@ int fgmres_run(wl_amg *a, const zd *bh, zd *xh, int nrhs, double tol, wl_info *i
       if (run[0] == 0) break;
     }
     k_trisolve<<<WL_GRID(nrhs, 128), 128, 0, s>>>(k);
+    wl_count_launches(2);
     if (pcyc == WL_FP64) k_maxpy<double><<<gE, 256, 0, s>>>(a->Z.as<zd>(), vs, jdone, k.y, m, 1.0, xh, E, nrhs);
     else k_maxpy<float><<<gE, 256, 0, s>>>(a->Z.as<zf>(), vs, jdone, k.y, m, 1.0, xh, E, nrhs);
     WL_CUDA(cudaGetLastError());
@@ -440,4 +461,58 @@ extern "C" int amg_solve(wl_amg *a, const void *b, void *x, int nrhs, double tol
   }
   WL_CUDA(cudaStreamSynchronize(s));
   return status;
+}
+
+// ------------------------------------------------------------ instrumentation
+extern "C" int wl_time_kernel(wl_amg *a, int kind, int level, int nrhs, int prec, int reps, double *avg_ms) {
+  if (!a || !avg_ms || nrhs < 1 || nrhs > MAX_BATCH || reps < 1 || level < 0 || level >= a->L ||
+      (prec != WL_FP64 && prec != WL_FP32 && prec != WL_FP32_BF16) || kind < WL_K_DHAT || kind > WL_K_GS_AXPY ||
+      ((kind == WL_K_KACZ || kind == WL_K_STENCIL || kind == WL_K_RESTRICT || kind == WL_K_PROLONG) &&
+       level == a->L - 1)) {
+    wl_set_error("wl_time_kernel: invalid argument");
+    return WL_EINVAL;
+  }
+  WL_TRY(wl::enter(a->op));
+  WL_TRY(wl::ensure_workspace(a, nrhs, prec));
+  cudaStream_t s = a->op->stream;
+  int m = a->prm.fgmres_m;
+  long E = (long)a->lev[0].n * 2 * nrhs;
+  int kc = std::min(11, m + 1);
+  KS k = ks_layout(a->small.p, m, nrhs);
+  Level &L = a->lev[level];
+  auto launch = [&](int rep) -> int {
+    switch (kind) {
+      case WL_K_DHAT: return wl::dhat_apply_dev(a->op, a->Z.p, prec != WL_FP64, a->w.as<zd>(), nrhs, s);
+      case WL_K_KACZ: return wl::kaczmarz_colour(a, level, prec, L.x.p, L.r.p, nrhs, rep & 15, s);
+      case WL_K_STENCIL: return wl::stencil_apply(a, level, prec, L.x.p, L.r.p, L.f.p, nrhs, s);
+      case WL_K_RESTRICT: return wl::restrict_op(a, level, prec, L.r.p, a->lev[level + 1].f.p, nrhs, s);
+      case WL_K_PROLONG: return wl::prolong_op(a, level, prec, a->lev[level + 1].x.p, L.x.p, nrhs, s);
+      case WL_K_COARSEST:
+        return wl::coarsest_apply(a, prec, a->lev[a->L - 1].f.p, a->lev[a->L - 1].x.p, nrhs, s);
+      case WL_K_GS_DOT:
+        return wl::mdots<double>(a, a->V.as<zd>(), E, kc, a->w.as<zd>(), E, nrhs, k.hcol, m + 1, 0, k.hpass, s);
+      default:
+        k_maxpy<double><<<WL_GRID(E, 256), 256, 0, s>>>(a->V.as<zd>(), E, kc, k.hpass, m + 1, -1.0, a->w.as<zd>(), E,
+                                                         nrhs);
+        wl_count_launches(1);
+        return WL_OK;
+    }
+  };
+  WL_TRY(launch(0));
+  cudaEvent_t e0, e1;
+  WL_CUDA(cudaEventCreate(&e0));
+  WL_CUDA(cudaEventCreate(&e1));
+  int rc = WL_OK;
+  if (cudaEventRecord(e0, s) != cudaSuccess) rc = WL_ECUDA;
+  for (int i = 0; i < reps && !rc; ++i) rc = launch(i + 1);
+  float ms = 0;
+  if (!rc && (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+              cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+    rc = WL_ECUDA;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  WL_CUDA(cudaGetLastError());
+  *avg_ms = (double)ms / reps;
+  return WL_OK;
 }

@@ -6,7 +6,13 @@
 // Vectors use the internal layout [n][2][nrhs] (site, spin, right-hand
 // side innermost) so that a warp covers consecutive right-hand sides of one
 // site and shares that site's stencil coefficients.
+#include <cooperative_groups.h>
+
+#include <algorithm>
+
 #include "wl_common.cuh"
+
+namespace cg = cooperative_groups;
 
 
 // ------------------------------------------------------------ stencil apply
@@ -42,25 +48,28 @@ __global__ void __launch_bounds__(256) k_stencil(Geo g, const S *__restrict__ A,
 
 // ---------------------------------------------------------------- Kaczmarz
 // One colour of the multicolour sweep.  Colour k = 4 (a mod 4) + (b mod 4);
-// thread q enumerates a = ka + 4 (q / (N/8)), b = kb + 4 (q mod N/8).
+// item q enumerates a = ka + 4 (q / (N/8)), b = kb + 4 (q mod N/8).
 // Column (h, t) of a gamma5-Hermitian A has the entries
 //   A_{(j,s),(h,t)} = g_s g_t conj(A[h][d][t][s]),  j = nb(h, d),
 // so s = <r, A e> / ||A e||^2 = g_t sum_{d,s} A[h][d][t][s] g_s r_{j,s} / den
 // reads only row h of the stencil; then x_(h,t) += omega s and
 // r_(j,s) -= omega s g_s g_t conj(A[h][d][t][s]).  Spin 0 precedes spin 1.
-template <typename T, typename S>
-__global__ void __launch_bounds__(128) k_kacz(Geo g, int colour, const S *__restrict__ A,
-                                              const T *__restrict__ den, cx<T> *__restrict__ x,
-                                              cx<T> *__restrict__ r, int nrhs, T omega) {
-  long tid = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  int n16 = g.nsites() >> 4;
-  if (tid >= (long)n16 * nrhs) return;
-  int q = (int)(tid / nrhs), rh = (int)(tid - (long)q * nrhs);
+__device__ __forceinline__ int kacz_site(const Geo &g, int colour, int q, int &px, int &py) {
   int nb8 = g.N >> 3;
   int a = (colour >> 2) + 4 * (q / nb8);
   int b = (colour & 3) + 4 * (q % nb8);
-  int px = (a + b) & (g.N - 1), py = (a - b) & (g.N - 1);
-  int h = g.idx(px, py);
+  px = (a + b) & (g.N - 1);
+  py = (a - b) & (g.N - 1);
+  return g.idx(px, py);
+}
+
+// one (site, right-hand side) item, one thread
+template <typename T, typename S>
+__device__ __forceinline__ void kacz_item(const Geo &g, int colour, int q, int rh, const S *__restrict__ A,
+                                          const T *__restrict__ den, cx<T> *__restrict__ x,
+                                          cx<T> *__restrict__ r, int nrhs, T omega) {
+  int px, py;
+  int h = kacz_site(g, colour, q, px, py);
   long jj[9];
   cx<T> rv[9][2];
 #pragma unroll
@@ -92,10 +101,8 @@ __global__ void __launch_bounds__(128) k_kacz(Geo g, int colour, const S *__rest
 #pragma unroll
       for (int s = 0; s < 2; ++s) {
         cx<T> a_ = ld<T>(Ah + d * 4 + t * 2 + s);
-        // rv -= sv * g_s g_t conj(a)
-        T gg = (s == t) ? (T)1 : (T)-1;
-        cx<T> c = cconj(a_);
-        cx<T> p = sv * c;
+        T gg = (s == t) ? (T)1 : (T)-1;  // g_s g_t
+        cx<T> p = sv * cconj(a_);
         rv[d][s] = mk<T>(rv[d][s].re - gg * p.re, rv[d][s].im - gg * p.im);
       }
     }
@@ -107,6 +114,89 @@ __global__ void __launch_bounds__(128) k_kacz(Geo g, int colour, const S *__rest
     r[jj[d]] = rv[d][0];
     r[jj[d] + nrhs] = rv[d][1];
   }
+}
+
+// one site with a single right-hand side, one warp: lane = 2 d + s holds
+// r_(nb(h,d), s); the inner products are warp sums (butterfly, all lanes)
+template <typename T, typename S>
+__device__ __forceinline__ void kacz_site_warp(const Geo &g, int colour, int q, int lane,
+                                               const S *__restrict__ A, const T *__restrict__ den,
+                                               cx<T> *__restrict__ x, cx<T> *__restrict__ r, T omega) {
+  int px, py;
+  int h = kacz_site(g, colour, q, px, py);
+  bool act = lane < 18;
+  int d = act ? lane >> 1 : 0, s = lane & 1;
+  long j = (long)g.nb(px, py, d) * 2 + s;
+  cx<T> rv = act ? r[j] : mk<T>(0, 0);
+  const S *Ah = A + (long)h * 36 + d * 4;
+  T gs = s ? (T)-1 : (T)1;
+#pragma unroll
+  for (int t = 0; t < 2; ++t) {
+    cx<T> a_ = act ? ld<T>(Ah + t * 2 + s) : mk<T>(0, 0);
+    cx<T> num = mk<T>(0, 0);
+    cfma(num, mk<T>(gs * a_.re, gs * a_.im), rv);
+#pragma unroll
+    for (int off = 16; off; off >>= 1) {
+      num.re += __shfl_xor_sync(0xffffffffu, num.re, off);
+      num.im += __shfl_xor_sync(0xffffffffu, num.im, off);
+    }
+    T sc = omega / den[2 * h + t];
+    if (t) sc = -sc;
+    cx<T> sv = sc * num;
+    T gg = (s == t) ? (T)1 : (T)-1;
+    cx<T> p = sv * cconj(a_);
+    rv = mk<T>(rv.re - gg * p.re, rv.im - gg * p.im);
+    if (lane == 0) {
+      long xo = (long)h * 2 + t;
+      x[xo] = x[xo] + sv;
+    }
+  }
+  if (act) r[j] = rv;
+}
+
+template <typename T, typename S>
+__global__ void __launch_bounds__(128) k_kacz(Geo g, int colour, const S *__restrict__ A,
+                                              const T *__restrict__ den, cx<T> *__restrict__ x,
+                                              cx<T> *__restrict__ r, int nrhs, T omega) {
+  long tid = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  int n16 = g.nsites() >> 4;
+  if (tid >= (long)n16 * nrhs) return;
+  int q = (int)(tid / nrhs), rh = (int)(tid - (long)q * nrhs);
+  kacz_item<T, S>(g, colour, q, rh, A, den, x, r, nrhs, omega);
+}
+
+template <typename T, typename S>
+__global__ void __launch_bounds__(128) k_kacz_warp(Geo g, int colour, const S *__restrict__ A,
+                                                   const T *__restrict__ den, cx<T> *__restrict__ x,
+                                                   cx<T> *__restrict__ r, T omega) {
+  int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (q >= (g.nsites() >> 4)) return;
+  kacz_site_warp<T, S>(g, colour, q, threadIdx.x & 31, A, den, x, r, omega);
+}
+
+// All colours of `sweeps` sweeps in one cooperative launch; a grid-wide
+// barrier separates the colours.  wpi = 1: one warp per site (nrhs = 1).
+template <typename T, typename S, int WPI>
+__global__ void __launch_bounds__(128) k_kacz_coop(Geo g, int sweeps, int wpi, const S *__restrict__ A,
+                                                   const T *__restrict__ den, cx<T> *__restrict__ x,
+                                                   cx<T> *__restrict__ r, int nrhs, T omega) {
+  cg::grid_group grid = cg::this_grid();
+  long n16 = g.nsites() >> 4;
+  long nthreads = (long)gridDim.x * blockDim.x;
+  long tid = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  for (int sw = 0; sw < sweeps; ++sw)
+    for (int c = 0; c < 16; ++c) {
+      if (WPI) {
+        for (long q = tid >> 5; q < n16; q += nthreads >> 5)
+          kacz_site_warp<T, S>(g, c, (int)q, threadIdx.x & 31, A, den, x, r, omega);
+      } else {
+        for (long it = tid; it < n16 * nrhs; it += nthreads) {
+          int q = (int)(it / nrhs), rh = (int)(it - (long)q * nrhs);
+          kacz_item<T, S>(g, c, q, rh, A, den, x, r, nrhs, omega);
+        }
+      }
+      grid.sync();
+    }
 }
 
 // ---------------------------------------------------------------- transfers
@@ -208,6 +298,7 @@ int stencil_apply(wl_amg *a, int l, int prec, const void *x, void *y, const void
   const LevelOps &o = ops_of(L, prec);
   long tot = (long)L.n * nrhs;
   unsigned grid = WL_GRID(tot, 256);
+  wl_count_launches(1);
   if (prec == WL_FP64)
     k_stencil<double, zd><<<grid, 256, 0, s>>>(L.geo, o.A.as<zd>(), (const zd *)x, (const zd *)f, (zd *)y, nrhs);
   else if (prec == WL_FP32)
@@ -218,21 +309,99 @@ int stencil_apply(wl_amg *a, int l, int prec, const void *x, void *y, const void
   return WL_OK;
 }
 
-int kaczmarz_sweeps(wl_amg *a, int l, int prec, void *x, void *r, int nrhs, int sweeps,
-                    cudaStream_t s) {
+int kaczmarz_colour(wl_amg *a, int l, int prec, void *x, void *r, int nrhs, int c, cudaStream_t s) {
   const Level &L = a->lev[l];
   const LevelOps &o = ops_of(L, prec);
-  long tot = (long)(L.n >> 4) * nrhs;
-  unsigned grid = WL_GRID(tot, 128);
+  long n16 = L.n >> 4;
+  wl_count_launches(1);
+  if (nrhs == 1) {
+    unsigned grid = WL_GRID(n16 * 32, 128);
+    if (prec == WL_FP64)
+      k_kacz_warp<double, zd><<<grid, 128, 0, s>>>(L.geo, c, o.A.as<zd>(), o.den.as<double>(), (zd *)x, (zd *)r, a->prm.omega);
+    else if (prec == WL_FP32)
+      k_kacz_warp<float, zf><<<grid, 128, 0, s>>>(L.geo, c, o.A.as<zf>(), o.den.as<float>(), (zf *)x, (zf *)r, (float)a->prm.omega);
+    else
+      k_kacz_warp<float, zb><<<grid, 128, 0, s>>>(L.geo, c, o.A.as<zb>(), o.den.as<float>(), (zf *)x, (zf *)r, (float)a->prm.omega);
+    return WL_OK;
+  }
+  unsigned grid = WL_GRID(n16 * nrhs, 128);
+  if (prec == WL_FP64)
+    k_kacz<double, zd><<<grid, 128, 0, s>>>(L.geo, c, o.A.as<zd>(), o.den.as<double>(), (zd *)x, (zd *)r, nrhs, a->prm.omega);
+  else if (prec == WL_FP32)
+    k_kacz<float, zf><<<grid, 128, 0, s>>>(L.geo, c, o.A.as<zf>(), o.den.as<float>(), (zf *)x, (zf *)r, nrhs, (float)a->prm.omega);
+  else
+    k_kacz<float, zb><<<grid, 128, 0, s>>>(L.geo, c, o.A.as<zb>(), o.den.as<float>(), (zf *)x, (zf *)r, nrhs, (float)a->prm.omega);
+  return WL_OK;
+}
+
+// resident blocks of 128 threads for the cooperative sweep (cached per
+// kernel instance)
+template <typename T, typename S>
+static int coop_blocks() {
+  static int cached = -1;
+  if (cached < 0) {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int p0 = 0, p1 = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p0, k_kacz_coop<T, S, 0>, 128, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p1, k_kacz_coop<T, S, 1>, 128, 0);
+    per = std::min(p0, p1);
+    cached = sms * per;
+  }
+  return cached;
+}
+
+template <typename T, typename S>
+static int launch_coop(const Level &L, const LevelOps &o, int sweeps, void *x, void *r, int nrhs, double omega,
+                       cudaStream_t s) {
+  long n16 = L.n >> 4;
+  int wpi = nrhs == 1;
+  long threads = wpi ? n16 * 32 : n16 * nrhs;
+  int maxb = coop_blocks<T, S>();
+  int blocks = (int)std::min<long>(WL_GRID(threads, 128), (long)maxb);
+  if (blocks < 1) return WL_EINVAL;
+  Geo g = L.geo;
+  const S *A = o.A.as<S>();
+  const T *den = o.den.as<T>();
+  cx<T> *xx = (cx<T> *)x, *rr = (cx<T> *)r;
+  T om = (T)omega;
+  void *args[] = {&g, &sweeps, &wpi, (void *)&A, (void *)&den, &xx, &rr, &nrhs, &om};
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(blocks);
+  cfg.blockDim = dim3(128);
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  const void *fn = wpi ? (const void *)k_kacz_coop<T, S, 1> : (const void *)k_kacz_coop<T, S, 0>;
+  WL_CUDA(cudaLaunchKernelExC(&cfg, fn, args));
+  return WL_OK;
+}
+
+// Per-colour work that fits one wave of resident blocks goes to the
+// cooperative sweep kernel (one launch for all colours); larger levels use
+// one launch per colour.
+int kaczmarz_sweeps(wl_amg *a, int l, int prec, void *x, void *r, int nrhs, int sweeps,
+                    cudaStream_t s) {
+  if (sweeps <= 0) return WL_OK;
+  const Level &L = a->lev[l];
+  long n16 = L.n >> 4;
+  long items = nrhs == 1 ? n16 * 32 : n16 * nrhs;
+  int maxb = prec == WL_FP64 ? coop_blocks<double, zd>() : prec == WL_FP32 ? coop_blocks<float, zf>()
+                                                                           : coop_blocks<float, zb>();
+  int mode = a->prm.sweep_kernel;
+  if (mode == 2 || (mode == 0 && items <= (long)maxb * 128)) {
+    const LevelOps &o = ops_of(L, prec);
+    wl_count_launches(1);
+    if (prec == WL_FP64) return launch_coop<double, zd>(L, o, sweeps, x, r, nrhs, a->prm.omega, s);
+    if (prec == WL_FP32) return launch_coop<float, zf>(L, o, sweeps, x, r, nrhs, a->prm.omega, s);
+    return launch_coop<float, zb>(L, o, sweeps, x, r, nrhs, a->prm.omega, s);
+  }
   for (int sw = 0; sw < sweeps; ++sw)
-    for (int c = 0; c < 16; ++c) {
-      if (prec == WL_FP64)
-        k_kacz<double, zd><<<grid, 128, 0, s>>>(L.geo, c, o.A.as<zd>(), o.den.as<double>(), (zd *)x, (zd *)r, nrhs, a->prm.omega);
-      else if (prec == WL_FP32)
-        k_kacz<float, zf><<<grid, 128, 0, s>>>(L.geo, c, o.A.as<zf>(), o.den.as<float>(), (zf *)x, (zf *)r, nrhs, (float)a->prm.omega);
-      else
-        k_kacz<float, zb><<<grid, 128, 0, s>>>(L.geo, c, o.A.as<zb>(), o.den.as<float>(), (zf *)x, (zf *)r, nrhs, (float)a->prm.omega);
-    }
+    for (int c = 0; c < 16; ++c) WL_TRY(kaczmarz_colour(a, l, prec, x, r, nrhs, c, s));
   WL_CUDA(cudaGetLastError());
   return WL_OK;
 }
@@ -243,6 +412,7 @@ int restrict_op(wl_amg *a, int l, int prec, const void *r, void *fc, int nrhs, c
   int lgB = ilog2(F.B);
   long tot = (long)Cl.n * nrhs;
   unsigned grid = WL_GRID(tot, 128);
+  wl_count_launches(1);
   if (prec == WL_FP64)
     k_restrict<double, zd><<<grid, 128, 0, s>>>(F.geo, Cl.geo, lgB, o.P.as<zd>(), (const zd *)r, (zd *)fc, nrhs);
   else if (prec == WL_FP32)
@@ -259,6 +429,7 @@ int prolong_op(wl_amg *a, int l, int prec, const void *e, void *x, int nrhs, cud
   int lgB = ilog2(F.B);
   long tot = (long)F.n * nrhs;
   unsigned grid = WL_GRID(tot, 256);
+  wl_count_launches(1);
   if (prec == WL_FP64)
     k_prolong<double, zd><<<grid, 256, 0, s>>>(F.geo, Cl.geo, lgB, o.P.as<zd>(), (const zd *)e, (zd *)x, nrhs);
   else if (prec == WL_FP32)
@@ -271,6 +442,7 @@ int prolong_op(wl_amg *a, int l, int prec, const void *e, void *x, int nrhs, cud
 
 int coarsest_apply(wl_amg *a, int prec, const void *f, void *x, int nrhs, cudaStream_t s) {
   dim3 grid(WL_GRID(a->nc, 8), nrhs);
+  wl_count_launches(1);
   if (prec == WL_FP64)
     k_coarsest<double><<<grid, 256, 0, s>>>(a->nc, a->Ainv.as<zd>(), (const zd *)f, (zd *)x, nrhs);
   else
@@ -301,6 +473,7 @@ static int cycle_level(wl_amg *a, int l, int nrhs, int prec, cudaStream_t s) {
     WL_TRY(cycle_level(a, l + 1, nrhs, prec, s));
     if (g > 0) {
       long ne = (long)C.n * 2 * nrhs;
+      wl_count_launches(1);
       if (prec == WL_FP64) k_axpy_inplace<double><<<WL_GRID(ne, 256), 256, 0, s>>>(C.x.as<zd>(), C.t.as<zd>(), ne);
       else k_axpy_inplace<float><<<WL_GRID(ne, 256), 256, 0, s>>>(C.x.as<zf>(), C.t.as<zf>(), ne);
       WL_CUDA(cudaGetLastError());
@@ -320,12 +493,16 @@ int cycle_run(wl_amg *a, int nrhs, int prec, cudaStream_t s) {
   for (auto &g : a->graphs)
     if (g.nrhs == nrhs && g.prec == prec) {
       WL_CUDA(cudaGraphLaunch(g.exec, s));
+      wl_count_launches(g.kernels);
       return WL_OK;
     }
   cudaGraph_t graph;
+  long long before = wl_launch_count();
   WL_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
   int rc = cycle_level(a, 0, nrhs, prec, s);
   cudaError_t e = cudaStreamEndCapture(s, &graph);
+  long long kernels = wl_launch_count() - before;  // captured, not yet run
+  wl_count_launches(-kernels);
   if (rc) {
     if (e == cudaSuccess) cudaGraphDestroy(graph);
     return rc;
@@ -334,11 +511,13 @@ int cycle_run(wl_amg *a, int nrhs, int prec, cudaStream_t s) {
   wl_amg::G gg;
   gg.nrhs = nrhs;
   gg.prec = prec;
+  gg.kernels = kernels;
   e = cudaGraphInstantiate(&gg.exec, graph, 0);
   cudaGraphDestroy(graph);
   WL_CUDA(e);
   a->graphs.push_back(gg);
   WL_CUDA(cudaGraphLaunch(gg.exec, s));
+  wl_count_launches(gg.kernels);
   return WL_OK;
 }
 

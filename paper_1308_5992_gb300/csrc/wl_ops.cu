@@ -20,6 +20,11 @@ void wl_set_error(const char *fmt, ...) {
 
 extern "C" const char *wl_last_error(void) { return g_err; }
 
+#include <atomic>
+static std::atomic<long long> g_launches(0);
+void wl_count_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+extern "C" long long wl_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
 int DBuf::alloc(size_t b) {
   if (b <= bytes && p) return WL_OK;
   release();
@@ -360,6 +365,7 @@ size_t prec_bytes(int prec) { return prec == WL_FP64 ? sizeof(zd) : sizeof(zf); 
 
 int to_internal(const zd *src, void *dst, int n2, int nrhs, int prec, cudaStream_t s) {
   long tot = (long)n2 * nrhs;
+  wl_count_launches(1);
   if (prec == WL_FP64) k_to_internal<double><<<WL_GRID(tot, 256), 256, 0, s>>>(src, (zd *)dst, n2, nrhs);
   else k_to_internal<float><<<WL_GRID(tot, 256), 256, 0, s>>>(src, (zf *)dst, n2, nrhs);
   WL_CUDA(cudaGetLastError());
@@ -368,6 +374,7 @@ int to_internal(const zd *src, void *dst, int n2, int nrhs, int prec, cudaStream
 
 int from_internal(const void *src, zd *dst, int n2, int nrhs, int prec, cudaStream_t s) {
   long tot = (long)n2 * nrhs;
+  wl_count_launches(1);
   if (prec == WL_FP64) k_from_internal<double><<<WL_GRID(tot, 256), 256, 0, s>>>((const zd *)src, dst, n2, nrhs);
   else k_from_internal<float><<<WL_GRID(tot, 256), 256, 0, s>>>((const zf *)src, dst, n2, nrhs);
   WL_CUDA(cudaGetLastError());
@@ -383,6 +390,7 @@ int dhat_apply_dev(wl_op *op, const void *x, int x_is_f32, zd *y, int nrhs, cuda
   zd *t = op->scratch.as<zd>();
   unsigned grid = WL_GRID(n * nrhs, 256);
   const zd *V = op->Uf64.as<zd>();
+  wl_count_launches(2);
   if (x_is_f32) {
     k_hop<double, float, double, double><<<grid, 256, 0, s>>>(g, V, 1, (const zf *)x, nullptr, t, nrhs);
     k_hop<double, double, float, double><<<grid, 256, 0, s>>>(g, V, 0, t, (const zf *)x, y, nrhs);
@@ -397,6 +405,7 @@ int dhat_apply_dev(wl_op *op, const void *x, int x_is_f32, zd *y, int nrhs, cuda
 int build_dhat_stencil(wl_op *op, zd *A, cudaStream_t s) {
   Geo g = op->geo;
   k_build_dhat<<<WL_GRID(g.nsites(), 128), 128, 0, s>>>(g, op->Uf64.as<zd>(), A);
+  wl_count_launches(1);
   WL_CUDA(cudaGetLastError());
   return symmetrise_stencil(g.N, A, s);
 }
@@ -404,6 +413,7 @@ int build_dhat_stencil(wl_op *op, zd *A, cudaStream_t s) {
 int symmetrise_stencil(int N, zd *A, cudaStream_t s) {
   Geo g = make_geo(N);
   k_symmetrise<<<WL_GRID(g.nsites() * 5, 128), 128, 0, s>>>(g, A);
+  wl_count_launches(1);
   WL_CUDA(cudaGetLastError());
   return WL_OK;
 }
@@ -411,6 +421,7 @@ int symmetrise_stencil(int N, zd *A, cudaStream_t s) {
 int compute_den64(int N, const zd *A, double *den, cudaStream_t s) {
   int n = N * N / 2;
   k_den64<<<WL_GRID(2 * n, 256), 256, 0, s>>>(n, A, den);
+  wl_count_launches(1);
   WL_CUDA(cudaGetLastError());
   return WL_OK;
 }
@@ -611,6 +622,7 @@ int eo_reduce_internal(wl_op *op, const zd *b, zd *bh, int nrhs, cudaStream_t s)
   Geo g = op->geo;
   long n = g.nsites();
   k_eo_reduce<<<WL_GRID(n * nrhs, 256), 256, 0, s>>>(g, op->c, op->Uf64.as<zd>(), b, bh, nrhs);
+  wl_count_launches(1);
   WL_CUDA(cudaGetLastError());
   return WL_OK;
 }
@@ -618,6 +630,7 @@ int eo_reconstruct_internal(wl_op *op, const zd *b, const zd *xe, zd *psi, int n
   Geo g = op->geo;
   long tot = (long)op->N * op->N * nrhs;
   k_eo_reconstruct<<<WL_GRID(tot, 256), 256, 0, s>>>(g, op->c, op->Uf64.as<zd>(), b, xe, psi, nrhs);
+  wl_count_launches(1);
   WL_CUDA(cudaGetLastError());
   return WL_OK;
 }
@@ -638,6 +651,7 @@ int take_even_internal(wl_op *op, const zd *psi, zd *xe, int nrhs, cudaStream_t 
   Geo g = op->geo;
   long n = g.nsites();
   k_take_even<<<WL_GRID(n * nrhs, 256), 256, 0, s>>>(g, psi, xe, nrhs);
+  wl_count_launches(1);
   WL_CUDA(cudaGetLastError());
   return WL_OK;
 }

@@ -5,8 +5,10 @@ torch tensors on the GPU (complex128, contiguous); the binding passes their
 device pointers and the current torch stream.  Importing this module fails
 loudly if the library cannot be loaded: there is no CPU path.
 """
+import atexit
 import ctypes as C
 import os
+import weakref
 
 from . import _build
 
@@ -15,6 +17,8 @@ WL_EINVAL, WL_OOM, WL_ECUDA, WL_TIMEOUT, WL_NAN, WL_BAD_HIERARCHY = -1, -2, -3, 
 WL_FP64, WL_FP32, WL_FP32_BF16 = 0, 1, 2
 WL_OP_D, WL_OP_DHAT = 0, 1
 WL_CYCLE_V, WL_CYCLE_W = 0, 1
+(WL_K_DHAT, WL_K_KACZ, WL_K_STENCIL, WL_K_RESTRICT, WL_K_PROLONG, WL_K_COARSEST, WL_K_GS_DOT,
+ WL_K_GS_AXPY) = range(8)
 
 
 class amg_params(C.Structure):
@@ -22,7 +26,7 @@ class amg_params(C.Structure):
                 ("setup_mu", C.c_int * 2), ("nu_pre", C.c_int), ("nu_post", C.c_int),
                 ("omega", C.c_double), ("cycle", C.c_int), ("fgmres_m", C.c_int),
                 ("max_restarts", C.c_int), ("precision", C.c_int), ("seed", C.c_ulonglong),
-                ("gs_passes", C.c_int), ("zero_guess", C.c_int)]
+                ("gs_passes", C.c_int), ("zero_guess", C.c_int), ("sweep_kernel", C.c_int)]
 
 
 class wl_info(C.Structure):
@@ -77,6 +81,8 @@ def lib():
             "amg_cycle": (i, [P, P, P, i, i]),
             "amg_fgmres": (i, [P, P, P, i, d, C.POINTER(wl_info)]),
             "wl_last_error": (C.c_char_p, []),
+            "wl_time_kernel": (i, [P, i, i, i, i, i, C.POINTER(d)]),
+            "wl_launch_count": (C.c_longlong, []),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -125,12 +131,31 @@ def amg_params_default(**kw):
 
 
 # --------------------------------------------------------------- handles
+# Live handles, destroyed in a fixed order (hierarchies before operators)
+# when the interpreter exits, while the library and the CUDA runtime are
+# still fully alive.
+_live_amg = weakref.WeakSet()
+_live_op = weakref.WeakSet()
+
+
+def _close_all():
+    for a in list(_live_amg):
+        a.close()
+    for o in list(_live_op):
+        o.close()
+
+
+atexit.register(_close_all)
+
+
 class wl_op:
     """Owns a wl_op* (Wilson operator for one gauge field)."""
 
     def __init__(self, ptr, L, m):
         self._p = ptr
         self.L, self.m = L, m
+        self._amgs = weakref.WeakSet()
+        _live_op.add(self)
 
     @property
     def handle(self):
@@ -138,6 +163,8 @@ class wl_op:
 
     def close(self):
         if self._p:
+            for a in list(self._amgs):   # a hierarchy never outlives its operator
+                a.close()
             lib().wl_destroy(self._p)
             self._p = None
 
@@ -154,6 +181,8 @@ class wl_amg:
     def __init__(self, ptr, op):
         self._p = ptr
         self.op = op
+        op._amgs.add(self)
+        _live_amg.add(self)
 
     @property
     def handle(self):
@@ -265,3 +294,13 @@ def wl_destroy(op):
 
 def amg_destroy(amg):
     amg.close()
+
+
+def wl_time_kernel(amg, kind, level, nrhs, prec, reps):
+    ms = C.c_double()
+    _chk(lib().wl_time_kernel(amg.handle, kind, level, nrhs, prec, reps, C.byref(ms)), "wl_time_kernel")
+    return ms.value
+
+
+def wl_launch_count():
+    return lib().wl_launch_count()

@@ -112,13 +112,16 @@ def test_level_apply(shared, name):
             assert rel(H(y), ref) <= tol, (l, prec, rel(H(y), ref))
 
 
-@pytest.mark.parametrize("name", ["T64", "C1"])
-def test_kaczmarz_sweep(O, shared, name):
-    """One multicolour sweep: GPU (row/gamma5 form) vs oracle (true columns)."""
-    w, op, h, amg, _ = shared(name)
+@pytest.mark.parametrize("name,nrhs,form", [("T64", 3, 1), ("T64", 3, 2), ("T64", 1, 1), ("T64", 1, 2),
+                                            ("C1", 3, 0), ("C2", 1, 1), ("C2", 5, 2)])
+def test_kaczmarz_sweep(O, shared, name, nrhs, form):
+    """One multicolour sweep: GPU (row/gamma5 form) vs oracle (true columns),
+    per-colour launches (form 1) and the cooperative single launch (form 2),
+    thread-per-item (nrhs > 1) and warp-per-site (nrhs = 1) kernels."""
+    w, op, h, _, path = shared(name)
+    amg = W.amg_import(op, path, W.amg_params_default(zero_guess=1, sweep_kernel=form))
     for l in range(h.L - 1):
         n = h.n(l)
-        nrhs = 3
         f = np.stack([cgauss(50 + l, r, n) for r in range(nrhs)])
         x0 = 0.1 * np.stack([cgauss(60 + l, r, n) for r in range(nrhs)])
         r0 = np.stack([f[r] - h.apply(l, x0[r]) for r in range(nrhs)])
@@ -166,6 +169,19 @@ def test_cycle(O, shared, name):
         xg = torch.zeros_like(T(f))
         W.amg_cycle(amg, T(f), xg, 2, prec)
         assert rel(H(xg), ref) <= tol, (prec, rel(H(xg), ref))
+
+
+@pytest.mark.parametrize("name", ["T64", "C2"])
+def test_w_cycle(O, shared, name):
+    """The W(4,4) cycle of Sec. 4 (gamma = 2 recursion), FP64 1e-12."""
+    w, op, h, _, path = shared(name)
+    amg = W.amg_import(op, path, W.amg_params_default(zero_guess=1, cycle=W.WL_CYCLE_W, nu_pre=4, nu_post=4))
+    n = h.n(0)
+    f = np.stack([cgauss(321, q, n) for q in range(2)])
+    ref = np.stack([h.cycle(f[q], nu1=4, nu2=4, gamma=2) for q in range(2)])
+    xg = torch.zeros_like(T(f))
+    W.amg_cycle(amg, T(f), xg, 2, W.WL_FP64)
+    assert rel(H(xg), ref) <= 1e-12, rel(H(xg), ref)
 
 
 # ---------------------------------------------------------- full solves
