@@ -41,6 +41,8 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="C4")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=8.0)
     return ap.parse_args()
 
 
@@ -166,7 +168,9 @@ def run_gb300(args, rank, world, local_rank):
 
     def params(precision):
         p = W.amg_params_default(k_r=w["k"], k_e=w["k"], seed=w["seed"], zero_guess=1,
-                                 precision=precision)
+                                 precision=precision, nu_pre=w["nu"], nu_post=w["nu"],
+                                 cycle=W.WL_CYCLE_W if w["cycle"] == "W" else W.WL_CYCLE_V,
+                                 fgmres_m=w["fgmres_m"], gs_passes=w["gs_passes"])
         p.levels = len(w["blocks"]) + 1
         for l, b in enumerate(w["blocks"]):
             p.block[l] = b
@@ -206,6 +210,7 @@ def run_gb300(args, rank, world, local_rank):
     launches0 = W.wl_launch_count()
     times, infos = [], []
     barrier()
+    torch.cuda.nvtx.range_push("timed")   # profilers select the timed steps by this range
     for _ in range(args.steps):
         flush.fill_(1.0)
         torch.cuda.synchronize()
@@ -215,6 +220,7 @@ def run_gb300(args, rank, world, local_rank):
         e1.record()
         torch.cuda.synchronize()
         times.append(e0.elapsed_time(e1))
+    torch.cuda.nvtx.range_pop()
     barrier()
     launches = W.wl_launch_count() - launches0
     clk = clocks.stop()
@@ -260,19 +266,33 @@ def run_gb300(args, rank, world, local_rank):
         torch.cuda.synchronize()
         p64.append(e0.elapsed_time(e1))
 
-    # roofline of the dominant kernel: the fine-level Kaczmarz colour pass
+    # Roofline.  The launch list of this workload (profiles/launches_c4_512x512_64rhs.md)
+    # puts the FP64 Gram-Schmidt multi-dot k_mdot first (about 30% of kernel time); it is
+    # FP64-ALU bound, so its peak is derived from the unit counts: 152 SMs x 2 FP64 FMA
+    # per clock x 2 flop x 2070 MHz = 1259 GFLOP/s.  One launch computes kc = 11 conjugate
+    # dot products of length E = 2 n0 nrhs complex numbers: 8 flop per complex term.
     n0 = N * N // 2
+    E = 2 * n0 * nrhs
+    kc = 11
+    dot_ms = W.wl_time_kernel(amg, W.WL_K_GS_DOT, 0, nrhs, prec, 20)
+    fp64_peak = 152 * 2 * 2 * 2070e6 / 1e9
+    dot_gflops = 8.0 * kc * E / (dot_ms * 1e-3) / 1e9
+    roof = {"kernel": "k_mdot<double> (Gram-Schmidt, 11 dots)", "bound": "alu", "achieved": round(dot_gflops, 1),
+            "peak": round(fp64_peak, 1), "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz",
+            "unit": "GFLOP/s", "frac": round(dot_gflops / fp64_peak, 4), "traffic": None,
+            "avg_launch_ms": round(dot_ms, 4), "algorithmic_flops": int(8 * kc * E)}
+    # second: the fine-level Kaczmarz colour pass (HBM bound).  One launch updates 1/16 of
+    # the sites: it reads and writes r on 9/16 of the sites and x on 1/16, and reads the
+    # stencil rows and denominators of 1/16 of the sites (each operand once)
     eb = 16 if prec == W.WL_FP64 else 8          # bytes of one complex value of the cycle
     sb = 16 if prec == W.WL_FP64 else (8 if prec == W.WL_FP32 else 4)  # stencil storage
     kacz_ms = W.wl_time_kernel(amg, W.WL_K_KACZ, 0, nrhs, prec, 160)
-    # one colour pass: r read + written on 9/16 of the sites, x on 1/16, stencil row
-    # and denominators of 1/16 of the sites (per launch, each operand once)
     kacz_bytes = n0 * nrhs * (9 / 16 * 2 * 2 * eb + 1 / 16 * 2 * 2 * eb) + n0 / 16 * (36 * sb + 2 * (eb // 2))
     hbm, src = peaks()
     achieved = kacz_bytes / (kacz_ms * 1e-3) / 1e9
-    roof = {"kernel": "k_kacz (fine level, one colour)", "bound": "hbm", "achieved": round(achieved, 1),
-            "peak": hbm, "peak_source": src, "unit": "GB/s", "frac": round(achieved / hbm, 4),
-            "traffic": None, "avg_launch_ms": round(kacz_ms, 5), "algorithmic_bytes": int(kacz_bytes)}
+    roof2 = {"kernel": "k_kacz<float> (fine level, one colour)", "bound": "hbm", "achieved": round(achieved, 1),
+             "peak": hbm, "peak_source": src, "unit": "GB/s", "frac": round(achieved / hbm, 4), "traffic": None,
+             "avg_launch_ms": round(kacz_ms, 5), "algorithmic_bytes": int(kacz_bytes)}
 
     out = {
         "metric": METRIC, "value": round(value, 3), "unit": "solves/s", "n_gpus": world,
@@ -281,10 +301,11 @@ def run_gb300(args, rank, world, local_rank):
         "dtype": "f32 cycle + f64 Krylov" if prec != W.WL_FP64 else "f64",
         "data": "synthetic (seeded U(1) Metropolis gauge, complex Gaussian right-hand sides)",
         "config": {"workload": "%s: %dx%d lattice, beta=%g, %d Metropolis sweeps, m=%.6f (smallest |eig| %g), "
-                               "%d grids, blocks %s, k=%d, %d RHS/step, V(2,2) Kaczmarz, FGMRES(20), tol %g"
+                               "%d grids, blocks %s, k=%d, %d RHS/step, %s(%d,%d) Kaczmarz cycle in %s, "
+                               "FGMRES(%d) with %d Gram-Schmidt pass(es) in FP64, tol %g"
                                % (args.workload, N, N, w["beta"], w["sweeps"], w["m"], w["target"],
-                                  len(w["blocks"]) + 1, w["blocks"], w["k"], nrhs,
-                                  ["fp64", "fp32", "bf16"][prec], TOL),
+                                  len(w["blocks"]) + 1, w["blocks"], w["k"], nrhs, w["cycle"], w["nu"], w["nu"],
+                                  ["fp64", "fp32", "fp32+bf16-storage"][prec], w["fgmres_m"], w["gs_passes"], TOL),
                    "nrhs": nrhs, "L": N, "precision": ["fp64", "fp32", "fp32_bf16"][prec],
                    "l2": "flushed (256 MB write) between timed steps", "parallelism": "replicas"},
         "iters_mean": round(sum(iters) / len(iters), 2), "iters_max": max(iters),
@@ -293,8 +314,10 @@ def run_gb300(args, rank, world, local_rank):
                                                                                          int(0.99 * len(times)))],
         "plain_fp64_single_rhs": {"value": round(1e3 / (sorted(p64)[1]), 3), "unit": "solves/s",
                                   "ms": sorted(p64)[1], "iters": inf64[0]["iters"]},
-        "e2e": e2e, "gpu_launches": int(launches), "roofline": roof, "clocks": clk,
+        "e2e": e2e, "gpu_launches": int(launches), "roofline": roof, "roofline_kaczmarz": roof2, "clocks": clk,
     }
+    if not args.no_serving:
+        out["serving"] = run_serving(args, rank, dev, W, torch)
     if oracle_proc is not None:
         proc, q = oracle_proc
         res = q.get(timeout=1800)
@@ -315,6 +338,79 @@ def run_gb300(args, rank, world, local_rank):
         else:
             out["cpu_baseline"] = {"value": None, "error": res.get("error")}
     return out
+
+
+def run_serving(args, rank, dev, W, torch):
+    """Continuous-batching serving over resident hierarchies of several lattice
+    sizes: a closed-loop burst measures capacity, then a seeded Poisson stream
+    of 1-32 RHS requests arrives at 70% of it for --serve-seconds."""
+    import numpy as np
+    from wl_inputs import workload, rhs_batch, uniform01
+    names = ["S00", "S01", "S02", "S03"]  # 64, 128, 256, 512 lattices, beta 6/10, targets 1e-2/1e-3
+    srv = W.srv_create(64 << 30, 32)
+    cfgs, pools = [], []
+    for nm in names:
+        w = workload(nm)
+        if w["m"] is None:
+            return {"unavailable": "no shift for %s" % nm}
+        op = W.wilson_create(torch.from_numpy(w["U"]).to(dev), w["N"], w["m"])
+        p = W.amg_params_default(k_r=w["k"], k_e=w["k"], seed=w["seed"], precision=W.WL_FP32, gs_passes=1,
+                                 nu_pre=4, nu_post=4)
+        p.levels = len(w["blocks"]) + 1
+        for l, b in enumerate(w["blocks"]):
+            p.block[l] = b
+        amg = W.amg_setup(op, p)
+        cfgs.append((nm, w, W.srv_add(srv, amg)))
+        pools.append(torch.from_numpy(rhs_batch(w["N"], 32, 7000 + len(pools))).to(dev))
+    W.srv_start(srv)
+    seed = 9000 + rank
+
+    def requests(n, stream):
+        u = uniform01(seed, stream, np.arange(3 * n, dtype=np.uint64)).reshape(n, 3)
+        return [(int(u[i, 0] * len(cfgs)), 1 + int(u[i, 1] * 32), u[i, 2]) for i in range(n)]
+
+    def submit(c, nr):
+        nm, w, cid = cfgs[c]
+        b = pools[c][:nr].contiguous()
+        x = torch.zeros_like(b)
+        torch.cuda.synchronize()
+        return W.srv_submit(srv, cid, b, x, nr, TOL), nr, x
+
+    # capacity: a closed-loop burst
+    burst = requests(16, 1)
+    t0 = time.perf_counter()
+    live = [submit(c, nr) for c, nr, _ in burst]
+    W.srv_drain(srv)
+    cap = sum(nr for _, nr, _ in live) / (time.perf_counter() - t0)
+    # open loop: Poisson arrivals at 70% of capacity (in right-hand sides per second)
+    mean_rhs = 16.5
+    rate = 0.7 * cap / mean_rhs
+    n = max(8, int(rate * args.serve_seconds))
+    reqs = requests(n, 2)
+    live, t = [], time.perf_counter()
+    tstart = t
+    for c, nr, u in reqs:
+        t += -np.log(max(u, 1e-12)) / rate
+        dt = t - time.perf_counter()
+        if dt > 0:
+            time.sleep(dt)
+        live.append(submit(c, nr))
+    W.srv_drain(srv)
+    wall = time.perf_counter() - tstart
+    lats, solved, worst = [], 0, 0.0
+    for rid, nr, x in live:
+        done, info, lat = W.srv_poll(srv, rid, nr)
+        lats.append(lat)
+        solved += nr
+        worst = max([worst] + [i["true_relres"] for i in info])
+    lats.sort()
+    srv.close()
+    return {"configs": ["%s:%dx%d" % (nm, w["N"], w["N"]) for nm, w, _ in cfgs], "requests": len(lats),
+            "rhs_per_request": "uniform 1..32", "arrival": "Poisson, seeded, %.2f req/s (70%% of %.1f solves/s "
+            "closed-loop capacity)" % (rate, cap), "p50_ms": round(lats[len(lats) // 2], 2),
+            "p99_ms": round(lats[min(len(lats) - 1, int(0.99 * len(lats)))], 2),
+            "solves_per_s": round(solved / wall, 2), "true_relres_max": worst,
+            "cycle": "V(4,4) FP32, FGMRES(20) FP64, 1 Gram-Schmidt pass", "slots_per_config": 32}
 
 
 def run_reference(args, rank, world):

@@ -164,6 +164,35 @@ int amg_cycle(wl_amg *amg, const void *f, void *x, int nrhs, int prec);
  * array [nrhs]. */
 int amg_fgmres(wl_amg *amg, const void *bhat, void *x, int nrhs, double tol, wl_info *info);
 
+/* ---- serving: continuous batching over resident hierarchies ----
+ * A server keeps hierarchies of several gauge fields (lattice sizes may
+ * differ) resident and answers solve requests.  srv_add reserves, for each
+ * hierarchy, a number of right-hand-side slots (max_slots_per_config, halved
+ * until the workspace fits the remaining device-memory budget; WL_OOM when
+ * not even one slot fits).  A worker thread per hierarchy admits queued
+ * right-hand sides into free slots at every FGMRES restart boundary, runs one
+ * restart cycle for the packed active slots on that hierarchy's work stream,
+ * and retires right-hand sides whose true FP64 relative residual reaches the
+ * request's tol, reconstructing their solution into the request's x.  So
+ * work of different hierarchies overlaps on the device and requests join
+ * while others run.  A right-hand side's arithmetic does not depend on its
+ * batch mates (all reductions are per right-hand side), so its result alone
+ * and in a mix agree up to the rounding of the reduction trees.
+ * Pointers b, x of srv_submit: device, full fields [nrhs][L][L][2] of the
+ * hierarchy's lattice, caller-owned, ready (synchronised) before the call and
+ * untouched by the caller until srv_poll reports the request done.  A
+ * hierarchy added to a server must not be used by other calls while the
+ * server runs.  srv_poll's latency is host wall time from srv_submit to the
+ * retirement of the request's last right-hand side. */
+typedef struct wl_server wl_server;
+int srv_create(unsigned long long hbm_budget_bytes, int max_slots_per_config, wl_server **out);
+int srv_add(wl_server *srv, wl_amg *amg, int *cfg_id);
+int srv_start(wl_server *srv);
+int srv_submit(wl_server *srv, int cfg, const void *b, void *x, int nrhs, double tol, long long *req_id);
+int srv_poll(wl_server *srv, long long req_id, int *done, wl_info *info /* host [nrhs] */, double *latency_ms);
+int srv_drain(wl_server *srv);
+void srv_destroy(wl_server *srv);
+
 /* ---- instrumentation (benchmarks, tests) ---- */
 enum {
   WL_K_DHAT = 0,      /* matrix-free FP64 Dhat apply (two hop kernels)       */

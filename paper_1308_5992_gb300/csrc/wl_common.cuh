@@ -155,6 +155,7 @@ struct wl_op {
   double m, c;
   cudaStream_t stream;  // the library's own non-blocking work stream
   cudaStream_t user;    // the caller's stream given to wilson_create
+  int device;           // CUDA device the operator lives on
   cudaEvent_t ev;       // orders the work stream after the caller's stream
   Geo geo;
   DBuf Uf64, Uf32;  // folded links V_mu(z) = sign * U_mu(z) / (2c), [2][N][N]

@@ -83,9 +83,13 @@ __global__ void k_mdot(const cx<Tv> *__restrict__ V, long vstride, int kc, const
   long stride = (long)gridDim.x * nt;
   for (long e = (long)blockIdx.x * nt + t; e < E; e += stride) {
     zd we = w[e];
+    zd v[KCH];
 #pragma unroll
     for (int k = 0; k < KCH; ++k)
-      if (k < kc) cfmac(acc[k], ccast<double>(V[k * vstride + e]), we);
+      if (k < kc) v[k] = ccast<double>(V[k * vstride + e]);
+#pragma unroll
+    for (int k = 0; k < KCH; ++k)
+      if (k < kc) cfmac(acc[k], v[k], we);
   }
 #pragma unroll
   for (int k = 0; k < KCH; ++k) sm[k * nt + t] = acc[k];
@@ -119,20 +123,33 @@ __global__ void k_mdot_final(const zd *__restrict__ part, int nblk, int kc, int 
   *o = accumulate ? (*o + s) : s;
 }
 
-// w -= sum_k V_k * coef[r][k]   (coef row stride cstride)
+// w += sign * sum_k V_k * coef[r][k]   (coef row stride cstride); the
+// k loop is unrolled by 4 with the four loads issued before the FMAs
 template <typename Tv>
-__global__ void k_maxpy(const cx<Tv> *__restrict__ V, long vstride, int kc, const zd *__restrict__ coef,
-                        int cstride, double sign, zd *__restrict__ w, long E, int R) {
+__global__ void __launch_bounds__(256) k_maxpy(const cx<Tv> *__restrict__ V, long vstride, int kc,
+                                               const zd *__restrict__ coef, int cstride, double sign,
+                                               zd *__restrict__ w, long E, int R) {
   long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= E) return;
   int r = (int)(e % R);
+  const zd *cr = coef + (long)r * cstride;
   zd acc = w[e];
-  for (int k = 0; k < kc; ++k) {
-    zd c = coef[(long)r * cstride + k];
-    zd v = ccast<double>(V[k * vstride + e]);
-    zd p = c * v;
-    acc.re = fma(sign, p.re, acc.re);
-    acc.im = fma(sign, p.im, acc.im);
+  int k = 0;
+  for (; k + 4 <= kc; k += 4) {
+    zd v[4], c[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) v[u] = ccast<double>(V[(k + u) * vstride + e]);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      c[u] = cr[k + u];
+      c[u] = mk(sign * c[u].re, sign * c[u].im);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) cfma(acc, c[u], v[u]);
+  }
+  for (; k < kc; ++k) {
+    zd c = cr[k];
+    cfma(acc, mk(sign * c.re, sign * c.im), ccast<double>(V[k * vstride + e]));
   }
   w[e] = acc;
 }
@@ -296,109 +313,154 @@ static int norms2(wl_amg *a, const zd *w, long E, int R, zd *tmp, double *out, c
   return WL_OK;
 }
 
-int fgmres_run(wl_amg *a, const zd *bh, zd *xh, int nrhs, double tol, wl_info *info) {
+// ||bh_r|| for every right-hand side (host output)
+int fg_norms(wl_amg *a, const zd *v, int nrhs, double *out) {
+  cudaStream_t s = a->op->stream;
+  long E = (long)a->lev[0].n * 2 * nrhs;
+  KS k = ks_layout(a->small.p, a->prm.fgmres_m, nrhs);
+  zd *tmpc = a->small.as<zd>() + (a->small.bytes / sizeof(zd)) - 2 * (size_t)nrhs - 8;
+  WL_TRY(norms2(a, v, E, nrhs, tmpc, k.nrm2, s));
+  double *h_d = (double *)a->h_small;
+  WL_CUDA(cudaMemcpyAsync(h_d, k.nrm2, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s));
+  WL_CUDA(cudaStreamSynchronize(s));
+  for (int r = 0; r < nrhs; ++r) out[r] = sqrt(h_d[r]);
+  return WL_OK;
+}
+
+// true FP64 residual a->rr = bh - Dhat x and its norms (host output); the
+// squared norms stay in the Krylov scalars for the next fg_cycle
+int fg_residual(wl_amg *a, const zd *bh, const zd *xh, int nrhs, double *rnorm) {
+  wl_op *op = a->op;
+  cudaStream_t s = op->stream;
+  long E = (long)a->lev[0].n * 2 * nrhs;
+  zd *w = a->w.as<zd>(), *rr = a->rr.as<zd>();
+  WL_TRY(dhat_apply_dev(op, xh, 0, w, nrhs, s));
+  k_sub<<<WL_GRID(E, 256), 256, 0, s>>>(bh, w, rr, E);
+  wl_count_launches(1);
+  KS k = ks_layout(a->small.p, a->prm.fgmres_m, nrhs);
+  zd *tmpc = a->small.as<zd>() + (a->small.bytes / sizeof(zd)) - 2 * (size_t)nrhs - 8;
+  WL_TRY(norms2(a, rr, E, nrhs, tmpc, k.nrm2, s));
+  double *h_d = (double *)a->h_small;
+  WL_CUDA(cudaMemcpyAsync(h_d, k.nrm2, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s));
+  WL_CUDA(cudaStreamSynchronize(s));
+  for (int r = 0; r < nrhs; ++r) {
+    rnorm[r] = sqrt(h_d[r]);
+    if (!std::isfinite(rnorm[r])) {
+      wl_set_error("non-finite residual for right-hand side %d", r);
+      return WL_NAN;
+    }
+  }
+  return WL_OK;
+}
+
+// One restart cycle of FGMRES(m) from the residual left by fg_residual, for
+// the right-hand sides with active[r] != 0 (the others are untouched):
+// Arnoldi with z_j = M(v_j), Gram-Schmidt, Givens; then x += Z y.
+// iters_out[r]: iterations this cycle ran for r (host).
+int fg_cycle(wl_amg *a, const zd *bnorm_h, zd *xh, int nrhs, double tol, const int *active, int *iters_out) {
   wl_op *op = a->op;
   cudaStream_t s = op->stream;
   int prec = a->prm.precision, m = a->prm.fgmres_m;
-  int pcyc = prec;  // cycle precision
-  long n2 = (long)a->lev[0].n * 2;
-  long E = n2 * nrhs;
-  long vs = E;  // stride between Krylov vectors
+  long E = (long)a->lev[0].n * 2 * nrhs;
+  long vs = E;
   KS k = ks_layout(a->small.p, m, nrhs);
   zd *V = a->V.as<zd>(), *w = a->w.as<zd>(), *rr = a->rr.as<zd>();
-  size_t zb_ = prec_bytes(pcyc);
+  size_t zb_ = prec_bytes(prec);
   char *Zb = (char *)a->Z.p;
   unsigned gE = WL_GRID(E, 256);
-  zd *tmpc = a->small.as<zd>() + (a->small.bytes / sizeof(zd)) - 2 * (size_t)nrhs - 8;
-
-  std::vector<int> active(nrhs, 1), iters(nrhs, 0), restarts(nrhs, 0);
-  std::vector<double> relres(nrhs, 0.0), bnorm(nrhs, 0.0);
   double *h_d = (double *)a->h_small;
-
-  // ||bhat||
-  WL_TRY(norms2(a, bh, E, nrhs, tmpc, k.nrm2, s));
-  WL_CUDA(cudaMemcpyAsync(h_d, k.nrm2, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s));
-  WL_CUDA(cudaStreamSynchronize(s));
-  for (int r = 0; r < nrhs; ++r) bnorm[r] = sqrt(h_d[r]) > 0 ? sqrt(h_d[r]) : 1.0;
-  WL_CUDA(cudaMemcpyAsync(k.bnorm, bnorm.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, s));
+  (void)bnorm_h;
+  WL_CUDA(cudaMemcpyAsync(k.active, active, sizeof(int) * nrhs, cudaMemcpyHostToDevice, s));
   WL_CUDA(cudaMemsetAsync(k.iters, 0, sizeof(int) * nrhs, s));
+  k_cycle_start<<<WL_GRID(nrhs, 128), 128, 0, s>>>(k);
+  k_scale_rhs<<<gE, 256, 0, s>>>(rr, V, k.inv, E, nrhs);
+  wl_count_launches(2);
+  int jdone = 0;
+  for (int j = 0; j < m; ++j) {
+    zd *vj = V + j * vs;
+    void *zj = Zb + (size_t)j * vs * zb_;
+    // z_j = M(v_j) in the cycle precision
+    if (prec == WL_FP64) WL_CUDA(cudaMemcpyAsync(a->lev[0].f.p, vj, sizeof(zd) * E, cudaMemcpyDeviceToDevice, s));
+    else {
+      k_cast<float, double><<<gE, 256, 0, s>>>(vj, a->lev[0].f.as<zf>(), E);
+      wl_count_launches(1);
+    }
+    WL_TRY(cycle_run(a, nrhs, prec, s));
+    WL_CUDA(cudaMemcpyAsync(zj, a->lev[0].x.p, zb_ * E, cudaMemcpyDeviceToDevice, s));
+    // w = Dhat z_j (FP64)
+    WL_TRY(dhat_apply_dev(op, zj, prec != WL_FP64, w, nrhs, s));
+    // Gram-Schmidt against v_0 .. v_j
+    k_zero_hcol<<<WL_GRID(nrhs, 128), 128, 0, s>>>(k);
+    wl_count_launches(1);
+    for (int pass = 0; pass < a->prm.gs_passes; ++pass) {
+      WL_TRY(mdots<double>(a, V, vs, j + 1, w, E, nrhs, k.hcol, m + 1, 1, k.hpass, s));
+      k_maxpy<double><<<gE, 256, 0, s>>>(V, vs, j + 1, k.hpass, m + 1, -1.0, w, E, nrhs);
+      wl_count_launches(1);
+    }
+    zd *tmpc = a->small.as<zd>() + (a->small.bytes / sizeof(zd)) - 2 * (size_t)nrhs - 8;
+    WL_TRY(norms2(a, w, E, nrhs, tmpc, k.nrm2, s));
+    WL_CUDA(cudaMemsetAsync(k.running, 0, sizeof(int) * 2, s));
+    k_givens<<<WL_GRID(nrhs, 128), 128, 0, s>>>(k, j, tol);
+    wl_count_launches(1);
+    if (j + 1 < m) {
+      k_scale_rhs<<<gE, 256, 0, s>>>(w, V + (j + 1) * vs, k.inv, E, nrhs);
+      wl_count_launches(1);
+    }
+    WL_CUDA(cudaGetLastError());
+    int run[2];
+    WL_CUDA(cudaMemcpyAsync(h_d + nrhs, k.running, sizeof(int) * 2, cudaMemcpyDeviceToHost, s));
+    WL_CUDA(cudaStreamSynchronize(s));
+    memcpy(run, h_d + nrhs, sizeof(int) * 2);
+    jdone = j + 1;
+    if (run[1]) {
+      wl_set_error("non-finite Arnoldi residual");
+      return WL_NAN;
+    }
+    if (run[0] == 0) break;
+  }
+  k_trisolve<<<WL_GRID(nrhs, 128), 128, 0, s>>>(k);
+  if (prec == WL_FP64) k_maxpy<double><<<gE, 256, 0, s>>>(a->Z.as<zd>(), vs, jdone, k.y, m, 1.0, xh, E, nrhs);
+  else k_maxpy<float><<<gE, 256, 0, s>>>(a->Z.as<zf>(), vs, jdone, k.y, m, 1.0, xh, E, nrhs);
+  wl_count_launches(2);
+  WL_CUDA(cudaGetLastError());
+  WL_CUDA(cudaMemcpyAsync(iters_out, k.iters, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, s));
+  WL_CUDA(cudaStreamSynchronize(s));
+  return WL_OK;
+}
+
+// ||bhat|| per right-hand side for the stopping test inside fg_cycle
+int fg_upload_bnorm(wl_amg *a, const double *bn, int nrhs) {
+  KS k = ks_layout(a->small.p, a->prm.fgmres_m, nrhs);
+  WL_CUDA(cudaMemcpyAsync(k.bnorm, bn, sizeof(double) * nrhs, cudaMemcpyHostToDevice, a->op->stream));
+  WL_CUDA(cudaStreamSynchronize(a->op->stream));
+  return WL_OK;
+}
+
+// restarted FGMRES on a fixed batch: every right-hand side runs until its
+// true residual is <= tol * ||bhat|| or max_restarts cycles are spent
+int fgmres_run(wl_amg *a, const zd *bh, zd *xh, int nrhs, double tol, wl_info *info) {
+  std::vector<int> active(nrhs, 1), iters(nrhs, 0), restarts(nrhs, 0), it(nrhs, 0);
+  std::vector<double> relres(nrhs, 0.0), bnorm(nrhs, 0.0), rn(nrhs, 0.0);
+  WL_TRY(fg_norms(a, bh, nrhs, bnorm.data()));
+  for (int r = 0; r < nrhs; ++r)
+    if (!(bnorm[r] > 0)) bnorm[r] = 1.0;
+  WL_TRY(fg_upload_bnorm(a, bnorm.data(), nrhs));
   int status = WL_OK;
   for (int cyc = 0;; ++cyc) {
-    // true residual in FP64: rr = bhat - Dhat x
-    WL_TRY(dhat_apply_dev(op, xh, 0, w, nrhs, s));
-    k_sub<<<gE, 256, 0, s>>>(bh, w, rr, E);
-    wl_count_launches(1);
-    WL_TRY(norms2(a, rr, E, nrhs, tmpc, k.nrm2, s));
-    WL_CUDA(cudaMemcpyAsync(h_d, k.nrm2, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s));
-    WL_CUDA(cudaStreamSynchronize(s));
+    WL_TRY(fg_residual(a, bh, xh, nrhs, rn.data()));
     int any = 0;
     for (int r = 0; r < nrhs; ++r) {
-      double rn = sqrt(h_d[r]);
-      if (!std::isfinite(rn)) {
-        wl_set_error("non-finite residual for right-hand side %d", r);
-        return WL_NAN;
-      }
-      relres[r] = rn / bnorm[r];
+      relres[r] = rn[r] / bnorm[r];
       active[r] = active[r] && relres[r] > tol && cyc < a->prm.max_restarts;
       any |= active[r];
     }
     if (!any) break;
-    WL_CUDA(cudaMemcpyAsync(k.active, active.data(), sizeof(int) * nrhs, cudaMemcpyHostToDevice, s));
-    k_cycle_start<<<WL_GRID(nrhs, 128), 128, 0, s>>>(k);
-    k_scale_rhs<<<gE, 256, 0, s>>>(rr, V, k.inv, E, nrhs);
-    wl_count_launches(2);
-    int jdone = 0;
-    for (int j = 0; j < m; ++j) {
-      zd *vj = V + j * vs;
-      void *zj = Zb + (size_t)j * vs * zb_;
-      // z_j = M(v_j) in the cycle precision
-      if (pcyc == WL_FP64) WL_CUDA(cudaMemcpyAsync(a->lev[0].f.p, vj, sizeof(zd) * E, cudaMemcpyDeviceToDevice, s));
-      else {
-        k_cast<float, double><<<gE, 256, 0, s>>>(vj, a->lev[0].f.as<zf>(), E);
-        wl_count_launches(1);
-      }
-      WL_TRY(cycle_run(a, nrhs, pcyc, s));
-      WL_CUDA(cudaMemcpyAsync(zj, a->lev[0].x.p, zb_ * E, cudaMemcpyDeviceToDevice, s));
-      // w = Dhat z_j (FP64)
-      WL_TRY(dhat_apply_dev(op, zj, pcyc != WL_FP64, w, nrhs, s));
-      // Gram-Schmidt against v_0 .. v_j
-      k_zero_hcol<<<WL_GRID(nrhs, 128), 128, 0, s>>>(k);
-      wl_count_launches(1);
-      for (int pass = 0; pass < a->prm.gs_passes; ++pass) {
-        WL_TRY(mdots<double>(a, V, vs, j + 1, w, E, nrhs, k.hcol, m + 1, 1, k.hpass, s));
-        k_maxpy<double><<<gE, 256, 0, s>>>(V, vs, j + 1, k.hpass, m + 1, -1.0, w, E, nrhs);
-        wl_count_launches(1);
-      }
-      WL_TRY(norms2(a, w, E, nrhs, tmpc, k.nrm2, s));
-      WL_CUDA(cudaMemsetAsync(k.running, 0, sizeof(int) * 2, s));
-      k_givens<<<WL_GRID(nrhs, 128), 128, 0, s>>>(k, j, tol);
-      wl_count_launches(1);
-      if (j + 1 < m) {
-        k_scale_rhs<<<gE, 256, 0, s>>>(w, V + (j + 1) * vs, k.inv, E, nrhs);
-        wl_count_launches(1);
-      }
-      WL_CUDA(cudaGetLastError());
-      int run[2];
-      WL_CUDA(cudaMemcpyAsync(h_d + nrhs, k.running, sizeof(int) * 2, cudaMemcpyDeviceToHost, s));
-      WL_CUDA(cudaStreamSynchronize(s));
-      memcpy(run, h_d + nrhs, sizeof(int) * 2);
-      jdone = j + 1;
-      if (run[1]) {
-        wl_set_error("non-finite Arnoldi residual");
-        return WL_NAN;
-      }
-      if (run[0] == 0) break;
-    }
-    k_trisolve<<<WL_GRID(nrhs, 128), 128, 0, s>>>(k);
-    wl_count_launches(2);
-    if (pcyc == WL_FP64) k_maxpy<double><<<gE, 256, 0, s>>>(a->Z.as<zd>(), vs, jdone, k.y, m, 1.0, xh, E, nrhs);
-    else k_maxpy<float><<<gE, 256, 0, s>>>(a->Z.as<zf>(), vs, jdone, k.y, m, 1.0, xh, E, nrhs);
-    WL_CUDA(cudaGetLastError());
-    for (int r = 0; r < nrhs; ++r)
+    WL_TRY(fg_cycle(a, nullptr, xh, nrhs, tol, active.data(), it.data()));
+    for (int r = 0; r < nrhs; ++r) {
+      iters[r] += it[r];
       if (active[r]) restarts[r]++;
+    }
   }
-  WL_CUDA(cudaMemcpyAsync(iters.data(), k.iters, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, s));
-  WL_CUDA(cudaStreamSynchronize(s));
   for (int r = 0; r < nrhs; ++r) {
     bool ok = relres[r] <= tol;
     if (!ok) status = WL_NOT_CONVERGED;

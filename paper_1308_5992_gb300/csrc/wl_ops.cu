@@ -457,6 +457,7 @@ extern "C" int wilson_create(const void *gauge, int L, double m, void *cuda_stre
   op->c = m + 2.0;
   op->user = (cudaStream_t)cuda_stream;
   op->geo = make_geo(L);
+  cudaGetDevice(&op->device);
   if (cudaStreamCreateWithFlags(&op->stream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&op->ev, cudaEventDisableTiming) != cudaSuccess) {
     wl_set_error("wilson_create: cannot create the work stream");

@@ -82,6 +82,13 @@ def lib():
             "amg_fgmres": (i, [P, P, P, i, d, C.POINTER(wl_info)]),
             "wl_last_error": (C.c_char_p, []),
             "wl_time_kernel": (i, [P, i, i, i, i, i, C.POINTER(d)]),
+            "srv_create": (i, [C.c_ulonglong, i, C.POINTER(P)]),
+            "srv_add": (i, [P, P, C.POINTER(i)]),
+            "srv_start": (i, [P]),
+            "srv_submit": (i, [P, i, P, P, i, d, C.POINTER(C.c_longlong)]),
+            "srv_poll": (i, [P, C.c_longlong, C.POINTER(i), C.POINTER(wl_info), C.POINTER(d)]),
+            "srv_drain": (i, [P]),
+            "srv_destroy": (None, [P]),
             "wl_launch_count": (C.c_longlong, []),
         }
         for name, (res, args) in sig.items():
@@ -138,7 +145,12 @@ _live_amg = weakref.WeakSet()
 _live_op = weakref.WeakSet()
 
 
+_live_srv = weakref.WeakSet()
+
+
 def _close_all():
+    for v in list(_live_srv):
+        v.close()
     for a in list(_live_amg):
         a.close()
     for o in list(_live_op):
@@ -304,3 +316,67 @@ def wl_time_kernel(amg, kind, level, nrhs, prec, reps):
 
 def wl_launch_count():
     return lib().wl_launch_count()
+
+
+# ------------------------------------------------------------------ serving
+class wl_server:
+    """Owns a wl_server*; keeps the hierarchies it serves alive."""
+
+    def __init__(self, ptr):
+        self._p = ptr
+        self.amgs = []
+        _live_srv.add(self)
+
+    @property
+    def handle(self):
+        return self._p
+
+    def close(self):
+        if self._p:
+            lib().srv_destroy(self._p)
+            self._p = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def srv_create(hbm_budget_bytes, max_slots_per_config):
+    out = C.c_void_p()
+    _chk(lib().srv_create(int(hbm_budget_bytes), max_slots_per_config, C.byref(out)), "srv_create")
+    return wl_server(out)
+
+
+def srv_add(srv, amg):
+    cid = C.c_int()
+    _chk(lib().srv_add(srv.handle, amg.handle, C.byref(cid)), "srv_add")
+    srv.amgs.append(amg)
+    return cid.value
+
+
+def srv_start(srv):
+    return _chk(lib().srv_start(srv.handle), "srv_start")
+
+
+def srv_submit(srv, cfg, b, x, nrhs, tol):
+    rid = C.c_longlong()
+    _chk(lib().srv_submit(srv.handle, cfg, _ptr(b), _ptr(x), nrhs, tol, C.byref(rid)), "srv_submit")
+    return rid.value
+
+
+def srv_poll(srv, req_id, nrhs):
+    done, lat = C.c_int(), C.c_double()
+    info = (wl_info * nrhs)()
+    rc = lib().srv_poll(srv.handle, req_id, C.byref(done), info, C.byref(lat))
+    _chk(rc, "srv_poll", ok=(WL_OK, WL_NOT_CONVERGED))
+    return bool(done.value), [i.as_dict() for i in info], lat.value
+
+
+def srv_drain(srv):
+    return _chk(lib().srv_drain(srv.handle), "srv_drain")
+
+
+def srv_destroy(srv):
+    srv.close()
