@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
+
+#include <atomic>
 #include <string>
 #include <vector>
 
@@ -151,6 +153,7 @@ struct DBuf {
 
 // ------------------------------------------------------------ host objects
 struct wl_op {
+  std::atomic<int> refs{1};  // the caller's handle plus one per live hierarchy
   int N;
   double m, c;
   cudaStream_t stream;  // the library's own non-blocking work stream
@@ -179,6 +182,7 @@ struct Level {
 };
 
 struct wl_amg {
+  std::atomic<int> refs{1};  // the caller's handle plus one per server using it
   wl_op *op;
   amg_params prm;
   int L;
@@ -205,6 +209,14 @@ struct wl_amg {
 
 // --------------------------------------------------------- internal C++ API
 namespace wl {
+// lifetime: an operator is freed when its last reference goes (the caller's
+// wl_destroy and every hierarchy built on it); a hierarchy likewise (the
+// caller's amg_destroy and every server it was added to), so the order in
+// which a caller drops its handles does not matter
+void op_retain(wl_op *op);
+void op_release(wl_op *op);
+void amg_retain(wl_amg *a);
+void amg_release(wl_amg *a);
 int enter(wl_op *op);  // work stream waits for everything queued on the caller's stream
 int ensure_workspace(wl_amg *a, int nrhs, int prec);
 int level_ops_build_copies(wl_amg *a);

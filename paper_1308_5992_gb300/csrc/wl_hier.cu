@@ -338,12 +338,21 @@ void amg_free(wl_amg *a) {
   a->red.release();
   a->small.release();
   if (a->h_small) cudaFreeHost(a->h_small);
+  wl_op *op = a->op;
   delete a;
+  if (op) op_release(op);
+}
+
+void amg_retain(wl_amg *a) { a->refs.fetch_add(1); }
+void amg_release(wl_amg *a) {
+  if (a->refs.fetch_sub(1) == 1) amg_free(a);
 }
 
 }  // namespace wl
 
-extern "C" void amg_destroy(wl_amg *a) { wl::amg_free(a); }
+extern "C" void amg_destroy(wl_amg *a) {
+  if (a) wl::amg_release(a);
+}
 
 extern "C" int amg_levels(wl_amg *a, int *N_out) {
   if (!a) return WL_EINVAL;
@@ -474,6 +483,7 @@ extern "C" int amg_import(wl_op *op, const char *path, const amg_params *params,
   WL_TRY(wl::enter(op));
   wl_amg *a = new wl_amg();
   a->op = op;
+  wl::op_retain(op);
   a->prm = prm;
   a->L = L;
   a->cap = 0;

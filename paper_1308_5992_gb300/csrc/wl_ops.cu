@@ -500,8 +500,7 @@ extern "C" int wilson_create(const void *gauge, int L, double m, void *cuda_stre
   return WL_OK;
 }
 
-extern "C" void wl_destroy(wl_op *op) {
-  if (!op) return;
+static void op_free(wl_op *op) {
   if (op->stream) cudaStreamSynchronize(op->stream);
   op->Uf64.release();
   op->Uf32.release();
@@ -510,6 +509,17 @@ extern "C" void wl_destroy(wl_op *op) {
   if (op->stream) cudaStreamDestroy(op->stream);
   delete op;
 }
+
+extern "C" void wl_destroy(wl_op *op) {
+  if (op) wl::op_release(op);
+}
+
+namespace wl {
+void op_retain(wl_op *op) { op->refs.fetch_add(1); }
+void op_release(wl_op *op) {
+  if (op->refs.fetch_sub(1) == 1) op_free(op);
+}
+}  // namespace wl
 
 namespace wl {
 int enter(wl_op *op) {

@@ -233,6 +233,7 @@ extern "C" int srv_add(wl_server *S, wl_amg *amg, int *cfg_id) {
     return rc;
   }
   W->bytes = need;
+  wl::amg_retain(amg);  // the hierarchy outlives the server's use of it
   S->used += need;
   *cfg_id = (int)S->w.size();
   S->w.push_back(W);
@@ -321,6 +322,7 @@ extern "C" void srv_destroy(wl_server *S) {
     W->PB.release();
     W->PX.release();
     W->cols.release();
+    wl::amg_release(W->amg);
     delete W;
   }
   for (auto &kv : S->reqs) delete kv.second;

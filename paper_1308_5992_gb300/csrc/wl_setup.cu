@@ -704,6 +704,7 @@ extern "C" int amg_setup(wl_op *op, const amg_params *params, wl_amg **out) {
   WL_TRY(wl::enter(op));
   wl_amg *a = new wl_amg();
   a->op = op;
+  wl::op_retain(op);
   a->prm = prm;
   a->L = prm.levels;
   a->cap = 0;
