@@ -164,6 +164,26 @@ int amg_cycle(wl_amg *amg, const void *f, void *x, int nrhs, int prec);
  * array [nrhs]. */
 int amg_fgmres(wl_amg *amg, const void *bhat, void *x, int nrhs, double tol, wl_info *info);
 
+/* y = Dhat x in FP64 with no device allocation (the paper has no counterpart;
+ * this is a service of the library).  For callers that cannot allocate device
+ * memory when they need the operator: a process whose device memory is
+ * already held by its own pool (a framework's caching allocator, say, so a
+ * raw cudaMalloc would fail), or a latency-critical loop that cannot afford
+ * the device-wide synchronisation cudaMalloc / cudaFree imply.  The odd-site
+ * intermediate lives in a fixed 16 MiB device array of the library
+ * (2^20 complex doubles, held on every GPU that loads the library until the
+ * process exits); the call allocates nothing, not even through torch.
+ * x, y: device, level-0 vectors [nrhs][L^2/2][2] complex128, caller-owned.
+ * Limit: L^2 * nrhs <= 2^20 (for example L = 512 with nrhs <= 4, L = 1024
+ * with nrhs = 1); larger sizes return WL_EINVAL with a message naming the
+ * limit.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) and caches it; make that first call before any
+ * stream capture.  All calls share the array, which keeps the last call's
+ * contents (every element read is first overwritten, so nothing needs
+ * clearing); calls whose work overlaps on the GPU race on it.  Synchronous:
+ * returns after y is written. */
+int wl_dhat_apply_noalloc(wl_op *op, const void *x, void *y, int nrhs);
+
 /* ---- serving: continuous batching over resident hierarchies ----
  * A server keeps hierarchies of several gauge fields (lattice sizes may
  * differ) resident and answers solve requests.  srv_add reserves, for each

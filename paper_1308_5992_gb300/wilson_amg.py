@@ -82,6 +82,7 @@ def lib():
             "amg_fgmres": (i, [P, P, P, i, d, C.POINTER(wl_info)]),
             "wl_last_error": (C.c_char_p, []),
             "wl_time_kernel": (i, [P, i, i, i, i, i, C.POINTER(d)]),
+            "wl_dhat_apply_noalloc": (i, [P, P, P, i]),
             "srv_create": (i, [C.c_ulonglong, i, C.POINTER(P)]),
             "srv_add": (i, [P, P, C.POINTER(i)]),
             "srv_start": (i, [P]),
@@ -380,3 +381,8 @@ def srv_drain(srv):
 
 def srv_destroy(srv):
     srv.close()
+
+
+def wl_dhat_apply_noalloc(op, x, y, nrhs):
+    """y = Dhat x through the allocation-free entry point (see the C header)."""
+    return _chk(lib().wl_dhat_apply_noalloc(op.handle, _ptr(x), _ptr(y), nrhs), "wl_dhat_apply_noalloc")
