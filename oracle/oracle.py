@@ -22,6 +22,7 @@ _lib = None
 
 ORDER_LEX = 0
 ORDER_COLOUR = 1
+ORDER_TILE = 2
 
 
 def build(force: bool = False) -> str:
@@ -65,7 +66,8 @@ def lib():
             "or_coarsest_solve": (i, [P, P, P]),
             "or_cycle": (i, [P, i, P, P, i, i, i, i]),
             "or_fgmres": (i, [P, P, P, d, i, i, i, i, i, i, P, P, P]),
-            "or_solve": (i, [i, P, d, P, P, P, d, i, i, i, i, i, P, P]),
+            "or_solve": (i, [i, P, d, P, P, P, d, i, i, i, i, i, i, P, P]),
+            "or_tile_size": (i, [i]),
             "or_ls_fit": (i, [i, i, i, P, P, P]),
             "or_galerkin": (i, [P, i, P]),
             "or_gen_eig": (i, [i, P, P, P, P]),
@@ -153,6 +155,10 @@ def colour(N, h):
 
 def neighbour(N, h, d):
     return lib().or_stencil_neighbour(N, h, d)
+
+
+def tile_size(N):
+    return lib().or_tile_size(N)
 
 
 def rng_u64(seed, stream, i):
@@ -312,10 +318,10 @@ class Hierarchy:
                                   precond, C.byref(it), C.byref(rs), C.byref(rr)), "fgmres")
         return x, dict(status=st, iters=it.value, restarts=rs.value, relres=rr.value)
 
-    def solve(self, b, tol=1e-10, m=20, max_restarts=50, nu1=2, nu2=2, gamma=1):
+    def solve(self, b, tol=1e-10, m=20, max_restarts=50, nu1=2, nu2=2, gamma=1, order=ORDER_COLOUR):
         b = _c(b)
         psi = np.zeros_like(b)
         it, rr = C.c_int(), C.c_double()
         st = _chk(lib().or_solve(self.N, _p(self.U), self.m, self._h, _p(b), _p(psi), tol, m,
-                                 max_restarts, nu1, nu2, gamma, C.byref(it), C.byref(rr)), "solve")
+                                 max_restarts, nu1, nu2, gamma, order, C.byref(it), C.byref(rr)), "solve")
         return psi, dict(status=st, iters=it.value, relres=rr.value)

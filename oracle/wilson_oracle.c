@@ -757,14 +757,47 @@ static void kaczmarz_update(const or_csr *AT, int i, cplx *x, cplx *r, double om
   for (int p = AT->rowptr[i]; p < AT->rowptr[i + 1]; ++p) r[AT->col[p]] -= s * AT->val[p];
 }
 
+/* Tile-coloured ordering (a reading of Sec. 3.1's parallel ordering that
+ * keeps each tile's work local): the (a, b) plane is cut into T x T tiles,
+ * tile (ta, tb) = (a / T, b / T) of the fundamental domain a in [0, N),
+ * b in [0, N/2), with tile colour (ta mod 2) + 2 (tb mod 2).  The sweep takes
+ * tile colours 0..3 in turn; inside a tile it takes the 16 site colours
+ * 0..15 in turn (sites in increasing (a, b), spin 0 then 1).  Variables of a
+ * site touch only its 3x3 (a, b) box, so tiles of one colour (one tile
+ * apart) are independent.  T = 8 when N >= 64 (then 4T divides N, which
+ * keeps the tile colouring consistent across the seam b = N/2 ~ 0);
+ * smaller grids use the plain 16-colour order. */
+int or_tile_size(int N) { return (N >= 64 && N % 32 == 0) ? 8 : 0; }
+
+static void tile_sweep(const or_csr *AT, int N, cplx *x, cplx *r, double omega) {
+  int T = or_tile_size(N);
+  for (int tc = 0; tc < 4; ++tc)
+    for (int ta = 0; ta < N / T; ++ta)
+      for (int tb = 0; tb < N / (2 * T); ++tb) {
+        if ((ta & 1) + 2 * (tb & 1) != tc) continue;
+        for (int c = 0; c < 16; ++c)
+          for (int i = 0; i < T; ++i)
+            for (int j = 0; j < T; ++j) {
+              int a = ta * T + i, b = tb * T + j;
+              if (4 * (a % 4) + (b % 4) != c) continue;
+              int site = site_of(N, a + b, a - b);
+              kaczmarz_update(AT, 2 * site, x, r, omega);
+              kaczmarz_update(AT, 2 * site + 1, x, r, omega);
+            }
+      }
+}
+
 int or_kaczmarz(const or_hier *h, int l, cplx *x, cplx *r, int order, int sweeps,
                 double omega, const int *perm) {
   if (l < 0 || l >= h->L) return OR_EINVAL;
   const or_csr *AT = &h->AT[l];
   int N = h->N[l], n = AT->nrow / 2;
-  if (order == OR_ORDER_COLOUR && N % 8) return OR_EINVAL;
+  if (order != OR_ORDER_LEX && N % 8) return OR_EINVAL;
+  if (order == OR_ORDER_TILE && !or_tile_size(N)) order = OR_ORDER_COLOUR;
   for (int sw = 0; sw < sweeps; ++sw) {
-    if (order == OR_ORDER_LEX) {
+    if (order == OR_ORDER_TILE) {
+      tile_sweep(AT, N, x, r, omega);
+    } else if (order == OR_ORDER_LEX) {
       for (int i = 0; i < 2 * n; ++i) kaczmarz_update(AT, i, x, r, omega);
     } else {
       for (int k = 0; k < 16; ++k)
@@ -887,7 +920,7 @@ int or_fgmres(const or_hier *h, const cplx *b, cplx *x, double tol, int mrestart
     int jend = 0;
     for (int j = 0; j < m; ++j) {
       cplx *vj = V + (size_t)j * n, *zj = Z + (size_t)j * n;
-      if (precond) rc = or_cycle(h, 0, vj, zj, nu1, nu2, gamma, OR_ORDER_COLOUR);
+      if (precond) rc = or_cycle(h, 0, vj, zj, nu1, nu2, gamma, precond == 2 ? OR_ORDER_TILE : OR_ORDER_COLOUR);
       else memcpy(zj, vj, sizeof(cplx) * n);
       if (rc) break;
       csr_matvec(&h->A[0], zj, w);
@@ -949,14 +982,14 @@ int or_fgmres(const or_hier *h, const cplx *b, cplx *x, double tol, int mrestart
 /* Sec. 4: D psi = b through the reduced system Dhat psi_e = bhat. */
 int or_solve(int N, const cplx *U, double m, const or_hier *h, const cplx *b,
              cplx *psi, double tol, int mrestart, int max_restarts, int nu1,
-             int nu2, int gamma, int *iters_out, double *relres_out) {
+             int nu2, int gamma, int order, int *iters_out, double *relres_out) {
   int n = n_sites(N) * 2;
   cplx *bh = malloc(sizeof(cplx) * n), *xe = calloc(n, sizeof(cplx));
   if (!bh || !xe) { free(bh); free(xe); return OR_ENOMEM; }
   int rc = or_eo_reduce(N, U, m, b, bh);
   int st = 1;
-  if (!rc) st = or_fgmres(h, bh, xe, tol, mrestart, max_restarts, nu1, nu2, gamma, 1,
-                          iters_out, NULL, relres_out);
+  if (!rc) st = or_fgmres(h, bh, xe, tol, mrestart, max_restarts, nu1, nu2, gamma,
+                          order == OR_ORDER_TILE ? 2 : 1, iters_out, NULL, relres_out);
   if (!rc && st >= 0) rc = or_eo_reconstruct(N, U, m, b, xe, psi);
   free(bh); free(xe);
   return rc ? rc : st;

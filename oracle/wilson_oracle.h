@@ -32,7 +32,7 @@ typedef struct {
   cplx *val;
 } or_csr;
 
-enum { OR_ORDER_LEX = 0, OR_ORDER_COLOUR = 1 };
+enum { OR_ORDER_LEX = 0, OR_ORDER_COLOUR = 1, OR_ORDER_TILE = 2 };
 
 #define OR_MAXLEV 8
 
@@ -81,6 +81,7 @@ int or_eo_reconstruct(int N, const cplx *U, double m, const cplx *b,
 
 /* ---- level geometry ---- */
 int or_colour(int N, int h);
+int or_tile_size(int N);
 int or_stencil_neighbour(int N, int h, int d);
 
 /* ---- hierarchy ---- */
@@ -107,7 +108,7 @@ int or_fgmres(const or_hier *h, const cplx *b, cplx *x, double tol, int mrestart
               int *iters_out, int *restarts_out, double *relres_out);
 int or_solve(int N, const cplx *U, double m, const or_hier *h, const cplx *b,
              cplx *psi, double tol, int mrestart, int max_restarts, int nu1,
-             int nu2, int gamma, int *iters_out, double *relres_out);
+             int nu2, int gamma, int order, int *iters_out, double *relres_out);
 
 /* ---- setup building blocks (Secs. 3.3-3.5) ---- */
 int or_ls_fit(int Nf, int B, int k, const cplx *V, const double *w, cplx *Pw);

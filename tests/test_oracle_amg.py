@@ -345,3 +345,61 @@ def test_rng_reference_values(O):
     assert R._sm_scalar(0x9E3779B97F4A7C15) == 0x6E789E6AA1B965F4
     for s, st, i in [(0, 0, 0), (123, 7, 99), (2**63 + 5, 3, 2**40)]:
         assert int(R.rng_u64(s, st, [i])[0]) == O.rng_u64(s, st, i)
+
+
+def _tile_order(O, N):
+    """the tile-coloured permutation written out from its definition"""
+    T = O.tile_size(N)
+    order = []
+    for tc in range(4):
+        for ta in range(N // T):
+            for tb in range(N // (2 * T)):
+                if (ta & 1) + 2 * (tb & 1) != tc:
+                    continue
+                for c in range(16):
+                    for i in range(T):
+                        for j in range(T):
+                            a, b = ta * T + i, tb * T + j
+                            if 4 * (a % 4) + (b % 4) != c:
+                                continue
+                            x, y = (a + b) % N, (a - b) % N
+                            order.append(y * (N // 2) + x // 2)
+    return order
+
+
+def test_tile_order_covers_every_site_and_tiles_are_independent(O):
+    """The tile-coloured ordering (a reading of Sec. 3.1's parallel
+    ordering): each site once per sweep, and tiles of one tile colour touch
+    disjoint 3x3 column supports, so they can be relaxed at the same time."""
+    for N in (64, 128):
+        T = O.tile_size(N)
+        assert T == 8
+        order = _tile_order(O, N)
+        assert sorted(order) == list(range(N * N // 2))
+        supp = {h: {O.neighbour(N, h, d) for d in range(9)} for h in range(N * N // 2)}
+        per_tile = N * N // 2 // ((N // T) * (N // (2 * T)))
+        tiles = [order[k:k + per_tile] for k in range(0, len(order), per_tile)]
+        ntc = len(tiles) // 4
+        for tc in range(4):
+            seen = set()
+            for t in tiles[tc * ntc:(tc + 1) * ntc]:
+                region = set().union(*(supp[h] for h in t))
+                assert not (region & seen)
+                seen |= region
+    assert O.tile_size(32) == 0  # small grids keep the 16-colour order
+
+
+def test_tile_sweep_is_a_forward_sweep(O, h64):
+    """One tile-coloured sweep equals the dense textbook forward sweep over
+    the variables in the tile order (spin 0 then 1 per site)."""
+    h, w = h64
+    A = h.dense(0)
+    n = A.shape[0] // 2
+    f = cgauss(15, 1, 2 * n)
+    order = []
+    for s_ in _tile_order(O, w["N"]):
+        order += [2 * s_, 2 * s_ + 1]
+    xr, _ = _dense_kaczmarz(A, f, np.zeros(2 * n, complex), order)
+    x, r = h.kaczmarz(0, np.zeros(2 * n), f, order=O.ORDER_TILE)
+    assert np.abs(x - xr).max() <= 1e-13 * np.abs(xr).max()
+    assert np.abs(r - (f - A @ x)).max() <= 1e-12 * np.abs(f).max()
