@@ -68,24 +68,50 @@ def shift_for(N, U, t):
                 min_re=float((ev + m).real.min()))
 
 
+def eta0_for(N, U):
+    """eta0 = min Re lambda(D_0): the eigenvalues nearest 0 locate the left
+    edge of the spectrum, a second shift-invert run centred there refines
+    it.  A run with eta_min(D) = eta then uses m = eta - eta0."""
+    D0 = O.wilson_csr(N, U, 0.0).tocsc()
+    ev = near_eigs(D0, 0.0, 12)
+    eta0 = ev.real.min()
+    ev = np.concatenate([ev, near_eigs(D0, eta0, 12)])
+    return dict(eta0=float(ev.real.min()), m=None, rule="eta_sweep")
+
+
+def _update(path, entries):
+    """Merge entries into the JSON file under an exclusive lock, so that
+    several runs on different workloads can proceed in parallel."""
+    import fcntl
+    with open(path + ".lock", "w") as lk:
+        fcntl.flock(lk, fcntl.LOCK_EX)
+        out = {}
+        if os.path.exists(path):
+            with open(path) as f:
+                out = json.load(f)
+        out.update(entries)
+        tmp = path + ".tmp"
+        with open(tmp, "w") as f:
+            json.dump(out, f, indent=1, sort_keys=True)
+        os.replace(tmp, path)
+
+
 def main(names):
     path = os.path.join(os.path.dirname(_HERE), "wl_inputs", "shifts.json")
-    out = {}
-    if os.path.exists(path):
-        with open(path) as f:
-            out = json.load(f)
     for name in names:
         t0 = time.time()
         w = W.workload(name)
-        r = shift_for(w["N"], w["U"], w["target"])
+        if w.get("eta_sweep"):
+            r = eta0_for(w["N"], w["U"])
+        else:
+            r = shift_for(w["N"], w["U"], w["target"])
         r["seconds"] = round(time.time() - t0, 1)
-        out[name] = r
+        entries = {name: r}
         for other, ow in W.WORKLOADS.items():   # workloads sharing this gauge and target
             if other != name and all(ow[k] == w[k] for k in ("N", "beta", "sweeps", "seed", "target")):
-                out[other] = dict(r, same_as=name)
+                entries[other] = dict(r, same_as=name)
         print(name, r, flush=True)
-        with open(path, "w") as f:
-            json.dump(out, f, indent=1, sort_keys=True)
+        _update(path, entries)
 
 
 if __name__ == "__main__":

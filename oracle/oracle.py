@@ -67,6 +67,7 @@ def lib():
             "or_cycle": (i, [P, i, P, P, i, i, i, i]),
             "or_fgmres": (i, [P, P, P, d, i, i, i, i, i, i, P, P, P]),
             "or_solve": (i, [i, P, d, P, P, P, d, i, i, i, i, i, i, P, P]),
+            "or_rho": (i, [P, P, d, i, i, i, i, i, P, P, P]),
             "or_tile_size": (i, [i]),
             "or_ls_fit": (i, [i, i, i, P, P, P]),
             "or_galerkin": (i, [P, i, P]),
@@ -197,13 +198,13 @@ class SetupParams(C.Structure):
                 ("gamma", C.c_int), ("setup_cycle", C.c_int), ("seed", C.c_uint64)]
 
 
-def setup_params(blocks, k_r=8, k_e=8, mu1=10, mu2=5, nu_pre=4, nu_post=4, gamma=2, seed=1):
+def setup_params(blocks, k_r=8, k_e=8, mu1=10, mu2=5, nu_pre=4, nu_post=4, gamma=2, seed=1, super_v=False):
     p = SetupParams()
     p.levels = len(blocks) + 1
     for i, b in enumerate(blocks):
         p.block[i] = b
     p.k_r, p.k_e, p.mu1, p.mu2 = k_r, k_e, mu1, mu2
-    p.nu_pre, p.nu_post, p.gamma, p.setup_cycle, p.seed = nu_pre, nu_post, gamma, 2, seed
+    p.nu_pre, p.nu_post, p.gamma, p.setup_cycle, p.seed = nu_pre, nu_post, gamma, 1 if super_v else 2, seed
     return p
 
 
@@ -317,6 +318,17 @@ class Hierarchy:
         st = _chk(lib().or_fgmres(self._h, _p(b), _p(x), tol, m, max_restarts, nu1, nu2, gamma,
                                   precond, C.byref(it), C.byref(rs), C.byref(rr)), "fgmres")
         return x, dict(status=st, iters=it.value, restarts=rs.value, relres=rr.value)
+
+    def rho(self, x0, tol=1e-8, maxit=100, nu1=4, nu2=4, gamma=2, order=ORDER_COLOUR):
+        """Sec. 4's estimate rho = |e^nu| / |e^(nu-1)| of the stand-alone
+        cycle on A_0 x = 0 from x0; returns (rho, nu, [|e^0|, .., |e^nu|],
+        met) where met says whether |e^nu| <= tol |e^0| was reached."""
+        x0 = _c(x0)
+        r, it = C.c_double(), C.c_int()
+        hist = np.zeros(maxit + 1)
+        st = _chk(lib().or_rho(self._h, _p(x0), tol, maxit, nu1, nu2, gamma, order, C.byref(r),
+                               C.byref(it), _p(hist)), "rho")
+        return r.value, it.value, hist[:it.value + 1], st == 0
 
     def solve(self, b, tol=1e-10, m=20, max_restarts=50, nu1=2, nu2=2, gamma=1, order=ORDER_COLOUR):
         b = _c(b)

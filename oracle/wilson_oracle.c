@@ -979,6 +979,41 @@ int or_fgmres(const or_hier *h, const cplx *b, cplx *x, double tol, int mrestart
   return rc ? rc : status;
 }
 
+/* Sec. 4, convergence estimate of the stand-alone solver: the cycle used as
+ * a stationary iteration x <- x + M(f - A_0 x) on A_0 x = 0, so the iterate
+ * is the error, e^nu = (I - M A_0) e^{nu-1} with e^0 = x0.  rho is
+ * |e^nu| / |e^{nu-1}| at the first nu with |e^nu| <= tol |e^0|, or at
+ * nu = maxit.  hist (optional, maxit + 1 entries): |e^k| for k <= nu.
+ * Returns 0 when the tolerance was met, 1 when maxit was reached. */
+int or_rho(const or_hier *h, const cplx *x0, double tol, int maxit, int nu1, int nu2,
+           int gamma, int order, double *rho_out, int *iters_out, double *hist) {
+  int n = h->A[0].nrow;
+  cplx *e = malloc(sizeof(cplx) * n), *w = malloc(sizeof(cplx) * n);
+  cplx *c = malloc(sizeof(cplx) * n);
+  if (!e || !w || !c) { free(e); free(w); free(c); return OR_ENOMEM; }
+  for (int i = 0; i < n; ++i) e[i] = x0[i];
+  double n0 = vnorm(n, e), prev = n0, rho = 0;
+  if (hist) hist[0] = n0;
+  int nu = 0, rc = 0, met = 0;
+  while (nu < maxit && !rc) {
+    csr_matvec(&h->A[0], e, w);                 /* residual of A_0 x = 0 is -A_0 e */
+    rc = or_cycle(h, 0, w, c, nu1, nu2, gamma, order);
+    if (rc) break;
+    for (int i = 0; i < n; ++i) e[i] -= c[i];   /* x + M(-A_0 x) = x - M(A_0 x) */
+    ++nu;
+    double cur = vnorm(n, e);
+    if (hist) hist[nu] = cur;
+    rho = prev > 0 ? cur / prev : 0;
+    prev = cur;
+    if (cur <= tol * n0) { met = 1; break; }
+  }
+  free(e); free(w); free(c);
+  if (rc) return rc;
+  *rho_out = rho;
+  *iters_out = nu;
+  return met ? 0 : 1;
+}
+
 /* Sec. 4: D psi = b through the reduced system Dhat psi_e = bhat. */
 int or_solve(int N, const cplx *U, double m, const or_hier *h, const cplx *b,
              cplx *psi, double tol, int mrestart, int max_restarts, int nu1,
@@ -1440,6 +1475,27 @@ static int setup_visit(setup_state *S, int l, int first, int mu) {
   return rc;
 }
 
+/* Sec. 4.2 super-V setup cycle: every grid is visited once and the coarsest
+ * eigensolve runs once per setup cycle; grid l >= 1 relaxes mu 2^l times
+ * before (both vector sets, then fit and injection) and after (the
+ * eigenvector set, Eq. 3.16) its coarse visit.  Reading: this gives each
+ * grid the relaxation count of the W-visits above (2^(l-1) visits with mu
+ * sweeps at each of the pre, middle and post nodes) in V(mu 2^l, mu 2^l)
+ * form; P of grid l is the one fitted before its coarse visit. */
+static int setup_visit_superv(setup_state *S, int l, int first, int mu) {
+  or_hier *h = S->h;
+  if (l == h->L - 1) return coarsest_eig(S);
+  int mul = mu << l;
+  int rc = relax_both(S, l, mul, !first);
+  if (!rc) rc = fit_level(S, l);
+  if (!rc) inject_all(S, l);
+  if (!rc) rc = setup_visit_superv(S, l + 1, first, mu);
+  if (!rc) rc = interp_e(S, l);
+  for (int e = 0; e < S->ke && !rc; ++e)
+    rc = relax_eig(h, l, S->Ve[l] + (size_t)e * lev_n(h, l), &S->le[l][e], mul);
+  return rc;
+}
+
 /* Sec. 4.1 adaptive step: the test vector on the finest grid with the
  * smallest |lambda| (Eq. 3.17) is improved by two solver cycles applied to
  * D_1 v = 0 (x <- x + M(0 - A x)). */
@@ -1514,14 +1570,14 @@ or_hier *or_setup(int N, const cplx *U, double m, const or_setup_params *p,
   if (!rc) rc = relax_both(&S, 0, p->mu1, 0);
   if (!rc) rc = fit_level(&S, 0);
   if (!rc) inject_all(&S, 0);
-  if (!rc) rc = setup_visit(&S, 1, 1, p->mu1);
+  if (!rc) rc = p->setup_cycle == 1 ? setup_visit_superv(&S, 1, 1, p->mu1) : setup_visit(&S, 1, 1, p->mu1);
   if (!rc) rc = interp_e(&S, 0);
   if (!rc) rc = adaptive_step(&S);
   /* cycle 2: green pre node on the finest grid, W-visit of level 1 */
   if (!rc) rc = relax_both(&S, 0, p->mu2, 1);
   if (!rc) rc = fit_level(&S, 0);
   if (!rc) inject_all(&S, 0);
-  if (!rc) rc = setup_visit(&S, 1, 0, p->mu2);
+  if (!rc) rc = p->setup_cycle == 1 ? setup_visit_superv(&S, 1, 0, p->mu2) : setup_visit(&S, 1, 0, p->mu2);
   if (!rc) rc = interp_e(&S, 0);
   if (!rc && ritz_out)
     for (int e = 0; e < S.ke; ++e) ritz_out[e] = S.le[0][e];

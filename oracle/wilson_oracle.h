@@ -60,7 +60,7 @@ typedef struct {
   int mu1, mu2;          /* relaxations per visit in setup cycles 1 and 2    */
   int nu_pre, nu_post;   /* solve-cycle smoothing (used by the adaptive step)*/
   int gamma;             /* 1 = V, 2 = W (solve cycle in the adaptive step)  */
-  int setup_cycle;       /* 2 = W-cycle setup (Fig. 3.1)                     */
+  int setup_cycle;       /* 2 = W-cycle setup (Fig. 3.2), 1 = super-V (Sec. 4.2) */
   uint64_t seed;
 } or_setup_params;
 
@@ -106,6 +106,8 @@ int or_cycle(const or_hier *h, int l, const cplx *f, cplx *x, int nu1, int nu2,
 int or_fgmres(const or_hier *h, const cplx *b, cplx *x, double tol, int mrestart,
               int max_restarts, int nu1, int nu2, int gamma, int precond,
               int *iters_out, int *restarts_out, double *relres_out);
+int or_rho(const or_hier *h, const cplx *x0, double tol, int maxit, int nu1, int nu2,
+           int gamma, int order, double *rho_out, int *iters_out, double *hist);
 int or_solve(int N, const cplx *U, double m, const or_hier *h, const cplx *b,
              cplx *psi, double tol, int mrestart, int max_restarts, int nu1,
              int nu2, int gamma, int order, int *iters_out, double *relres_out);

@@ -403,3 +403,66 @@ def test_tile_sweep_is_a_forward_sweep(O, h64):
     x, r = h.kaczmarz(0, np.zeros(2 * n), f, order=O.ORDER_TILE)
     assert np.abs(x - xr).max() <= 1e-13 * np.abs(xr).max()
     assert np.abs(r - (f - A @ x)).max() <= 1e-12 * np.abs(f).max()
+
+
+def test_rho_two_grid_projector(O, h32):
+    """Sec. 4's rho with no smoothing on two grids: the error propagator
+    I - P A_c^-1 P^H A of a Galerkin coarse correction is a projector
+    (its square is itself), so after one iteration the error stays put and
+    rho = 1 exactly, while the first step reduces the error."""
+    x0 = cgauss(4, 1, h32.n(0))
+    rho, nu, hist, met = h32.rho(x0, tol=1e-300, maxit=6, nu1=0, nu2=0, gamma=1)
+    assert nu == 6 and not met
+    assert hist[1] < hist[0]
+    assert abs(rho - 1.0) <= 1e-12
+    assert np.abs(hist[1:] / hist[1] - 1.0).max() <= 1e-12
+
+
+def test_rho_is_the_spectral_radius(O, h32):
+    """After 100 iterations the ratio |e^nu| / |e^(nu-1)| of Sec. 4 equals
+    the spectral radius of the error propagator I - M A_0, assembled column
+    by column from the cycle and handed to a dense eigensolver."""
+    A = h32.dense(0)
+    n = A.shape[0]
+    E = np.eye(n, dtype=complex)
+    for j in range(n):
+        E[:, j] -= h32.cycle(A[:, j], nu1=1, nu2=1, gamma=1)
+    sr = np.abs(np.linalg.eigvals(E)).max()
+    rho, nu, hist, met = h32.rho(cgauss(4, 1, n), tol=1e-300, maxit=100, nu1=1, nu2=1, gamma=1)
+    assert nu == 100 and not met
+    assert abs(rho - sr) <= 1e-6 * sr, (rho, sr)
+
+
+def test_rho_stops_at_tolerance(O, h64):
+    """The estimate is taken at the first iteration whose error norm is
+    below tol times the initial one (W(4,4), Sec. 4)."""
+    h, _ = h64
+    rho, nu, hist, met = h.rho(cgauss(4, 2, h.n(0)), tol=1e-8, maxit=100, nu1=4, nu2=4, gamma=2)
+    assert met and nu < 100
+    assert hist[-1] <= 1e-8 * hist[0] < hist[-2]
+    assert abs(rho - hist[-1] / hist[-2]) <= 1e-15
+    assert rho < 0.6
+
+
+def test_super_v_setup(O, h64):
+    """Sec. 4.2's super-V setup (each grid visited once): on two grids it is
+    the W setup (the only coarse visit is the coarsest eigensolve); on three
+    grids it yields a convergent stand-alone W(4,4) solver and a
+    preconditioner within the quality band of the W setup."""
+    U = metropolis_u1(32, 6.0, 100, 21)
+    pw = O.setup_params([2], k_r=6, k_e=6, mu1=6, mu2=3, seed=5)
+    pv = O.setup_params([2], k_r=6, k_e=6, mu1=6, mu2=3, seed=5, super_v=True)
+    hw, hv = O.Hierarchy.setup(32, U, -0.05, pw), O.Hierarchy.setup(32, U, -0.05, pv)
+    assert np.array_equal(hw.dense(0, 1), hv.dense(0, 1))
+    h, w = h64
+    p = O.setup_params(w["blocks"], k_r=w["k"], k_e=w["k"], seed=w["seed"], super_v=True)
+    hs = O.Hierarchy.setup(w["N"], w["U"], w["m"], p)
+    assert not np.array_equal(hs.dense(1, 1), h.dense(1, 1))
+    x0 = cgauss(4, 3, h.n(0))
+    rho_v, nu_v, _, met_v = hs.rho(x0, tol=1e-8, maxit=100, nu1=4, nu2=4, gamma=2)
+    rho_w, nu_w, _, _ = h.rho(x0, tol=1e-8, maxit=100, nu1=4, nu2=4, gamma=2)
+    assert met_v and rho_v < 0.9
+    bh = O.eo_reduce(w["N"], w["U"], w["m"], rhs_batch(w["N"], 1, 6)[0])
+    _, iv = hs.fgmres(bh, tol=1e-8, m=32, max_restarts=5, nu1=4, nu2=4, gamma=2)
+    _, iw = h.fgmres(bh, tol=1e-8, m=32, max_restarts=5, nu1=4, nu2=4, gamma=2)
+    assert iv["status"] == 0 and iv["iters"] <= 2 * iw["iters"] + 5, (iv, iw, rho_v, rho_w)

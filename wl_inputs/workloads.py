@@ -49,6 +49,20 @@ for _i in range(16):
         N=_N, beta=6.0 if _i % 2 == 0 else 10.0, sweeps=200, target=1e-2 if (_i // 2) % 2 == 0 else 1e-3,
         seed=5000 + _i, blocks=_levels(_N), k=8, precision="fp32", nrhs=0)
 
+# Sec. 4's experiments: N = 128 and 256, beta = 3, 6, 10, three seeded
+# configurations each, 2x2 cells down to the N = 16 coarsest grid (4 and 5
+# grids), k_r = k_e = 8, W(4,4) cycles and GMRES(32).  The shift is not fixed
+# here: a run picks eta_min(D) = eta from PAPER_ETAS and uses m = eta - eta0,
+# eta0 = min Re lambda(D_0) of the seeded gauge field (stored in shifts.json).
+PAPER_ETAS = [1e-1, 3e-2, 1e-2, 3e-3, 1e-3]
+for _N in (128, 256):
+    for _bi, _beta in enumerate((3.0, 6.0, 10.0)):
+        for _c in range(3):
+            WORKLOADS["P%d_b%d_c%d" % (_N, _beta, _c)] = dict(
+                N=_N, beta=_beta, sweeps=500, target=None, seed=7000 + 100 * (_N // 128) + 10 * _bi + _c,
+                blocks=[2] * (int(np.log2(_N)) - 4), k=8, precision="fp64", nrhs=1, nu=4, cycle="W",
+                fgmres_m=32, eta_sweep=True)
+
 # tiny cases for parity tests (targets are loose; shifts computed the same way)
 WORKLOADS["T16"] = dict(N=16, beta=6.0, sweeps=50, target=5e-2, seed=11, blocks=[], k=4,
                         precision="fp64", nrhs=1)
@@ -59,7 +73,7 @@ WORKLOADS["T64"] = dict(N=64, beta=6.0, sweeps=100, target=1e-2, seed=13, blocks
 
 
 # solve-cycle parameters (defaults: V(2,2), FGMRES(20), two Gram-Schmidt passes)
-_SOLVE = dict(nu=2, cycle="V", fgmres_m=20, gs_passes=2)
+_SOLVE = dict(nu=2, cycle="V", fgmres_m=20, gs_passes=2, kacz_order=0)
 for _name, _w in WORKLOADS.items():
     for _k, _v in _SOLVE.items():
         _w.setdefault(_k, _v)
@@ -97,14 +111,19 @@ def cached_gauge(N, beta, sweeps, seed):
     return U
 
 
-def workload(name: str, with_gauge: bool = True):
-    """Return a dict with the workload parameters, its shift m (if computed)
-    and, optionally, the gauge field U[2][N][N]."""
+def workload(name: str, with_gauge: bool = True, eta=None):
+    """Return a dict with the workload parameters, its shift m (if computed;
+    with eta, the shift that makes eta_min(D) = eta) and, optionally, the
+    gauge field U[2][N][N]."""
     w = dict(WORKLOADS[name])
     w["name"] = name
     w["levels"] = len(w["blocks"]) + 1
     sh = _shifts().get(name)
-    w["m"] = None if sh is None else float(sh["m"])
+    w["m"] = None if sh is None or sh.get("m") is None else float(sh["m"])
+    w["eta0"] = None if sh is None or sh.get("eta0") is None else float(sh["eta0"])
+    if eta is not None:   # eta_min(D) = eta: m = eta - min Re lambda(D_0)
+        w["m"] = None if w["eta0"] is None else float(eta) - w["eta0"]
+        w["eta"] = float(eta)
     if with_gauge:
         w["U"] = cached_gauge(w["N"], w["beta"], w["sweeps"], w["seed"])
     return w
