@@ -43,6 +43,18 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=8.0)
+    ap.add_argument("--serve-configs", type=int, default=4,
+                    help="resident configurations S00.. of the serving mix (16 = all five lattice sizes)")
+    ap.add_argument("--serve-hbm-gb", type=float, default=64.0, help="device-memory budget of the server")
+    ap.add_argument("--nrhs", type=int, default=0, help="override the workload's RHS per step")
+    ap.add_argument("--kacz-order", type=int, default=-1, help="override the Kaczmarz ordering (0 or 1)")
+    ap.add_argument("--study", default="", choices=["", "rho"],
+                    help="rho: Sec. 4's experiment (rho, GMRES(32) iterations, residual and error "
+                         "across an eta_min sweep) instead of the benchmark; one JSON line per case")
+    ap.add_argument("--study-sizes", default="128,256")
+    ap.add_argument("--study-configs", type=int, default=3)
+    ap.add_argument("--study-setup", default="W", choices=["W", "superV"],
+                    help="setup cycles of the study: W (Sec. 4.1) or super-V (Sec. 4.2)")
     return ap.parse_args()
 
 
@@ -156,7 +168,9 @@ def run_gb300(args, rank, world, local_rank):
     w = workload(args.workload)
     if w["m"] is None:
         raise SystemExit("no shift for workload %s (run oracle/make_shifts.py)" % args.workload)
-    N, nrhs = w["N"], max(1, w["nrhs"])
+    if args.kacz_order >= 0:
+        w["kacz_order"] = args.kacz_order
+    N, nrhs = w["N"], max(1, args.nrhs or w["nrhs"])
     prec = {"fp64": W.WL_FP64, "fp32": W.WL_FP32, "bf16": W.WL_FP32_BF16}[w["precision"]]
 
     # CPU baseline leg: the oracle, started before the first GPU call
@@ -170,7 +184,8 @@ def run_gb300(args, rank, world, local_rank):
         p = W.amg_params_default(k_r=w["k"], k_e=w["k"], seed=w["seed"], zero_guess=1,
                                  precision=precision, nu_pre=w["nu"], nu_post=w["nu"],
                                  cycle=W.WL_CYCLE_W if w["cycle"] == "W" else W.WL_CYCLE_V,
-                                 fgmres_m=w["fgmres_m"], gs_passes=w["gs_passes"])
+                                 fgmres_m=w["fgmres_m"], gs_passes=w["gs_passes"],
+                                 kacz_order=w["kacz_order"])
         p.levels = len(w["blocks"]) + 1
         for l, b in enumerate(w["blocks"]):
             p.block[l] = b
@@ -340,14 +355,26 @@ def run_gb300(args, rank, world, local_rank):
     return out
 
 
+def _cache_gauge(name):
+    from wl_inputs import workload
+    workload(name)
+    return name
+
+
 def run_serving(args, rank, dev, W, torch):
     """Continuous-batching serving over resident hierarchies of several lattice
     sizes: a closed-loop burst measures capacity, then a seeded Poisson stream
     of 1-32 RHS requests arrives at 70% of it for --serve-seconds."""
     import numpy as np
     from wl_inputs import workload, rhs_batch, uniform01
-    names = ["S00", "S01", "S02", "S03"]  # 64, 128, 256, 512 lattices, beta 6/10, targets 1e-2/1e-3
-    srv = W.srv_create(64 << 30, 32)
+    # S00..S15 cycle over 64, 128, 256, 512, 1024 lattices, beta 6/10, targets 1e-2/1e-3
+    names = ["S%02d" % i for i in range(args.serve_configs)]
+    # generate (and cache) the gauge fields in parallel host processes; spawn,
+    # since this process already holds a CUDA context
+    import multiprocessing as mp
+    with mp.get_context("spawn").Pool(max(1, min(len(names), os.cpu_count() or 1))) as pool:
+        pool.map(_cache_gauge, names)
+    srv = W.srv_create(int(args.serve_hbm_gb * (1 << 30)), 32)
     cfgs, pools = [], []
     for nm in names:
         w = workload(nm)
@@ -362,6 +389,11 @@ def run_serving(args, rank, dev, W, torch):
         amg = W.amg_setup(op, p)
         cfgs.append((nm, w, W.srv_add(srv, amg)))
         pools.append(torch.from_numpy(rhs_batch(w["N"], 32, 7000 + len(pools))).to(dev))
+    slots, reserved = [], 0
+    for _, _, cid in cfgs:
+        n_, b_ = W.srv_info(srv, cid)
+        slots.append(n_)
+        reserved += b_
     W.srv_start(srv)
     seed = 9000 + rank
 
@@ -410,7 +442,8 @@ def run_serving(args, rank, dev, W, torch):
             "closed-loop capacity)" % (rate, cap), "p50_ms": round(lats[len(lats) // 2], 2),
             "p99_ms": round(lats[min(len(lats) - 1, int(0.99 * len(lats)))], 2),
             "solves_per_s": round(solved / wall, 2), "true_relres_max": worst,
-            "cycle": "V(4,4) FP32, FGMRES(20) FP64, 1 Gram-Schmidt pass", "slots_per_config": 32}
+            "cycle": "V(4,4) FP32, FGMRES(20) FP64, 1 Gram-Schmidt pass", "slots_per_config": slots,
+            "hbm_budget_gb": args.serve_hbm_gb, "hbm_reserved_gb": round(reserved / (1 << 30), 2)}
 
 
 def run_reference(args, rank, world):
@@ -438,6 +471,80 @@ def run_reference(args, rank, world):
                     "d2h_bytes_per_step": 0}}
 
 
+def run_study_rho(args):
+    """Sec. 4's experiment on seeded stand-ins for its gauge ensembles:
+    N = 128 / 256, beta = 3 / 6 / 10, up to three configurations each, 2x2
+    cells down to N = 16, k_r = k_e = 8, setup mu = 10 / 5 with the W(4,4)
+    adaptive step, FP64 W(4,4) solve cycle.  For every eta_min(D) of the
+    sweep: rho of the stand-alone cycle (to 1e-8 or 100 iterations), the
+    GMRES(32) iterations to a 1e-8 relative residual, that residual, and the
+    relative error against a 1e-13 solve of the same hierarchy."""
+    import numpy as np
+    import torch
+    from paper_1308_5992_gb300 import wilson_amg as W
+    from wl_inputs import workload, rhs_batch, cgauss
+    from wl_inputs.workloads import WORKLOADS, PAPER_ETAS
+    dev = torch.device("cuda", 0)
+    sizes = [int(v) for v in args.study_sizes.split(",") if v]
+    rows = []
+    for name, spec in WORKLOADS.items():
+        if not spec.get("eta_sweep") or spec["N"] not in sizes or int(name[-1]) >= args.study_configs:
+            continue
+        w0 = workload(name)
+        if w0["eta0"] is None:
+            print(json.dumps({"study": "rho", "workload": name, "unavailable": "no eta0 in shifts.json"}))
+            continue
+        Ud = torch.from_numpy(w0["U"]).to(dev)
+        N = w0["N"]
+        n = N * N  # level-0 unknowns (N^2 / 2 sites, 2 spins)
+        for eta in PAPER_ETAS:
+            w = workload(name, with_gauge=False, eta=eta)
+            op = W.wilson_create(Ud, N, w["m"])
+            p = W.amg_params_default(k_r=w["k"], k_e=w["k"], seed=w["seed"], zero_guess=1, precision=W.WL_FP64,
+                                     nu_pre=4, nu_post=4, cycle=W.WL_CYCLE_W, fgmres_m=32, max_restarts=20,
+                                     setup_cycle=1 if args.study_setup == "superV" else 0)
+            p.levels = len(w["blocks"]) + 1
+            for l, b in enumerate(w["blocks"]):
+                p.block[l] = b
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            amg = W.amg_setup(op, p)
+            torch.cuda.synchronize()
+            setup_s = time.perf_counter() - t0
+            x0 = torch.from_numpy(cgauss(w["seed"], 77, n)[None, :]).to(dev)
+            xe = torch.zeros_like(x0)
+            rc_r, rho, nu, _ = W.amg_rho(amg, x0, xe, 1, 1e-8, 100)
+            b = torch.from_numpy(rhs_batch(N, 1, w["seed"])).to(dev)
+            psi = torch.zeros_like(b)
+            rc, info = W.amg_solve(amg, b, psi, 1, 1e-8)
+            ref = torch.zeros_like(b)
+            rc2, info2 = W.amg_solve(amg, b, ref, 1, 1e-13)
+            err = float(torch.linalg.vector_norm(psi - ref) / torch.linalg.vector_norm(ref))
+            row = {"study": "rho", "setup": args.study_setup, "workload": name, "N": N, "beta": w["beta"],
+                   "eta": eta, "m": w["m"],
+                   "rho": float(rho[0]), "rho_iters": int(nu[0]), "rho_met": rc_r == W.WL_OK,
+                   "gmres_iters": info[0]["iters"], "restarts": info[0]["restarts"],
+                   "relres": info[0]["true_relres"], "relerr": err, "ref_relres": info2[0]["true_relres"],
+                   "setup_s": round(setup_s, 3)}
+            rows.append(row)
+            print(json.dumps(row), flush=True)
+            amg.close()
+            op.close()
+    summary = {}
+    for r in rows:
+        key = "N%d_beta%g" % (r["N"], r["beta"])
+        summary.setdefault(key, []).append(r)
+    out = {}
+    for key, rs in summary.items():
+        rh = [r["rho"] for r in rs]
+        out[key] = {"cases": len(rs), "rho_median": round(float(np.median(rh)), 3),
+                    "rho_max": round(max(rh), 3), "rho_above_0.6": sum(v > 0.6 for v in rh),
+                    "gmres_iters_max": max(r["gmres_iters"] for r in rs),
+                    "restarted": sum(r["restarts"] > 1 for r in rs),
+                    "err_over_res_max": round(max(r["relerr"] / max(r["relres"], 1e-300) for r in rs), 1)}
+    print(json.dumps({"study": "rho", "setup": args.study_setup, "summary": out}))
+
+
 def main():
     faulthandler.enable()
     args = parse()
@@ -448,6 +555,10 @@ def main():
         out = run_reference(args, rank, world)
         if out is not None:
             print(json.dumps(out))
+        return
+    if args.study == "rho":
+        if rank == 0:
+            run_study_rho(args)
         return
     if world > 1:
         import torch

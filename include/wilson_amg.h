@@ -78,9 +78,28 @@ typedef struct {
   unsigned long long seed;/* seed of the setup's random test vectors                */
   int gs_passes;          /* Gram-Schmidt passes (1 = CGS, 2 = CGS with one reorth.) */
   int zero_guess;         /* 1: amg_solve ignores the contents of x                 */
-  int sweep_kernel;       /* Kaczmarz launch form: 0 = automatic, 1 = one launch
-                             per colour, 2 = one cooperative launch per level visit
-                             (same arithmetic and order; results agree to rounding) */
+  int sweep_kernel;       /* Kaczmarz launch form: 0 = autotuned (before the first
+                             cycle of a batch width is captured, every form of one
+                             sweep is timed on each level and the fastest kept; until
+                             then, or for per-step calls, a heuristic), 1 = one launch
+                             per colour, 2 = one cooperative launch per level visit.
+                             Every form computes the same numbers in the same order. */
+  int kacz_order;         /* Kaczmarz ordering: 0 = 16 colours (a mod 4, b mod 4) over the
+                             whole grid; 1 = tile-coloured: 8x8 tiles in (a, b) with four
+                             tile colours, the 16 colours inside each tile (grids with
+                             N >= 64; smaller grids keep order 0).  Both are forward
+                             sweeps over a permutation of the variables (Sec. 3.1). */
+  int arnoldi_matvec;     /* precision of the Arnoldi matvec w = Dhat z_j inside a
+                             restart cycle: 0 = FP64, 1 = the cycle precision when it is
+                             FP32 or BF16 (FP32 arithmetic, result widened to FP64 for
+                             the Gram-Schmidt).  The true residual at every restart
+                             stays FP64, so the accuracy is unchanged; a cycle whose
+                             Arnoldi relation holds to FP32 rounding may need one more
+                             restart. */
+  int setup_cycle;        /* bootstrap setup cycles: 0 = W-cycle (Fig. 3.2), 1 = super-V
+                             (Sec. 4.2: each grid visited once, mu 2^l relaxations
+                             before and after the coarse visit on grid l, one coarsest
+                             eigensolve per setup cycle) */
 } amg_params;
 
 typedef struct {
@@ -163,6 +182,20 @@ int amg_cycle(wl_amg *amg, const void *f, void *x, int nrhs, int prec);
 /* FGMRES on Dhat x = bhat (level-0 vectors, x = initial guess); info host
  * array [nrhs]. */
 int amg_fgmres(wl_amg *amg, const void *bhat, void *x, int nrhs, double tol, wl_info *info);
+/* Sec. 4's convergence estimate of the stand-alone solver: the configured
+ * cycle (V or W, nu_pre / nu_post, precision) used as the stationary
+ * iteration x <- x + M(0 - Dhat x) on Dhat x = 0, Dhat in FP64, so the
+ * iterate is the error e.  From e^0 = x0 (level-0 vectors [nrhs][L^2/2][2],
+ * device) it runs until |e^nu| <= tol |e^0| for every right-hand side or
+ * nu = maxit; rho[r] = |e^nu| / |e^(nu-1)| at the right-hand side's own
+ * stopping nu (iters[r]).  rho, iters: host [nrhs]; hist: host
+ * [nrhs][maxit + 1] or NULL, |e^k| for k <= iters[r] (rest untouched).
+ * x (device, same layout) receives the error after the batch's last
+ * iteration.  Returns WL_OK if every right-hand side met tol,
+ * WL_NOT_CONVERGED otherwise; WL_EINVAL for nrhs outside 1..256, tol < 0
+ * or maxit < 1; WL_NAN if a norm became non-finite. */
+int amg_rho(wl_amg *amg, const void *x0, void *x, int nrhs, double tol, int maxit, double *rho, int *iters,
+            double *hist);
 
 /* y = Dhat x in FP64 with no device allocation (the paper has no counterpart;
  * this is a service of the library).  For callers that cannot allocate device
@@ -203,10 +236,15 @@ int wl_dhat_apply_noalloc(wl_op *op, const void *x, void *y, int nrhs);
  * untouched by the caller until srv_poll reports the request done.  A
  * hierarchy added to a server must not be used by other calls while the
  * server runs.  srv_poll's latency is host wall time from srv_submit to the
- * retirement of the request's last right-hand side. */
+ * retirement of the request's last right-hand side.  srv_start captures the
+ * cycle graph of every packed width (1 .. slots) of every hierarchy before
+ * the workers start, so no stream capture runs while clients work and
+ * clients may synchronise the whole device. */
 typedef struct wl_server wl_server;
 int srv_create(unsigned long long hbm_budget_bytes, int max_slots_per_config, wl_server **out);
 int srv_add(wl_server *srv, wl_amg *amg, int *cfg_id);
+/* Slots reserved for configuration cfg and the device bytes they hold. */
+int srv_info(wl_server *srv, int cfg, int *slots, unsigned long long *bytes);
 int srv_start(wl_server *srv);
 int srv_submit(wl_server *srv, int cfg, const void *b, void *x, int nrhs, double tol, long long *req_id);
 int srv_poll(wl_server *srv, long long req_id, int *done, wl_info *info /* host [nrhs] */, double *latency_ms);
@@ -222,7 +260,8 @@ enum {
   WL_K_PROLONG = 4,   /* P from level + 1 to `level`                          */
   WL_K_COARSEST = 5,  /* dense FP64 coarsest solve                            */
   WL_K_GS_DOT = 6,    /* FP64 multi-dot of 11 Krylov vectors (Gram-Schmidt)   */
-  WL_K_GS_AXPY = 7    /* FP64 multi-axpy of 11 Krylov vectors                 */
+  WL_K_GS_AXPY = 7,   /* FP64 multi-axpy of 11 Krylov vectors                 */
+  WL_K_KACZ_TILE = 8  /* one tile-colour launch (a quarter of a tile-coloured sweep) on `level` */
 };
 /* Average duration (host output, milliseconds) of one launch of kernel
  * family `kind` in the launch configuration the solver uses for `nrhs`
@@ -231,6 +270,13 @@ enum {
  * hierarchy's own work buffers (their contents are not preserved).
  * Errors: WL_EINVAL. */
 int wl_time_kernel(wl_amg *amg, int kind, int level, int nrhs, int prec, int reps, double *avg_ms);
+/* Kaczmarz launch form used on `level` (not the coarsest) for `nrhs`
+ * right-hand sides in precision `prec`: form 0 = one launch per colour,
+ * 1 = cooperative launch with *param blocks, 2 = tile-coloured kernel with
+ * right-hand-side chunk *param; *us = the autotuner's measured time of one
+ * sweep in microseconds, 0 when the form was not measured (explicit
+ * sweep_kernel, or no cycle of that width yet).  Errors: WL_EINVAL. */
+int amg_sweep_form(wl_amg *amg, int level, int nrhs, int prec, int *form, int *param, float *us);
 /* Number of kernels this library has launched in this process (a captured
  * graph counts each of its kernel nodes at every replay). */
 long long wl_launch_count(void);

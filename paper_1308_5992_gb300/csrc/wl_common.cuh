@@ -56,6 +56,14 @@ __host__ __device__ __forceinline__ void cfma(cx<T> &acc, cx<T> a, cx<T> b) {
   acc.im = fma(a.re, b.im, acc.im);
   acc.im = fma(a.im, b.re, acc.im);
 }
+// subtract a * b from acc (the negations fold into the FMAs)
+template <typename T>
+__host__ __device__ __forceinline__ void cfms(cx<T> &acc, cx<T> a, cx<T> b) {
+  acc.re = fma(-a.re, b.re, acc.re);
+  acc.re = fma(a.im, b.im, acc.re);
+  acc.im = fma(-a.re, b.im, acc.im);
+  acc.im = fma(-a.im, b.re, acc.im);
+}
 // accumulate conj(a) * b into acc
 template <typename T>
 __host__ __device__ __forceinline__ void cfmac(cx<T> &acc, cx<T> a, cx<T> b) {
@@ -68,6 +76,32 @@ __host__ __device__ __forceinline__ void cfmac(cx<T> &acc, cx<T> a, cx<T> b) {
 template <typename To, typename From>
 __host__ __device__ __forceinline__ cx<To> ccast(cx<From> a) {
   return mk((To)a.re, (To)a.im);
+}
+
+// Exact float -> double widening on the integer pipes: for a normal float
+// the double has the same sign, the exponent rebiased by 1023 - 127 = 896
+// and the 23 mantissa bits shifted up by 29.  Zero, subnormal, inf and NaN
+// take the hardware conversion.  (On this GPU the hardware conversion runs
+// on the FP64 pipe, which FP64-bound kernels are short of.)
+__device__ __forceinline__ double f2d(float f) {
+  unsigned u = __float_as_uint(f);
+  unsigned e = (u >> 23) & 0xffu;
+  if (e == 0u || e == 0xffu) return (double)f;
+  unsigned long long d = ((unsigned long long)(u & 0x80000000u) << 32) |
+                         ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)(u & 0x7fffffu) << 29);
+  return __longlong_as_double((long long)d);
+}
+template <typename To, typename From>
+struct Widen {
+  __device__ __forceinline__ static cx<To> get(cx<From> a) { return ccast<To>(a); }
+};
+template <>
+struct Widen<double, float> {
+  __device__ __forceinline__ static cx<double> get(cx<float> a) { return mk(f2d(a.re), f2d(a.im)); }
+};
+template <typename To, typename From>
+__device__ __forceinline__ cx<To> widen(cx<From> a) {
+  return Widen<To, From>::get(a);
 }
 
 // storage of operator coefficients: complex double, complex float or bf16 pair
@@ -173,12 +207,22 @@ struct LevelOps {
   DBuf P;    // interpolation weights to the next level [n][2][4]
 };
 
+// launch form of a Kaczmarz sweep on one level, chosen by the autotuner
+// (measured) or by the heuristic: form 0 = one launch per colour, 1 = one
+// cooperative launch for all colours (param = blocks), 2 = tile-coloured
+// kernel (param = right-hand-side chunk R)
+struct KTune {
+  int nrhs, prec, form, param;
+  float us;  // measured time of one sweep (0 if not measured)
+};
+
 struct Level {
   int N, B, n;  // lattice side, cell size to the next level (0 at coarsest), sites
   Geo geo;
   LevelOps op64, op32, opbf;  // FP64 master, FP32 copy, BF16 copy (den in FP32)
   // cycle work vectors, [n][2][nrhs_cap] in the cycle precision
   DBuf x, r, f, t;
+  std::vector<KTune> tune;    // autotuned sweep forms per (nrhs, precision)
 };
 
 struct wl_amg {
@@ -222,13 +266,18 @@ int ensure_workspace(wl_amg *a, int nrhs, int prec);
 int level_ops_build_copies(wl_amg *a);
 int coarsest_invert(wl_amg *a);
 int cycle_run(wl_amg *a, int nrhs, int prec, cudaStream_t s);  // lev[0].f -> lev[0].x
+int cycle_prepare(wl_amg *a, int nrhs, int prec, cudaStream_t s, const wl_amg::G **out);  // capture only
 int cycle_direct(wl_amg *a, int nrhs, int prec, cudaStream_t s);
 int dhat_apply_dev(wl_op *op, const void *x, int x_is_f32, zd *y, int nrhs, cudaStream_t s);
+int dhat_apply_dev32(wl_op *op, const zf *x, zd *y, int nrhs, cudaStream_t s);
 int stencil_apply(wl_amg *a, int l, int prec, const void *x, void *y, const void *f, int nrhs,
                   cudaStream_t s);
 int kaczmarz_sweeps(wl_amg *a, int l, int prec, void *x, void *r, int nrhs, int sweeps,
                     cudaStream_t s);
 int kaczmarz_colour(wl_amg *a, int l, int prec, void *x, void *r, int nrhs, int c, cudaStream_t s);
+int kaczmarz_tile(wl_amg *a, int l, int prec, void *x, void *r, int nrhs, int tc, cudaStream_t s, int R = 0);
+int autotune_sweeps(wl_amg *a, int nrhs, int prec, cudaStream_t s);  // every level but the coarsest
+KTune sweep_form_of(wl_amg *a, int l, int prec, int nrhs);
 int restrict_op(wl_amg *a, int l, int prec, const void *r, void *fc, int nrhs, cudaStream_t s);
 int prolong_op(wl_amg *a, int l, int prec, const void *e, void *x, int nrhs, cudaStream_t s);
 int coarsest_apply(wl_amg *a, int prec, const void *f, void *x, int nrhs, cudaStream_t s);

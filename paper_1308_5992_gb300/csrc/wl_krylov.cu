@@ -25,12 +25,13 @@ int resolve_levels(int N, amg_params *p, int *Nl);
 struct KS {
   int m, nrhs;
   zd *hcol;    // [nrhs][m+1] accumulated column of H
-  zd *hpass;   // [nrhs][m+1] coefficients of the current Gram-Schmidt pass
+  zd *hpass;   // [m+1][nrhs] coefficients of the current Gram-Schmidt pass (rhs innermost)
   zd *H;       // [nrhs][m+1][m]
   zd *g;       // [nrhs][m+1]
   zd *cs;      // [nrhs][m]
   double *cc;  // [nrhs][m]
   zd *y;       // [nrhs][m]
+  zd *yT;      // [m][nrhs] the same, rhs innermost
   double *bnorm, *beta, *nrm2, *inv;  // [nrhs]
   int *active, *stop, *jend, *iters;  // [nrhs]
   int *running;                       // [1]
@@ -53,6 +54,7 @@ static KS ks_layout(void *base, int m, int nrhs) {
   k.cs = (zd *)take(sizeof(zd) * nrhs * m);
   k.cc = (double *)take(sizeof(double) * nrhs * m);
   k.y = (zd *)take(sizeof(zd) * nrhs * m);
+  k.yT = (zd *)take(sizeof(zd) * nrhs * m);
   k.bnorm = (double *)take(sizeof(double) * nrhs);
   k.beta = (double *)take(sizeof(double) * nrhs);
   k.nrm2 = (double *)take(sizeof(double) * nrhs);
@@ -119,37 +121,40 @@ __global__ void k_mdot_final(const zd *__restrict__ part, int nblk, int kc, int 
   }
   if (lane) return;
   zd *o = out + (long)r * ostride + k0 + k;
-  if (copy_to) copy_to[(long)r * ostride + k0 + k] = s;
+  if (copy_to) copy_to[(long)(k0 + k) * R + r] = s;  // rhs innermost
   *o = accumulate ? (*o + s) : s;
 }
 
-// w += sign * sum_k V_k * coef[r][k]   (coef row stride cstride); the
+// w += sign * sum_k V_k * coef[k][r]   (coef row stride cstride, rhs
+// innermost so a warp's coefficient loads are contiguous); the
 // k loop is unrolled by 4 with the four loads issued before the FMAs
-template <typename Tv>
+template <typename Tv, int NEG>
 __global__ void __launch_bounds__(256) k_maxpy(const cx<Tv> *__restrict__ V, long vstride, int kc,
-                                               const zd *__restrict__ coef, int cstride, double sign,
-                                               zd *__restrict__ w, long E, int R) {
+                                               const zd *__restrict__ coef, int cstride, zd *__restrict__ w,
+                                               long E, int R) {
   long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= E) return;
   int r = (int)(e % R);
-  const zd *cr = coef + (long)r * cstride;
+  const zd *cr = coef + r;
   zd acc = w[e];
   int k = 0;
   for (; k + 4 <= kc; k += 4) {
     zd v[4], c[4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) v[u] = ccast<double>(V[(k + u) * vstride + e]);
+    for (int u = 0; u < 4; ++u) v[u] = widen<double>(V[(k + u) * vstride + e]);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) c[u] = cr[(long)(k + u) * cstride];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      c[u] = cr[k + u];
-      c[u] = mk(sign * c[u].re, sign * c[u].im);
+      if (NEG) cfms(acc, c[u], v[u]);
+      else cfma(acc, c[u], v[u]);
     }
-#pragma unroll
-    for (int u = 0; u < 4; ++u) cfma(acc, c[u], v[u]);
   }
   for (; k < kc; ++k) {
-    zd c = cr[k];
-    cfma(acc, mk(sign * c.re, sign * c.im), ccast<double>(V[k * vstride + e]));
+    zd c = cr[(long)k * cstride];
+    zd v = widen<double>(V[k * vstride + e]);
+    if (NEG) cfms(acc, c, v);
+    else cfma(acc, c, v);
   }
   w[e] = acc;
 }
@@ -243,6 +248,7 @@ __global__ void k_trisolve(KS k) {
     double dn = cnorm2(d);
     y[i] = (dn > 0) ? mk((s.re * d.re + s.im * d.im) / dn, (s.im * d.re - s.re * d.im) / dn) : mk(0.0, 0.0);
   }
+  for (int i = 0; i < m; ++i) k.yT[(long)i * k.nrhs + r] = y[i];
 }
 
 // start of a cycle: beta = ||r||, inv = active ? 1/beta : 0, g = (beta, 0..)
@@ -388,13 +394,14 @@ int fg_cycle(wl_amg *a, const zd *bnorm_h, zd *xh, int nrhs, double tol, const i
     WL_TRY(cycle_run(a, nrhs, prec, s));
     WL_CUDA(cudaMemcpyAsync(zj, a->lev[0].x.p, zb_ * E, cudaMemcpyDeviceToDevice, s));
     // w = Dhat z_j (FP64)
-    WL_TRY(dhat_apply_dev(op, zj, prec != WL_FP64, w, nrhs, s));
+    if (prec != WL_FP64 && a->prm.arnoldi_matvec == 1) WL_TRY(dhat_apply_dev32(op, (const zf *)zj, w, nrhs, s));
+    else WL_TRY(dhat_apply_dev(op, zj, prec != WL_FP64, w, nrhs, s));
     // Gram-Schmidt against v_0 .. v_j
     k_zero_hcol<<<WL_GRID(nrhs, 128), 128, 0, s>>>(k);
     wl_count_launches(1);
     for (int pass = 0; pass < a->prm.gs_passes; ++pass) {
       WL_TRY(mdots<double>(a, V, vs, j + 1, w, E, nrhs, k.hcol, m + 1, 1, k.hpass, s));
-      k_maxpy<double><<<gE, 256, 0, s>>>(V, vs, j + 1, k.hpass, m + 1, -1.0, w, E, nrhs);
+      k_maxpy<double, 1><<<gE, 256, 0, s>>>(V, vs, j + 1, k.hpass, nrhs, w, E, nrhs);
       wl_count_launches(1);
     }
     zd *tmpc = a->small.as<zd>() + (a->small.bytes / sizeof(zd)) - 2 * (size_t)nrhs - 8;
@@ -419,8 +426,8 @@ int fg_cycle(wl_amg *a, const zd *bnorm_h, zd *xh, int nrhs, double tol, const i
     if (run[0] == 0) break;
   }
   k_trisolve<<<WL_GRID(nrhs, 128), 128, 0, s>>>(k);
-  if (prec == WL_FP64) k_maxpy<double><<<gE, 256, 0, s>>>(a->Z.as<zd>(), vs, jdone, k.y, m, 1.0, xh, E, nrhs);
-  else k_maxpy<float><<<gE, 256, 0, s>>>(a->Z.as<zf>(), vs, jdone, k.y, m, 1.0, xh, E, nrhs);
+  if (prec == WL_FP64) k_maxpy<double, 0><<<gE, 256, 0, s>>>(a->Z.as<zd>(), vs, jdone, k.yT, nrhs, xh, E, nrhs);
+  else k_maxpy<float, 0><<<gE, 256, 0, s>>>(a->Z.as<zf>(), vs, jdone, k.yT, nrhs, xh, E, nrhs);
   wl_count_launches(2);
   WL_CUDA(cudaGetLastError());
   WL_CUDA(cudaMemcpyAsync(iters_out, k.iters, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, s));
@@ -496,6 +503,78 @@ extern "C" int amg_fgmres(wl_amg *a, const void *bhat, void *x, int nrhs, double
   return rc;
 }
 
+// e -= z, z in the cycle precision (widened exactly to double)
+template <typename Tz>
+__global__ void k_sub_inplace(zd *__restrict__ e, const cx<Tz> *__restrict__ z, long E) {
+  long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < E) {
+    zd w = widen<double>(z[i]);
+    e[i].re -= w.re;
+    e[i].im -= w.im;
+  }
+}
+
+// Sec. 4's convergence estimate: the configured cycle as a stationary
+// iteration on Dhat x = 0, e <- e - M(Dhat e), Dhat in FP64, M in the
+// hierarchy's precision; per right-hand side rho = |e^nu| / |e^(nu-1)| at
+// the first nu with |e^nu| <= tol |e^0| or at nu = maxit.
+extern "C" int amg_rho(wl_amg *a, const void *x0, void *x, int nrhs, double tol, int maxit, double *rho,
+                       int *iters, double *hist) {
+  if (!a || !x0 || !x || !rho || !iters || nrhs < 1 || nrhs > MAX_BATCH || !(tol >= 0) || maxit < 1) {
+    wl_set_error("amg_rho: invalid argument (1 <= nrhs <= %d, tol >= 0, maxit >= 1)", MAX_BATCH);
+    return WL_EINVAL;
+  }
+  int prec = a->prm.precision;
+  WL_TRY(wl::enter(a->op));
+  WL_TRY(wl::ensure_workspace(a, nrhs, prec));
+  cudaStream_t s = a->op->stream;
+  int n2 = a->lev[0].n * 2;
+  long E = (long)n2 * nrhs;
+  unsigned gE = WL_GRID(E, 256);
+  zd *e = a->xh.as<zd>(), *w = a->w.as<zd>();
+  WL_TRY(wl::to_internal((const zd *)x0, e, n2, nrhs, WL_FP64, s));
+  std::vector<double> n0(nrhs), prev(nrhs), cur(nrhs);
+  std::vector<int> done(nrhs, 0);
+  WL_TRY(wl::fg_norms(a, e, nrhs, n0.data()));
+  for (int r = 0; r < nrhs; ++r) {
+    prev[r] = n0[r];
+    rho[r] = 0;
+    iters[r] = 0;
+    if (hist) hist[(size_t)r * (maxit + 1)] = n0[r];
+  }
+  int left = nrhs;
+  for (int nu = 1; nu <= maxit && left > 0; ++nu) {
+    WL_TRY(wl::dhat_apply_dev(a->op, e, 0, w, nrhs, s));
+    if (prec == WL_FP64) {
+      WL_CUDA(cudaMemcpyAsync(a->lev[0].f.p, w, sizeof(zd) * E, cudaMemcpyDeviceToDevice, s));
+    } else {
+      k_cast<float, double><<<gE, 256, 0, s>>>(w, a->lev[0].f.as<zf>(), E);
+      wl_count_launches(1);
+    }
+    WL_TRY(wl::cycle_run(a, nrhs, prec, s));
+    if (prec == WL_FP64) k_sub_inplace<double><<<gE, 256, 0, s>>>(e, a->lev[0].x.as<zd>(), E);
+    else k_sub_inplace<float><<<gE, 256, 0, s>>>(e, a->lev[0].x.as<zf>(), E);
+    wl_count_launches(1);
+    WL_CUDA(cudaGetLastError());
+    WL_TRY(wl::fg_norms(a, e, nrhs, cur.data()));
+    for (int r = 0; r < nrhs; ++r) {
+      if (done[r]) continue;
+      if (!std::isfinite(cur[r])) return WL_NAN;
+      rho[r] = prev[r] > 0 ? cur[r] / prev[r] : 0;
+      iters[r] = nu;
+      if (hist) hist[(size_t)r * (maxit + 1) + nu] = cur[r];
+      prev[r] = cur[r];
+      if (cur[r] <= tol * n0[r]) {
+        done[r] = 1;
+        --left;
+      }
+    }
+  }
+  WL_TRY(wl::from_internal(e, (zd *)x, n2, nrhs, WL_FP64, s));
+  WL_CUDA(cudaStreamSynchronize(s));
+  return left ? WL_NOT_CONVERGED : WL_OK;
+}
+
 extern "C" int amg_solve(wl_amg *a, const void *b, void *x, int nrhs, double tol, wl_info *info) {
   if (!a || !b || !x || nrhs < 1 || !(tol > 0)) {
     wl_set_error("amg_solve: invalid argument");
@@ -528,8 +607,9 @@ extern "C" int amg_solve(wl_amg *a, const void *b, void *x, int nrhs, double tol
 // ------------------------------------------------------------ instrumentation
 extern "C" int wl_time_kernel(wl_amg *a, int kind, int level, int nrhs, int prec, int reps, double *avg_ms) {
   if (!a || !avg_ms || nrhs < 1 || nrhs > MAX_BATCH || reps < 1 || level < 0 || level >= a->L ||
-      (prec != WL_FP64 && prec != WL_FP32 && prec != WL_FP32_BF16) || kind < WL_K_DHAT || kind > WL_K_GS_AXPY ||
-      ((kind == WL_K_KACZ || kind == WL_K_STENCIL || kind == WL_K_RESTRICT || kind == WL_K_PROLONG) &&
+      (prec != WL_FP64 && prec != WL_FP32 && prec != WL_FP32_BF16) || kind < WL_K_DHAT || kind > WL_K_KACZ_TILE ||
+      ((kind == WL_K_KACZ || kind == WL_K_STENCIL || kind == WL_K_RESTRICT || kind == WL_K_PROLONG ||
+        kind == WL_K_KACZ_TILE) &&
        level == a->L - 1)) {
     wl_set_error("wl_time_kernel: invalid argument");
     return WL_EINVAL;
@@ -546,6 +626,7 @@ extern "C" int wl_time_kernel(wl_amg *a, int kind, int level, int nrhs, int prec
     switch (kind) {
       case WL_K_DHAT: return wl::dhat_apply_dev(a->op, a->Z.p, prec != WL_FP64, a->w.as<zd>(), nrhs, s);
       case WL_K_KACZ: return wl::kaczmarz_colour(a, level, prec, L.x.p, L.r.p, nrhs, rep & 15, s);
+      case WL_K_KACZ_TILE: return wl::kaczmarz_tile(a, level, prec, L.x.p, L.r.p, nrhs, rep & 3, s);
       case WL_K_STENCIL: return wl::stencil_apply(a, level, prec, L.x.p, L.r.p, L.f.p, nrhs, s);
       case WL_K_RESTRICT: return wl::restrict_op(a, level, prec, L.r.p, a->lev[level + 1].f.p, nrhs, s);
       case WL_K_PROLONG: return wl::prolong_op(a, level, prec, a->lev[level + 1].x.p, L.x.p, nrhs, s);
@@ -554,8 +635,8 @@ extern "C" int wl_time_kernel(wl_amg *a, int kind, int level, int nrhs, int prec
       case WL_K_GS_DOT:
         return wl::mdots<double>(a, a->V.as<zd>(), E, kc, a->w.as<zd>(), E, nrhs, k.hcol, m + 1, 0, k.hpass, s);
       default:
-        k_maxpy<double><<<WL_GRID(E, 256), 256, 0, s>>>(a->V.as<zd>(), E, kc, k.hpass, m + 1, -1.0, a->w.as<zd>(), E,
-                                                         nrhs);
+        k_maxpy<double, 1><<<WL_GRID(E, 256), 256, 0, s>>>(a->V.as<zd>(), E, kc, k.hpass, nrhs, a->w.as<zd>(), E,
+                                                            nrhs);
         wl_count_launches(1);
         return WL_OK;
     }

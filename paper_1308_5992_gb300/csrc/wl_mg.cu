@@ -63,6 +63,17 @@ __device__ __forceinline__ int kacz_site(const Geo &g, int colour, int q, int &p
   return g.idx(px, py);
 }
 
+// rv -= g sv conj(a) with g = +1 or -1: the products fold into four FMAs
+// (sv conj(a) = (sv.re a.re + sv.im a.im) + i (sv.im a.re - sv.re a.im))
+template <typename T>
+__device__ __forceinline__ void r_sub(cx<T> &rv, T g, cx<T> sv, cx<T> a) {
+  T sr = g * sv.re, si = g * sv.im;  // exact: g = +-1
+  rv.re = fma(-sr, a.re, rv.re);
+  rv.re = fma(-si, a.im, rv.re);
+  rv.im = fma(-si, a.re, rv.im);
+  rv.im = fma(sr, a.im, rv.im);
+}
+
 // one (site, right-hand side) item, one thread
 template <typename T, typename S>
 __device__ __forceinline__ void kacz_item(const Geo &g, int colour, int q, int rh, const S *__restrict__ A,
@@ -101,9 +112,7 @@ __device__ __forceinline__ void kacz_item(const Geo &g, int colour, int q, int r
 #pragma unroll
       for (int s = 0; s < 2; ++s) {
         cx<T> a_ = ld<T>(Ah + d * 4 + t * 2 + s);
-        T gg = (s == t) ? (T)1 : (T)-1;  // g_s g_t
-        cx<T> p = sv * cconj(a_);
-        rv[d][s] = mk<T>(rv[d][s].re - gg * p.re, rv[d][s].im - gg * p.im);
+        r_sub(rv[d][s], (s == t) ? (T)1 : (T)-1, sv, a_);  // g_s g_t
       }
     }
   }
@@ -143,9 +152,7 @@ __device__ __forceinline__ void kacz_site_warp(const Geo &g, int colour, int q, 
     T sc = omega / den[2 * h + t];
     if (t) sc = -sc;
     cx<T> sv = sc * num;
-    T gg = (s == t) ? (T)1 : (T)-1;
-    cx<T> p = sv * cconj(a_);
-    rv = mk<T>(rv.re - gg * p.re, rv.im - gg * p.im);
+    r_sub(rv, (s == t) ? (T)1 : (T)-1, sv, a_);
     if (lane == 0) {
       long xo = (long)h * 2 + t;
       x[xo] = x[xo] + sv;
@@ -197,6 +204,270 @@ __global__ void __launch_bounds__(128) k_kacz_coop(Geo g, int sweeps, int wpi, c
       }
       grid.sync();
     }
+}
+
+// Tile-coloured sweep (reading of Sec. 3.1's parallel ordering, the
+// oracle's OR_ORDER_TILE): 8 x 8 tiles in (a, b), tile colour
+// (ta mod 2) + 2 (tb mod 2); one launch per tile colour.  A block owns one
+// tile and a chunk of right-hand sides: the stencil rows of the tile and r of
+// the tile plus its one-site halo are staged in shared memory, the 16 site
+// colours run in turn (4 sites each), x of a site is updated in place in
+// global memory when its colour comes up (each site is visited once per
+// launch), and r is written back.  Same-colour tiles touch disjoint
+// (tile + halo) regions, so the write-back does not race.
+#define KT 8            // tile side
+#define KTH (KT + 2)    // with halo
+// asynchronous global -> shared copies (cp.async): the staging loads of a
+// block are all in flight at once and waited for together
+__device__ __forceinline__ void cp_async(void *smem, const void *gmem, int bytes) {
+  unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  if (bytes == 16) asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem));
+  else if (bytes == 8) asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem));
+  else asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::); }
+
+// tile origin of block b for tile colour tc
+__device__ __forceinline__ void tile_origin(const Geo &g, int tc, int &A0, int &B0) {
+  int nb4 = g.N / (4 * KT);  // tiles of one colour along b
+  A0 = ((tc & 1) + 2 * (blockIdx.x / nb4)) * KT;
+  B0 = ((tc >> 1) + 2 * (blockIdx.x % nb4)) * KT;
+}
+
+// stencil rows and denominators of the tile's 64 sites -> shared memory
+template <typename T, typename S>
+__device__ __forceinline__ void tile_stage_rows(const Geo &g, int A0, int B0, const S *__restrict__ A,
+                                                const T *__restrict__ den, S *As, T *ds) {
+  const int rowc = 36 * (int)sizeof(S) / 16;  // a row is 36 sizeof(S) bytes, a multiple of 16
+  for (int e = threadIdx.x; e < KT * KT * rowc; e += blockDim.x) {
+    int ks = e / rowc, c16 = e - ks * rowc;
+    int a = A0 + ks / KT, b = B0 + ks % KT;
+    long h = g.idx(a + b, a - b);
+    cp_async((char *)(As + ks * 36) + 16 * c16, (const char *)(A + h * 36) + 16 * c16, 16);
+  }
+  for (int e = threadIdx.x; e < KT * KT * 2; e += blockDim.x) {
+    int ks = e >> 1;
+    int a = A0 + ks / KT, b = B0 + ks % KT;
+    long h = g.idx(a + b, a - b);
+    cp_async(ds + e, den + 2 * h + (e & 1), (int)sizeof(T));
+  }
+}
+
+// Several right-hand sides: a block of 4 R threads, thread (k, q) owns site k
+// of the current colour step and right-hand side r0 + q.  Shared memory: A
+// rows [64][36], den [64][2], r of tile + halo [100][2][R].  vec: r rows
+// start on 16-byte boundaries (16-byte copies), else one complex per copy.
+template <typename T, typename S, int R>
+__global__ void __launch_bounds__(4 * R) k_kacz_tile(Geo g, int tc, const S *__restrict__ A,
+                                                     const T *__restrict__ den, cx<T> *__restrict__ x,
+                                                     cx<T> *__restrict__ r, int nrhs, int vec, T omega) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  S *As = (S *)sm_raw;
+  T *ds = (T *)(As + KT * KT * 36);
+  cx<T> *rs = (cx<T> *)(ds + KT * KT * 2);
+  constexpr int NT = 4 * R;
+  constexpr int E = 16 / (int)sizeof(cx<T>);  // complex numbers per 16-byte copy
+  constexpr int CPR = R / E;                   // 16-byte pieces per staged row
+  int A0, B0;
+  tile_origin(g, tc, A0, B0);
+  int r0 = blockIdx.y * R;
+  int Rc = min(R, nrhs - r0);
+  int tid = threadIdx.x;
+  tile_stage_rows<T, S>(g, A0, B0, A, den, As, ds);
+  if (vec) {
+    for (int e = tid; e < KTH * KTH * 2 * CPR; e += NT) {
+      int c = e % CPR, row = e / CPR, ls = row >> 1;
+      if (c * E >= Rc) continue;
+      int a = A0 + ls / KTH - 1, b = B0 + ls % KTH - 1;
+      long h = g.idx(a + b, a - b);
+      cp_async(rs + row * R + c * E, r + (h * 2 + (row & 1)) * nrhs + r0 + c * E, 16);
+    }
+  } else {
+    for (int e = tid; e < KTH * KTH * 2 * R; e += NT) {
+      int q = e % R, row = e / R, ls = row >> 1;
+      if (q >= Rc) continue;
+      int a = A0 + ls / KTH - 1, b = B0 + ls % KTH - 1;
+      long h = g.idx(a + b, a - b);
+      cp_async(rs + e, r + (h * 2 + (row & 1)) * nrhs + r0 + q, (int)sizeof(cx<T>));
+    }
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  const int k = tid / R, q = tid % R;
+  const bool act = q < Rc;
+  // thread (k, q) visits quadrant k of the tile, one site per colour step;
+  // x of the site four steps ahead is loaded while the current step runs
+  // (a ring of four), so the HBM latency of x is off the step's critical path
+  auto x_at = [&](int c) -> long {
+    int i = (c >> 2) + 4 * (k >> 1), j = (c & 3) + 4 * (k & 1);
+    return (long)g.idx(A0 + i + B0 + j, A0 + i - B0 - j) * 2 * nrhs + r0 + q;
+  };
+  cx<T> xp[4][2];
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+    if (act) {
+      long xo = x_at(u);
+      xp[u][0] = x[xo];
+      xp[u][1] = x[xo + nrhs];
+    }
+  for (int c0 = 0; c0 < 16; c0 += 4) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int c = c0 + u;
+      int i = (c >> 2) + 4 * (k >> 1), j = (c & 3) + 4 * (k & 1);
+      if (act) {
+        int ks = i * KT + j;
+        const S *Ah = As + ks * 36;
+        cx<T> rv[9][2];
+#pragma unroll
+        for (int d = 0; d < 9; ++d) {
+          int ls = (i + d / 3) * KTH + (j + d % 3);  // (i + da + 1, j + db + 1)
+          rv[d][0] = rs[(ls * 2) * R + q];
+          rv[d][1] = rs[(ls * 2 + 1) * R + q];
+        }
+        cx<T> sv[2];
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+          cx<T> a_[9][2];
+#pragma unroll
+          for (int d = 0; d < 9; ++d) {
+            a_[d][0] = ld<T>(Ah + d * 4 + t * 2 + 0);
+            a_[d][1] = ld<T>(Ah + d * 4 + t * 2 + 1);
+          }
+          cx<T> num = mk<T>(0, 0);
+#pragma unroll
+          for (int d = 0; d < 9; ++d) {
+            cfma(num, a_[d][0], rv[d][0]);
+            cfma(num, mk<T>(-a_[d][1].re, -a_[d][1].im), rv[d][1]);
+          }
+          T sc = omega / ds[2 * ks + t];
+          if (t) sc = -sc;
+          sv[t] = sc * num;
+#pragma unroll
+          for (int d = 0; d < 9; ++d)
+#pragma unroll
+            for (int sp = 0; sp < 2; ++sp) {
+              r_sub(rv[d][sp], (sp == t) ? (T)1 : (T)-1, sv[t], a_[d][sp]);
+            }
+        }
+        long xo = x_at(c);
+        x[xo] = xp[u][0] + sv[0];
+        x[xo + nrhs] = xp[u][1] + sv[1];
+        if (c + 4 < 16) {
+          long xn = x_at(c + 4);
+          xp[u][0] = x[xn];
+          xp[u][1] = x[xn + nrhs];
+        }
+#pragma unroll
+        for (int d = 0; d < 9; ++d) {
+          int ls = (i + d / 3) * KTH + (j + d % 3);
+          rs[(ls * 2) * R + q] = rv[d][0];
+          rs[(ls * 2 + 1) * R + q] = rv[d][1];
+        }
+      }
+      __syncthreads();
+    }
+  }
+  // write r back (tile and halo)
+  if (vec) {
+    for (int e = tid; e < KTH * KTH * 2 * CPR; e += NT) {
+      int c = e % CPR, row = e / CPR, ls = row >> 1;
+      if (c * E >= Rc) continue;
+      int a = A0 + ls / KTH - 1, b = B0 + ls % KTH - 1;
+      long h = g.idx(a + b, a - b);
+      *(int4 *)(r + (h * 2 + (row & 1)) * nrhs + r0 + c * E) = *(const int4 *)(rs + row * R + c * E);
+    }
+  } else {
+    for (int e = tid; e < KTH * KTH * 2 * R; e += NT) {
+      int q2 = e % R, row = e / R, ls = row >> 1;
+      if (q2 >= Rc) continue;
+      int a = A0 + ls / KTH - 1, b = B0 + ls % KTH - 1;
+      long h = g.idx(a + b, a - b);
+      r[(h * 2 + (row & 1)) * nrhs + r0 + q2] = rs[e];
+    }
+  }
+}
+
+// One right-hand side: a warp per site of the colour step, lane = 2 d + s
+// holds one term of the row's inner product; shared memory: A rows, den and
+// r of tile + halo [100][2].
+template <typename T, typename S>
+__global__ void __launch_bounds__(128) k_kacz_tile1(Geo g, int tc, const S *__restrict__ A,
+                                                    const T *__restrict__ den, cx<T> *__restrict__ x,
+                                                    cx<T> *__restrict__ r, T omega) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  S *As = (S *)sm_raw;
+  T *ds = (T *)(As + KT * KT * 36);
+  cx<T> *rs = (cx<T> *)(ds + KT * KT * 2);
+  int A0, B0;
+  tile_origin(g, tc, A0, B0);
+  int tid = threadIdx.x;
+  tile_stage_rows<T, S>(g, A0, B0, A, den, As, ds);
+  for (int e = tid; e < KTH * KTH * 2; e += blockDim.x) {
+    int ls = e >> 1;
+    int a = A0 + ls / KTH - 1, b = B0 + ls % KTH - 1;
+    long h = g.idx(a + b, a - b);
+    cp_async(rs + e, r + h * 2 + (e & 1), (int)sizeof(cx<T>));
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  const int k = tid >> 5, lane = tid & 31;
+  // lane 0 of warp k holds x of its quadrant's sites four colour steps ahead
+  auto x_at = [&](int c) -> long {
+    int i = (c >> 2) + 4 * (k >> 1), j = (c & 3) + 4 * (k & 1);
+    return (long)g.idx(A0 + i + B0 + j, A0 + i - B0 - j) * 2;
+  };
+  cx<T> xp[4][2];
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+    if (k < 4 && lane == 0) {
+      xp[u][0] = x[x_at(u)];
+      xp[u][1] = x[x_at(u) + 1];
+    }
+  for (int c0 = 0; c0 < 16; c0 += 4) {
+#pragma unroll
+   for (int u = 0; u < 4; ++u) {
+    const int c = c0 + u;
+    if (k < 4) {
+      int i = (c >> 2) + 4 * (k >> 1), j = (c & 3) + 4 * (k & 1);
+      int ks = i * KT + j;
+      bool act = lane < 18;
+      int d = act ? lane >> 1 : 0, sp = lane & 1;
+      int ls = (i + d / 3) * KTH + (j + d % 3);  // (i + da + 1, j + db + 1)
+      cx<T> rv = act ? rs[ls * 2 + sp] : mk<T>(0, 0);
+      const S *Ah = As + ks * 36 + d * 4;
+      T gs = sp ? (T)-1 : (T)1;
+#pragma unroll
+      for (int t = 0; t < 2; ++t) {
+        cx<T> a_ = act ? ld<T>(Ah + t * 2 + sp) : mk<T>(0, 0);
+        cx<T> num = mk<T>(0, 0);
+        cfma(num, mk<T>(gs * a_.re, gs * a_.im), rv);
+#pragma unroll
+        for (int off = 16; off; off >>= 1) {
+          num.re += __shfl_xor_sync(0xffffffffu, num.re, off);
+          num.im += __shfl_xor_sync(0xffffffffu, num.im, off);
+        }
+        T sc = omega / ds[2 * ks + t];
+        if (t) sc = -sc;
+        cx<T> sv = sc * num;
+        r_sub(rv, (sp == t) ? (T)1 : (T)-1, sv, a_);
+        if (lane == 0) x[x_at(c) + t] = xp[u][t] + sv;
+      }
+      if (lane == 0 && c + 4 < 16) {
+        xp[u][0] = x[x_at(c + 4)];
+        xp[u][1] = x[x_at(c + 4) + 1];
+      }
+      if (act) rs[ls * 2 + sp] = rv;
+    }
+    __syncthreads();
+   }
+  }
+  for (int e = tid; e < KTH * KTH * 2; e += blockDim.x) {
+    int ls = e >> 1;
+    int a = A0 + ls / KTH - 1, b = B0 + ls % KTH - 1;
+    long h = g.idx(a + b, a - b);
+    r[h * 2 + (e & 1)] = rs[e];
+  }
 }
 
 // ---------------------------------------------------------------- transfers
@@ -354,12 +625,13 @@ static int coop_blocks() {
 
 template <typename T, typename S>
 static int launch_coop(const Level &L, const LevelOps &o, int sweeps, void *x, void *r, int nrhs, double omega,
-                       cudaStream_t s) {
+                       cudaStream_t s, int want_blocks) {
   long n16 = L.n >> 4;
   int wpi = nrhs == 1;
   long threads = wpi ? n16 * 32 : n16 * nrhs;
-  int maxb = coop_blocks<T, S>();
+  int maxb = coop_blocks<T, S>();  // all blocks must be resident at once
   int blocks = (int)std::min<long>(WL_GRID(threads, 128), (long)maxb);
+  if (want_blocks > 0) blocks = std::min(blocks, want_blocks);
   if (blocks < 1) return WL_EINVAL;
   Geo g = L.geo;
   const S *A = o.A.as<S>();
@@ -381,29 +653,194 @@ static int launch_coop(const Level &L, const LevelOps &o, int sweeps, void *x, v
   return WL_OK;
 }
 
-// Per-colour work that fits one wave of resident blocks goes to the
-// cooperative sweep kernel (one launch for all colours); larger levels use
-// one launch per colour.
-int kaczmarz_sweeps(wl_amg *a, int l, int prec, void *x, void *r, int nrhs, int sweeps,
-                    cudaStream_t s) {
-  if (sweeps <= 0) return WL_OK;
+// tile-coloured launch for tile colour tc (one quarter of a sweep)
+static bool tile_ok(int N) { return N >= 64 && N % (4 * KT) == 0; }
+
+// shared memory of a tile block: A rows, denominators and r of tile + halo
+template <typename T, typename S>
+static size_t tile_smem(int R) {
+  return (size_t)KT * KT * 36 * sizeof(S) + (size_t)KT * KT * 2 * sizeof(T) + (size_t)KTH * KTH * 2 * R * sizeof(cx<T>);
+}
+
+template <typename T, typename S, int R>
+static int launch_tile_r(const Level &L, const LevelOps &o, int tc, void *x, void *r, int nrhs, double omega,
+                         cudaStream_t s) {
+  size_t smem = tile_smem<T, S>(R);
+  // set once per instantiation (thread-safe static initialisation)
+  static const cudaError_t attr = cudaFuncSetAttribute((const void *)k_kacz_tile<T, S, R>,
+                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  WL_CUDA(attr);
+  int vec = ((uintptr_t)r % 16 == 0) && (sizeof(T) == 8 || nrhs % 2 == 0);
+  dim3 grid((L.N / (2 * KT)) * (L.N / (4 * KT)), (nrhs + R - 1) / R);
+  k_kacz_tile<T, S, R><<<grid, 4 * R, smem, s>>>(L.geo, tc, o.A.as<S>(), o.den.as<T>(), (cx<T> *)x, (cx<T> *)r,
+                                                 nrhs, vec, (T)omega);
+  return WL_OK;
+}
+
+// right-hand-side chunk of the tile kernel: the smallest of 8, 16, 32
+// (FP64: 8, 16) that covers nrhs, so that few lanes idle and shared memory
+// stays below 64 KB (FP32) or 90 KB (FP64) per block
+static int tile_default_R(int nrhs, int prec) {
+  if (nrhs <= 8) return 8;
+  if (prec == WL_FP64 || nrhs <= 16) return 16;
+  return 32;
+}
+
+template <typename T, typename S>
+static int launch_tile(const Level &L, const LevelOps &o, int tc, void *x, void *r, int nrhs, double omega,
+                       cudaStream_t s, int R) {
+  if (nrhs == 1) {
+    size_t smem = tile_smem<T, S>(1);
+    k_kacz_tile1<T, S><<<(L.N / (2 * KT)) * (L.N / (4 * KT)), 128, smem, s>>>(
+        L.geo, tc, o.A.as<S>(), o.den.as<T>(), (cx<T> *)x, (cx<T> *)r, (T)omega);
+    return WL_OK;
+  }
+  if (R == 8) return launch_tile_r<T, S, 8>(L, o, tc, x, r, nrhs, omega, s);
+  if (R == 16 || sizeof(T) == 8) return launch_tile_r<T, S, 16>(L, o, tc, x, r, nrhs, omega, s);
+  return launch_tile_r<T, S, (sizeof(T) == 8 ? 16 : 32)>(L, o, tc, x, r, nrhs, omega, s);
+}
+
+int kaczmarz_tile(wl_amg *a, int l, int prec, void *x, void *r, int nrhs, int tc, cudaStream_t s, int R) {
   const Level &L = a->lev[l];
+  if (!tile_ok(L.N)) return WL_EINVAL;
+  const LevelOps &o = ops_of(L, prec);
+  if (R <= 0) R = tile_default_R(nrhs, prec);
+  wl_count_launches(1);
+  if (prec == WL_FP64) return launch_tile<double, zd>(L, o, tc, x, r, nrhs, a->prm.omega, s, R);
+  if (prec == WL_FP32) return launch_tile<float, zf>(L, o, tc, x, r, nrhs, a->prm.omega, s, R);
+  return launch_tile<float, zb>(L, o, tc, x, r, nrhs, a->prm.omega, s, R);
+}
+
+static int coop_max_blocks(int prec) {
+  return prec == WL_FP64 ? coop_blocks<double, zd>() : prec == WL_FP32 ? coop_blocks<float, zf>()
+                                                                       : coop_blocks<float, zb>();
+}
+
+// blocks of 128 threads that cover one colour's work
+static long colour_blocks(const Level &L, int nrhs) {
   long n16 = L.n >> 4;
-  long items = nrhs == 1 ? n16 * 32 : n16 * nrhs;
-  int maxb = prec == WL_FP64 ? coop_blocks<double, zd>() : prec == WL_FP32 ? coop_blocks<float, zf>()
-                                                                           : coop_blocks<float, zb>();
-  int mode = a->prm.sweep_kernel;
-  if (mode == 2 || (mode == 0 && items <= (long)maxb * 128)) {
+  return WL_GRID(nrhs == 1 ? n16 * 32 : n16 * nrhs, 128);
+}
+
+static int run_sweeps(wl_amg *a, int l, int prec, void *x, void *r, int nrhs, int sweeps, const KTune &t,
+                      cudaStream_t s) {
+  const Level &L = a->lev[l];
+  if (t.form == 2) {
+    for (int sw = 0; sw < sweeps; ++sw)
+      for (int tc = 0; tc < 4; ++tc) WL_TRY(kaczmarz_tile(a, l, prec, x, r, nrhs, tc, s, t.param));
+  } else if (t.form == 1) {
     const LevelOps &o = ops_of(L, prec);
     wl_count_launches(1);
-    if (prec == WL_FP64) return launch_coop<double, zd>(L, o, sweeps, x, r, nrhs, a->prm.omega, s);
-    if (prec == WL_FP32) return launch_coop<float, zf>(L, o, sweeps, x, r, nrhs, a->prm.omega, s);
-    return launch_coop<float, zb>(L, o, sweeps, x, r, nrhs, a->prm.omega, s);
+    int rc;
+    if (prec == WL_FP64) rc = launch_coop<double, zd>(L, o, sweeps, x, r, nrhs, a->prm.omega, s, t.param);
+    else if (prec == WL_FP32) rc = launch_coop<float, zf>(L, o, sweeps, x, r, nrhs, a->prm.omega, s, t.param);
+    else rc = launch_coop<float, zb>(L, o, sweeps, x, r, nrhs, a->prm.omega, s, t.param);
+    WL_TRY(rc);
+  } else {
+    for (int sw = 0; sw < sweeps; ++sw)
+      for (int c = 0; c < 16; ++c) WL_TRY(kaczmarz_colour(a, l, prec, x, r, nrhs, c, s));
   }
-  for (int sw = 0; sw < sweeps; ++sw)
-    for (int c = 0; c < 16; ++c) WL_TRY(kaczmarz_colour(a, l, prec, x, r, nrhs, c, s));
   WL_CUDA(cudaGetLastError());
   return WL_OK;
+}
+
+// The sweep form for (level, nrhs, precision).  The ordering is the user's
+// (kacz_order); within it every form computes the same numbers, so the
+// choice only affects speed.  Order: an explicit sweep_kernel, else the
+// autotuner's measured choice, else the heuristic (cooperative launch when
+// one colour's work fits one wave of resident blocks).
+KTune sweep_form_of(wl_amg *a, int l, int prec, int nrhs) {
+  const Level &L = a->lev[l];
+  KTune t{nrhs, prec, 0, 0, 0.f};
+  bool tile = a->prm.kacz_order == 1 && tile_ok(L.N);
+  if (a->prm.sweep_kernel == 0)
+    for (const KTune &k : L.tune)
+      if (k.nrhs == nrhs && k.prec == prec && (k.form == 2) == tile) return k;
+  if (tile) {
+    t.form = 2;
+    t.param = tile_default_R(nrhs, prec);
+    return t;
+  }
+  int maxb = coop_max_blocks(prec);
+  long need = colour_blocks(L, nrhs);
+  int mode = a->prm.sweep_kernel;
+  if (mode == 2 || (mode == 0 && need <= maxb)) {
+    t.form = 1;
+    t.param = (int)std::min<long>(need, maxb);
+  }
+  return t;
+}
+
+int kaczmarz_sweeps(wl_amg *a, int l, int prec, void *x, void *r, int nrhs, int sweeps, cudaStream_t s) {
+  if (sweeps <= 0) return WL_OK;
+  return run_sweeps(a, l, prec, x, r, nrhs, sweeps, sweep_form_of(a, l, prec, nrhs), s);
+}
+
+// Autotuner: time every launch form of one sweep on each level (the level's
+// own cycle buffers, whose contents the next cycle overwrites) and keep the
+// fastest.  Candidates: per-colour launches and the cooperative launch at
+// 1, 1/2 and 1/4 of the resident-block limit (colour order); right-hand-side
+// chunks 8, 16, 32 (tile order).  Runs outside stream capture, once per
+// (nrhs, precision); sweep_kernel != 0 disables it.
+int autotune_sweeps(wl_amg *a, int nrhs, int prec, cudaStream_t s) {
+  if (a->prm.sweep_kernel != 0 || nrhs > a->cap) return WL_OK;
+  cudaEvent_t e0, e1;
+  WL_CUDA(cudaEventCreate(&e0));
+  WL_CUDA(cudaEventCreate(&e1));
+  int rc = WL_OK;
+  for (int l = 0; l < a->L - 1 && rc == WL_OK; ++l) {
+    Level &L = a->lev[l];
+    bool tile = a->prm.kacz_order == 1 && tile_ok(L.N);
+    bool have = false;
+    for (const KTune &k : L.tune)
+      if (k.nrhs == nrhs && k.prec == prec && (k.form == 2) == tile) have = true;
+    if (have) continue;
+    std::vector<KTune> cand;
+    if (tile) {
+      for (int R : {8, 16, 32}) {
+        if (prec == WL_FP64 && R > 16) continue;
+        if (nrhs > 1 && R / 2 >= nrhs && R > 8) continue;  // mostly idle lanes
+        cand.push_back(KTune{nrhs, prec, 2, nrhs == 1 ? 1 : R, 0.f});
+        if (nrhs == 1) break;
+      }
+    } else {
+      cand.push_back(KTune{nrhs, prec, 0, 0, 0.f});
+      int maxb = coop_max_blocks(prec);
+      long need = colour_blocks(L, nrhs);
+      if (need <= 4L * maxb)
+        for (int div : {1, 2, 4}) {
+          int b = (int)std::min<long>(need, std::max(1, maxb / div));
+          bool dup = false;
+          for (const KTune &c : cand) dup |= (c.form == 1 && c.param == b);
+          if (!dup) cand.push_back(KTune{nrhs, prec, 1, b, 0.f});
+        }
+    }
+    KTune best = cand[0];
+    float best_us = 1e30f;
+    for (KTune &c : cand) {
+      rc = run_sweeps(a, l, prec, L.x.p, L.r.p, nrhs, 1, c, s);  // warm-up
+      if (rc) break;
+      if ((rc = (cudaEventRecord(e0, s) == cudaSuccess) ? WL_OK : WL_ECUDA)) break;
+      for (int rep = 0; rep < 3 && rc == WL_OK; ++rep) rc = run_sweeps(a, l, prec, L.x.p, L.r.p, nrhs, 1, c, s);
+      if (rc) break;
+      float ms = 0;
+      if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+          cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+        rc = WL_ECUDA;
+        break;
+      }
+      c.us = ms * 1e3f / 3;
+      if (c.us < best_us) {
+        best_us = c.us;
+        best = c;
+      }
+    }
+    if (rc == WL_OK) L.tune.push_back(best);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc == WL_ECUDA) wl_set_error("autotune_sweeps: CUDA error while timing");
+  return rc;
 }
 
 int restrict_op(wl_amg *a, int l, int prec, const void *r, void *fc, int nrhs, cudaStream_t s) {
@@ -489,19 +926,23 @@ static int cycle_level(wl_amg *a, int l, int nrhs, int prec, cudaStream_t s) {
 int cycle_direct(wl_amg *a, int nrhs, int prec, cudaStream_t s) { return cycle_level(a, 0, nrhs, prec, s); }
 
 // lev[0].x = M(lev[0].f); captured once per (nrhs, precision) as a CUDA graph
-int cycle_run(wl_amg *a, int nrhs, int prec, cudaStream_t s) {
+// Capture and instantiate the cycle graph for (nrhs, prec) unless it exists;
+// nothing is launched.  A capture in progress forbids device-wide
+// synchronisation anywhere in the process, so callers that run beside other
+// threads (the serving workers) capture every width they need up front.
+int cycle_prepare(wl_amg *a, int nrhs, int prec, cudaStream_t s, const wl_amg::G **out) {
   for (auto &g : a->graphs)
     if (g.nrhs == nrhs && g.prec == prec) {
-      WL_CUDA(cudaGraphLaunch(g.exec, s));
-      wl_count_launches(g.kernels);
+      if (out) *out = &g;
       return WL_OK;
     }
+  WL_TRY(autotune_sweeps(a, nrhs, prec, s));  // measured launch forms, before the capture
   cudaGraph_t graph;
   long long before = wl_launch_count();
   WL_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
   int rc = cycle_level(a, 0, nrhs, prec, s);
   cudaError_t e = cudaStreamEndCapture(s, &graph);
-  long long kernels = wl_launch_count() - before;  // captured, not yet run
+  long long kernels = wl_launch_count() - before;  // captured, not run
   wl_count_launches(-kernels);
   if (rc) {
     if (e == cudaSuccess) cudaGraphDestroy(graph);
@@ -516,8 +957,15 @@ int cycle_run(wl_amg *a, int nrhs, int prec, cudaStream_t s) {
   cudaGraphDestroy(graph);
   WL_CUDA(e);
   a->graphs.push_back(gg);
-  WL_CUDA(cudaGraphLaunch(gg.exec, s));
-  wl_count_launches(gg.kernels);
+  if (out) *out = &a->graphs.back();
+  return WL_OK;
+}
+
+int cycle_run(wl_amg *a, int nrhs, int prec, cudaStream_t s) {
+  const wl_amg::G *g = nullptr;
+  WL_TRY(cycle_prepare(a, nrhs, prec, s, &g));
+  WL_CUDA(cudaGraphLaunch(g->exec, s));
+  wl_count_launches(g->kernels);
   return WL_OK;
 }
 
@@ -639,5 +1087,18 @@ extern "C" int amg_cycle(wl_amg *a, const void *f, void *x, int nrhs, int prec) 
   WL_TRY(wl::cycle_run(a, nrhs, prec, s));
   WL_TRY(wl::from_internal(a->lev[0].x.p, (zd *)x, n2, nrhs, pin, s));
   WL_CUDA(cudaStreamSynchronize(s));
+  return WL_OK;
+}
+
+extern "C" int amg_sweep_form(wl_amg *a, int level, int nrhs, int prec, int *form, int *param, float *us) {
+  if (!a || !form || !param || !us || level < 0 || level >= a->L - 1 || nrhs < 1 ||
+      (prec != WL_FP64 && prec != WL_FP32 && prec != WL_FP32_BF16)) {
+    wl_set_error("amg_sweep_form: invalid argument");
+    return WL_EINVAL;
+  }
+  KTune t = wl::sweep_form_of(a, level, prec, nrhs);
+  *form = t.form;
+  *param = t.param;
+  *us = t.us;
   return WL_OK;
 }

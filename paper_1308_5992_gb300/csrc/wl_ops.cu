@@ -99,14 +99,14 @@ __global__ void k_hop(Geo g, const cx<Tc> *__restrict__ V, int par_out,
       int lx = fwd ? x : xn, ly = fwd ? y : yn;  // link V_mu(p) or V_mu(p - mu)
       cx<Tc> link = V[(mu * N + ly) * N + lx];
       long j = (long)g.idx(xn, yn) * 2 * nrhs + r;
-      cx<Tc> v0 = ccast<Tc>(in[j]), v1 = ccast<Tc>(in[j + nrhs]);
+      cx<Tc> v0 = widen<Tc>(in[j]), v1 = widen<Tc>(in[j + nrhs]);
       hop_acc(o0, o1, mu, fwd, link, v0, v1);
     }
   }
   long o = (long)h * 2 * nrhs + r;
   if (sub) {
-    o0 = ccast<Tc>(sub[o]) - o0;
-    o1 = ccast<Tc>(sub[o + nrhs]) - o1;
+    o0 = widen<Tc>(sub[o]) - o0;
+    o1 = widen<Tc>(sub[o + nrhs]) - o1;
   }
   out[o] = ccast<Tout>(o0);
   out[o + nrhs] = ccast<Tout>(o1);
@@ -398,6 +398,21 @@ int dhat_apply_dev(wl_op *op, const void *x, int x_is_f32, zd *y, int nrhs, cuda
     k_hop<double, double, double, double><<<grid, 256, 0, s>>>(g, V, 1, (const zd *)x, nullptr, t, nrhs);
     k_hop<double, double, double, double><<<grid, 256, 0, s>>>(g, V, 0, t, (const zd *)x, y, nrhs);
   }
+  WL_CUDA(cudaGetLastError());
+  return WL_OK;
+}
+
+// y = Dhat x in FP32 arithmetic (FP32 links, x float), y widened to double
+int dhat_apply_dev32(wl_op *op, const zf *x, zd *y, int nrhs, cudaStream_t s) {
+  Geo g = op->geo;
+  long n = g.nsites();
+  WL_TRY(op->scratch.alloc(sizeof(zd) * n * 2 * nrhs));
+  zf *t = op->scratch.as<zf>();
+  unsigned grid = WL_GRID(n * nrhs, 256);
+  const zf *V = op->Uf32.as<zf>();
+  wl_count_launches(2);
+  k_hop<float, float, float, float><<<grid, 256, 0, s>>>(g, V, 1, x, nullptr, t, nrhs);
+  k_hop<float, float, float, double><<<grid, 256, 0, s>>>(g, V, 0, t, x, y, nrhs);
   WL_CUDA(cudaGetLastError());
   return WL_OK;
 }

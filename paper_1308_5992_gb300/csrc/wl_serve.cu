@@ -240,10 +240,30 @@ extern "C" int srv_add(wl_server *S, wl_amg *amg, int *cfg_id) {
   return WL_OK;
 }
 
+extern "C" int srv_info(wl_server *S, int cfg, int *slots, unsigned long long *bytes) {
+  if (!S || !slots || !bytes) return WL_EINVAL;
+  std::lock_guard<std::mutex> lk(S->mu);
+  if (cfg < 0 || cfg >= (int)S->w.size()) {
+    wl_set_error("srv_info: no configuration %d", cfg);
+    return WL_EINVAL;
+  }
+  *slots = S->w[cfg]->cap;
+  *bytes = S->w[cfg]->bytes;
+  return WL_OK;
+}
+
 extern "C" int srv_start(wl_server *S) {
   if (!S) return WL_EINVAL;
   std::lock_guard<std::mutex> lk(S->mu);
   if (S->started) return WL_OK;
+  // capture the cycle graph of every packed width now: a capture while
+  // client threads run would make their device-wide synchronisation fail
+  for (Worker *W : S->w) {
+    wl_amg *a = W->amg;
+    WL_CUDA(cudaSetDevice(a->op->device));
+    for (int q = 1; q <= W->cap; ++q) WL_TRY(wl::cycle_prepare(a, q, a->prm.precision, a->op->stream, nullptr));
+    WL_CUDA(cudaStreamSynchronize(a->op->stream));
+  }
   S->started = true;
   for (Worker *W : S->w) W->th = std::thread(serve_loop, S, W);
   return WL_OK;

@@ -631,6 +631,22 @@ static int visit(Setup &S, int l, bool first, int mu) {
   return relax_eig(S, l, mu);
 }
 
+// Sec. 4.2 super-V setup: one visit per grid, mu 2^l relaxations before
+// (both sets, then fit and injection) and after (eigenvector set) the
+// coarse visit, so each grid relaxes as often as in the W-visits above while
+// the coarsest eigensolve runs once per setup cycle
+static int visit_superv(Setup &S, int l, bool first, int mu) {
+  wl_amg *a = S.a;
+  if (l == a->L - 1) return coarsest_eig(S);
+  int mul = mu << l;
+  WL_TRY(relax_both(S, l, mul, !first));
+  WL_TRY(fit_level(S, l));
+  WL_TRY(inject_all(S, l));
+  WL_TRY(visit_superv(S, l + 1, first, mu));
+  WL_TRY(interp_e(S, l));
+  return relax_eig(S, l, mul);
+}
+
 __global__ void k_axpy_col(zd *V, const zd *e, long n2, int k, int q) {
   long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n2) V[i * k + q] = V[i * k + q] + e[i];
@@ -741,14 +757,15 @@ extern "C" int amg_setup(wl_op *op, const amg_params *params, wl_amg **out) {
   if (!rc) rc = relax_both(S, 0, prm.setup_mu[0], false);
   if (!rc) rc = fit_level(S, 0);
   if (!rc) rc = inject_all(S, 0);
-  if (!rc) rc = visit(S, 1, true, prm.setup_mu[0]);
+  if (!rc) rc = prm.setup_cycle == 1 ? visit_superv(S, 1, true, prm.setup_mu[0]) : visit(S, 1, true, prm.setup_mu[0]);
   if (!rc) rc = interp_e(S, 0);
   if (!rc) rc = adaptive_step(S);
   // setup cycle 2
   if (!rc) rc = relax_both(S, 0, prm.setup_mu[1], true);
   if (!rc) rc = fit_level(S, 0);
   if (!rc) rc = inject_all(S, 0);
-  if (!rc) rc = visit(S, 1, false, prm.setup_mu[1]);
+  if (!rc) rc = prm.setup_cycle == 1 ? visit_superv(S, 1, false, prm.setup_mu[1])
+                                     : visit(S, 1, false, prm.setup_mu[1]);
   if (!rc) rc = interp_e(S, 0);
   if (!rc) rc = wl::hier_finish(a);
   if (S.cs) cusolverDnDestroy(S.cs);

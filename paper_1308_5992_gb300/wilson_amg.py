@@ -18,7 +18,7 @@ WL_FP64, WL_FP32, WL_FP32_BF16 = 0, 1, 2
 WL_OP_D, WL_OP_DHAT = 0, 1
 WL_CYCLE_V, WL_CYCLE_W = 0, 1
 (WL_K_DHAT, WL_K_KACZ, WL_K_STENCIL, WL_K_RESTRICT, WL_K_PROLONG, WL_K_COARSEST, WL_K_GS_DOT,
- WL_K_GS_AXPY) = range(8)
+ WL_K_GS_AXPY, WL_K_KACZ_TILE) = range(9)
 
 
 class amg_params(C.Structure):
@@ -26,7 +26,9 @@ class amg_params(C.Structure):
                 ("setup_mu", C.c_int * 2), ("nu_pre", C.c_int), ("nu_post", C.c_int),
                 ("omega", C.c_double), ("cycle", C.c_int), ("fgmres_m", C.c_int),
                 ("max_restarts", C.c_int), ("precision", C.c_int), ("seed", C.c_ulonglong),
-                ("gs_passes", C.c_int), ("zero_guess", C.c_int), ("sweep_kernel", C.c_int)]
+                ("gs_passes", C.c_int), ("zero_guess", C.c_int), ("sweep_kernel", C.c_int),
+                ("kacz_order", C.c_int), ("arnoldi_matvec", C.c_int),
+                ("setup_cycle", C.c_int)]
 
 
 class wl_info(C.Structure):
@@ -80,12 +82,15 @@ def lib():
             "amg_coarsest": (i, [P, P, P, i]),
             "amg_cycle": (i, [P, P, P, i, i]),
             "amg_fgmres": (i, [P, P, P, i, d, C.POINTER(wl_info)]),
+            "amg_rho": (i, [P, P, P, i, d, i, P, P, P]),
+            "amg_sweep_form": (i, [P, i, i, i, P, P, P]),
             "wl_last_error": (C.c_char_p, []),
             "wl_time_kernel": (i, [P, i, i, i, i, i, C.POINTER(d)]),
             "wl_dhat_apply_noalloc": (i, [P, P, P, i]),
             "srv_create": (i, [C.c_ulonglong, i, C.POINTER(P)]),
             "srv_add": (i, [P, P, C.POINTER(i)]),
             "srv_start": (i, [P]),
+            "srv_info": (i, [P, i, C.POINTER(i), C.POINTER(C.c_ulonglong)]),
             "srv_submit": (i, [P, i, P, P, i, d, C.POINTER(C.c_longlong)]),
             "srv_poll": (i, [P, C.c_longlong, C.POINTER(i), C.POINTER(wl_info), C.POINTER(d)]),
             "srv_drain": (i, [P]),
@@ -271,6 +276,29 @@ def amg_fgmres(amg, bhat, x, nrhs, tol):
     return rc, [i.as_dict() for i in info]
 
 
+def amg_rho(amg, x0, x, nrhs, tol=1e-8, maxit=100, hist=False):
+    """Sec. 4's rho of the stand-alone cycle on Dhat x = 0 from x0; returns
+    (rc, rho[nrhs], iters[nrhs], hist [nrhs][maxit + 1] or None)."""
+    import numpy as np
+    rho = np.zeros(nrhs)
+    it = np.zeros(nrhs, dtype=np.int32)
+    h = np.zeros((nrhs, maxit + 1)) if hist else None
+    rc = _chk(lib().amg_rho(amg.handle, _ptr(x0), _ptr(x), nrhs, tol, maxit, rho.ctypes.data_as(C.c_void_p),
+                            it.ctypes.data_as(C.c_void_p), h.ctypes.data_as(C.c_void_p) if hist else None),
+              "amg_rho", ok=(WL_OK, WL_NOT_CONVERGED))
+    return rc, rho, it, h
+
+
+def amg_sweep_form(amg, level, nrhs, prec):
+    """(form, param, us) of the Kaczmarz sweep on `level`: form 0 per-colour
+    launches, 1 cooperative (param blocks), 2 tile kernel (param RHS chunk);
+    us = measured time of one sweep (0 if not measured)."""
+    f, p, u = C.c_int(), C.c_int(), C.c_float()
+    _chk(lib().amg_sweep_form(amg.handle, level, nrhs, prec, C.byref(f), C.byref(p), C.byref(u)),
+         "amg_sweep_form")
+    return f.value, p.value, u.value
+
+
 def amg_level_apply(amg, level, x, y, nrhs, prec=WL_FP64):
     return _chk(lib().amg_level_apply(amg.handle, level, _ptr(x), _ptr(y), nrhs, prec),
                 "amg_level_apply")
@@ -355,6 +383,13 @@ def srv_add(srv, amg):
     _chk(lib().srv_add(srv.handle, amg.handle, C.byref(cid)), "srv_add")
     srv.amgs.append(amg)
     return cid.value
+
+
+def srv_info(srv, cfg):
+    """(slots, device bytes) reserved for configuration cfg."""
+    n, b = C.c_int(), C.c_ulonglong()
+    _chk(lib().srv_info(srv.handle, cfg, C.byref(n), C.byref(b)), "srv_info")
+    return n.value, b.value
 
 
 def srv_start(srv):

@@ -44,3 +44,19 @@ def test_params_defaults_and_errors():
     assert rc == W.WL_EINVAL and "power of two" in W.last_error()
     rc = W.lib().wilson_create(None, 32, 0.1, None, ctypes.byref(out))
     assert rc == W.WL_EINVAL
+
+
+def test_float_widening_formula():
+    """The kernels widen normal floats to doubles with integer operations
+    (sign, exponent + 896, mantissa << 29); check the formula is exact for
+    every normal exponent against numpy's conversion."""
+    import numpy as np
+    rng = np.random.default_rng(0)
+    mant = rng.integers(0, 1 << 23, size=4096, dtype=np.uint32)
+    for e in range(1, 255):
+        for sign in (0, 1):
+            u = (np.uint32(sign) << np.uint32(31)) | (np.uint32(e) << np.uint32(23)) | mant
+            f = u.view(np.float32)
+            d = ((u.astype(np.uint64) & np.uint64(0x80000000)) << np.uint64(32)) | \
+                (np.uint64(e + 896) << np.uint64(52)) | ((u.astype(np.uint64) & np.uint64(0x7FFFFF)) << np.uint64(29))
+            assert np.array_equal(d.view(np.float64), f.astype(np.float64))

@@ -134,6 +134,104 @@ def test_kaczmarz_sweep(O, shared, name, nrhs, form):
             assert rel(H(rg), rr) <= tol, (l, prec, rel(H(rg), rr))
 
 
+@pytest.mark.parametrize("name,nrhs", [("T64", 1), ("T64", 3), ("T64", 16), ("C2", 40), ("C2", 19), ("C2", 1)])
+def test_kaczmarz_tile_sweep(O, shared, name, nrhs):
+    """Tile-coloured sweep (8x8 tiles, shared-memory kernel) against the
+    oracle's tile order; grids below 64 keep the 16-colour order."""
+    w, op, h, _, path = shared(name)
+    amg = W.amg_import(op, path, W.amg_params_default(zero_guess=1, kacz_order=1))
+    for l in range(h.L - 1):
+        n = h.n(l)
+        f = np.stack([cgauss(150 + l, r, n) for r in range(nrhs)])
+        x0 = 0.1 * np.stack([cgauss(160 + l, r, n) for r in range(nrhs)])
+        r0 = np.stack([f[r] - h.apply(l, x0[r]) for r in range(nrhs)])
+        ref = [h.kaczmarz(l, x0[r], r0[r], order=O.ORDER_TILE, sweeps=2) for r in range(nrhs)]
+        xr, rr = np.stack([a for a, _ in ref]), np.stack([b for _, b in ref])
+        for prec, tol in ((W.WL_FP64, 1e-13), (W.WL_FP32, 1e-5)):
+            xg, rg = T(x0), T(r0)
+            W.amg_kaczmarz(amg, l, xg, rg, nrhs, 2, prec)
+            assert rel(H(xg), xr) <= tol, (l, prec, rel(H(xg), xr))
+            assert rel(H(rg), rr) <= tol, (l, prec, rel(H(rg), rr))
+
+
+@pytest.mark.parametrize("order", [0, 1])
+def test_sweep_forms_agree_and_autotuner(O, shared, order):
+    """Every launch form of a Kaczmarz sweep computes the same numbers in the
+    same order: per-colour launches, the cooperative launch and the
+    autotuner's choice give bitwise-equal x and r; after the first cycle of a
+    batch width every non-coarsest level has a measured form."""
+    w, op, h, _, path = shared("C2")
+    nrhs, prec = 4, W.WL_FP32
+    outs = {}
+    for sk in (1, 2, 0):
+        amg = W.amg_import(op, path, W.amg_params_default(zero_guess=1, sweep_kernel=sk, kacz_order=order,
+                                                          precision=prec))
+        if sk == 0:
+            f = T(np.stack([cgauss(180, r, h.n(0)) for r in range(nrhs)]))
+            W.amg_cycle(amg, f, torch.zeros_like(f), nrhs, prec)
+            for l in range(h.L - 1):
+                form, param, us = W.amg_sweep_form(amg, l, nrhs, prec)
+                assert us > 0 and form in (0, 1, 2), (l, form, param, us)
+                assert (form == 2) == (order == 1 and h.Nl[l] >= 64)
+        res = []
+        for l in range(h.L - 1):
+            n = h.n(l)
+            x0 = 0.1 * np.stack([cgauss(190 + l, r, n) for r in range(nrhs)])
+            r0 = np.stack([cgauss(200 + l, r, n) for r in range(nrhs)])
+            xg, rg = T(x0), T(r0)
+            W.amg_kaczmarz(amg, l, xg, rg, nrhs, 2, prec)
+            res.append((H(xg), H(rg)))
+        outs[sk] = res
+        amg.close()
+    for sk in (2, 0):
+        for l, ((xa, ra), (xb, rb)) in enumerate(zip(outs[1], outs[sk])):
+            assert np.array_equal(xa, xb) and np.array_equal(ra, rb), (sk, l)
+
+
+def test_tile_ordered_solve(O, shared):
+    w, op, h, _, path = shared("C2")
+    amg = W.amg_import(op, path, W.amg_params_default(zero_guess=1, kacz_order=1))
+    b = rhs_batch(w["N"], 2, 17)
+    psi = torch.zeros_like(T(b))
+    rc, info = W.amg_solve(amg, T(b), psi, 2, 1e-13)
+    assert rc == W.WL_OK
+    for q in range(2):
+        ref, oi = h.solve(b[q], tol=1e-13, order=O.ORDER_TILE)
+        assert np.linalg.norm(H(psi[q]) - ref) / np.linalg.norm(ref) <= 1e-10
+        assert abs(info[q]["iters"] - oi["iters"]) <= 2, (info[q], oi)
+
+
+@pytest.mark.parametrize("cycle", [W.WL_CYCLE_V, W.WL_CYCLE_W])
+def test_rho_protocol(O, shared, cycle):
+    """Sec. 4's convergence estimate rho = |e^nu| / |e^(nu-1)| of the
+    stand-alone cycle on Dhat x = 0, stopped at |e^nu| <= 1e-8 |e^0|:
+    GPU FP64 cycle against the oracle's on a shared hierarchy (error norms
+    1e-9 relative, same stopping iteration); the FP32 cycle inside the FP64
+    iteration gives the same rate and stopping point within rounding."""
+    w, op, h, _, path = shared("C2")
+    n, R = h.n(0), 3
+    x0 = np.stack([cgauss(170, r, n) for r in range(R)])
+    refs = [h.rho(x0[r], tol=1e-8, maxit=100, nu1=4, nu2=4, gamma=cycle + 1) for r in range(R)]
+    for prec in (W.WL_FP64, W.WL_FP32):
+        amg = W.amg_import(op, path, W.amg_params_default(cycle=cycle, nu_pre=4, nu_post=4, precision=prec))
+        x = torch.zeros_like(T(x0))
+        rc, rho, it, hist = W.amg_rho(amg, T(x0), x, R, 1e-8, 100, hist=True)
+        assert rc == W.WL_OK
+        for r in range(R):
+            rr, ir, hr, met = refs[r]
+            assert met
+            if prec == W.WL_FP64:
+                assert it[r] == ir, (r, it[r], ir)
+                assert np.abs(hist[r, :ir + 1] / hr - 1).max() <= 1e-9
+                assert abs(rho[r] - rr) <= 1e-9 * rr
+            else:
+                k = min(it[r], ir)
+                assert abs(int(it[r]) - ir) <= 1, (r, it[r], ir)
+                assert np.abs(hist[r, :k + 1] / hr[:k + 1] - 1).max() <= 1e-3
+                assert abs(rho[r] - rr) <= 0.05 * rr
+        amg.close()
+
+
 @pytest.mark.parametrize("name", ["T64", "C1"])
 def test_transfers_and_coarsest(shared, name):
     w, op, h, amg, _ = shared(name)
@@ -244,6 +342,31 @@ def test_gpu_setup_quality(O, ops):
     ho = O.Hierarchy.setup(w["N"], w["U"], w["m"],
                            O.setup_params(w["blocks"], k_r=w["k"], k_e=w["k"], seed=w["seed"]))
     ref, oi = ho.solve(b[0], tol=1e-13)
+    assert np.linalg.norm(H(psi[0]) - ref) / np.linalg.norm(ref) <= 1e-9
+    assert info[0]["iters"] <= 2 * oi["iters"] + 5, (info, oi)
+
+
+def test_gpu_super_v_setup_quality(O, ops):
+    """Sec. 4.2's super-V setup on the GPU: the stand-alone W(4,4) cycle
+    converges and GMRES(32) needs iterations within the band of the oracle's
+    super-V setup of the same configuration; solutions match to 1e-9."""
+    w, op = ops("C2")
+    p = W.amg_params_default(k_r=w["k"], k_e=w["k"], seed=w["seed"], zero_guess=1, setup_cycle=1,
+                             cycle=W.WL_CYCLE_W, nu_pre=4, nu_post=4, fgmres_m=32)
+    for l, b in enumerate(w["blocks"]):
+        p.block[l] = b
+    p.levels = len(w["blocks"]) + 1
+    amg = W.amg_setup(op, p)
+    x0 = T(cgauss(4, 3, w["N"] ** 2)[None, :])
+    rc, rho, nu, _ = W.amg_rho(amg, x0, torch.zeros_like(x0), 1, 1e-8, 100)
+    assert rc == W.WL_OK and rho[0] < 0.9, (rho, nu)
+    b = rhs_batch(w["N"], 1, 14)
+    psi = torch.zeros_like(T(b))
+    rc, info = W.amg_solve(amg, T(b), psi, 1, 1e-12)
+    assert rc == W.WL_OK
+    ho = O.Hierarchy.setup(w["N"], w["U"], w["m"], O.setup_params(w["blocks"], k_r=w["k"], k_e=w["k"],
+                                                                  seed=w["seed"], super_v=True))
+    ref, oi = ho.solve(b[0], tol=1e-13, m=32, nu1=4, nu2=4, gamma=2)
     assert np.linalg.norm(H(psi[0]) - ref) / np.linalg.norm(ref) <= 1e-9
     assert info[0]["iters"] <= 2 * oi["iters"] + 5, (info, oi)
 
