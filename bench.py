@@ -30,6 +30,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "Wilson-AMG solves/s at 1e-10 rel err (mixed+batched vs plain FP64); p99 ms"
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the kernels the
+# roofline reports, from ncu captures of the C4 workload at 64 right-hand sides
+# (profiles/traffic_c4_512x512_64rhs.md); None until captured for the current kernel
+TRAFFIC = {"k_mdot": 3228150000, "k_kacz_tile": 126950000}
 TOL = 1e-10
 
 
@@ -51,6 +55,9 @@ def parse():
     ap.add_argument("--study", default="", choices=["", "rho"],
                     help="rho: Sec. 4's experiment (rho, GMRES(32) iterations, residual and error "
                          "across an eta_min sweep) instead of the benchmark; one JSON line per case")
+    ap.add_argument("--kernel-only", default="", choices=["", "dot", "axpy", "kacz", "tile", "dhat"],
+                    help="set up the workload, then time one kernel family (wl_time_kernel) inside an NVTX "
+                         "range 'cap' for profilers; prints one JSON line")
     ap.add_argument("--study-sizes", default="128,256")
     ap.add_argument("--study-configs", type=int, default=3)
     ap.add_argument("--study-setup", default="W", choices=["W", "superV"],
@@ -180,12 +187,14 @@ def run_gb300(args, rank, world, local_rank):
 
     op = W.wilson_create(torch.from_numpy(w["U"]).to(dev), N, w["m"])
 
-    def params(precision):
+    def params(precision, plain=False):
+        # plain: the method as the paper states it (16-colour Kaczmarz, FP64 throughout)
         p = W.amg_params_default(k_r=w["k"], k_e=w["k"], seed=w["seed"], zero_guess=1,
                                  precision=precision, nu_pre=w["nu"], nu_post=w["nu"],
                                  cycle=W.WL_CYCLE_W if w["cycle"] == "W" else W.WL_CYCLE_V,
                                  fgmres_m=w["fgmres_m"], gs_passes=w["gs_passes"],
-                                 kacz_order=w["kacz_order"])
+                                 kacz_order=0 if plain else w["kacz_order"],
+                                 arnoldi_matvec=0 if plain else w["arnoldi_matvec"])
         p.levels = len(w["blocks"]) + 1
         for l, b in enumerate(w["blocks"]):
             p.block[l] = b
@@ -198,7 +207,7 @@ def run_gb300(args, rank, world, local_rank):
     setup_s = time.perf_counter() - t0
     hier = os.path.join("/tmp", "wl_bench_%d_%d.wlh" % (os.getpid(), rank))
     W.amg_export(amg, hier)
-    amg64 = W.amg_import(op, hier, params(W.WL_FP64))  # same hierarchy, plain FP64 cycle
+    amg64 = W.amg_import(op, hier, params(W.WL_FP64, plain=True))  # same hierarchy, plain FP64 method
     os.remove(hier)
 
     b_host = torch.from_numpy(rhs_batch(N, nrhs, 100 + 1000 * rank)).pin_memory()
@@ -281,33 +290,44 @@ def run_gb300(args, rank, world, local_rank):
         torch.cuda.synchronize()
         p64.append(e0.elapsed_time(e1))
 
-    # Roofline.  The launch list of this workload (profiles/launches_c4_512x512_64rhs.md)
-    # puts the FP64 Gram-Schmidt multi-dot k_mdot first (about 30% of kernel time); it is
-    # FP64-ALU bound, so its peak is derived from the unit counts: 152 SMs x 2 FP64 FMA
-    # per clock x 2 flop x 2070 MHz = 1259 GFLOP/s.  One launch computes kc = 11 conjugate
-    # dot products of length E = 2 n0 nrhs complex numbers: 8 flop per complex term.
+    # Roofline.  The launch list of this workload (profiles/launches_c4_512x512_64rhs.md) ranks
+    # the FP64 Gram-Schmidt multi-dot k_mdot first, then the fine-level Kaczmarz kernel.
     n0 = N * N // 2
     E = 2 * n0 * nrhs
+    hbm, src = peaks()
+    eb = 16 if prec == W.WL_FP64 else 8          # bytes of one complex value of the cycle
+    sb = 16 if prec == W.WL_FP64 else (8 if prec == W.WL_FP32 else 4)  # stencil storage
+    # k_mdot: FP64-ALU bound, peak derived from the unit counts (152 SMs x 2 FP64 FMA per
+    # clock x 2 flop x 2070 MHz = 1259 GFLOP/s); one launch computes kc = 11 conjugate dot
+    # products of length E = 2 n0 nrhs complex numbers, 8 flop per complex term
     kc = 11
     dot_ms = W.wl_time_kernel(amg, W.WL_K_GS_DOT, 0, nrhs, prec, 20)
     fp64_peak = 152 * 2 * 2 * 2070e6 / 1e9
     dot_gflops = 8.0 * kc * E / (dot_ms * 1e-3) / 1e9
-    roof = {"kernel": "k_mdot<double> (Gram-Schmidt, 11 dots)", "bound": "alu", "achieved": round(dot_gflops, 1),
-            "peak": round(fp64_peak, 1), "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz",
-            "unit": "GFLOP/s", "frac": round(dot_gflops / fp64_peak, 4), "traffic": None,
-            "avg_launch_ms": round(dot_ms, 4), "algorithmic_flops": int(8 * kc * E)}
-    # second: the fine-level Kaczmarz colour pass (HBM bound).  One launch updates 1/16 of
-    # the sites: it reads and writes r on 9/16 of the sites and x on 1/16, and reads the
-    # stencil rows and denominators of 1/16 of the sites (each operand once)
-    eb = 16 if prec == W.WL_FP64 else 8          # bytes of one complex value of the cycle
-    sb = 16 if prec == W.WL_FP64 else (8 if prec == W.WL_FP32 else 4)  # stencil storage
+    roof_dot = {"kernel": "k_mdot<double> (Gram-Schmidt, 11 dots)", "bound": "alu", "achieved": round(dot_gflops, 1),
+                "peak": round(fp64_peak, 1), "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz",
+                "unit": "GFLOP/s", "frac": round(dot_gflops / fp64_peak, 4), "traffic": TRAFFIC.get("k_mdot"),
+                "avg_launch_ms": round(dot_ms, 4), "algorithmic_flops": int(8 * kc * E)}
+    # k_kacz: one colour pass (1/16 of the sites): r read and written on 9/16 of the sites,
+    # x on 1/16, stencil rows and denominators of 1/16 of the sites (each operand once)
     kacz_ms = W.wl_time_kernel(amg, W.WL_K_KACZ, 0, nrhs, prec, 160)
     kacz_bytes = n0 * nrhs * (9 / 16 * 2 * 2 * eb + 1 / 16 * 2 * 2 * eb) + n0 / 16 * (36 * sb + 2 * (eb // 2))
-    hbm, src = peaks()
     achieved = kacz_bytes / (kacz_ms * 1e-3) / 1e9
-    roof2 = {"kernel": "k_kacz<float> (fine level, one colour)", "bound": "hbm", "achieved": round(achieved, 1),
-             "peak": hbm, "peak_source": src, "unit": "GB/s", "frac": round(achieved / hbm, 4), "traffic": None,
-             "avg_launch_ms": round(kacz_ms, 5), "algorithmic_bytes": int(kacz_bytes)}
+    roof_kacz = {"kernel": "k_kacz (fine level, one of 16 colour passes)", "bound": "hbm",
+                 "achieved": round(achieved, 1), "peak": hbm, "peak_source": src, "unit": "GB/s",
+                 "frac": round(achieved / hbm, 4), "traffic": None, "avg_launch_ms": round(kacz_ms, 5),
+                 "algorithmic_bytes": int(kacz_bytes)}
+    # k_kacz_tile: one tile colour (1/4 of the sites, a quarter of a sweep): r and x read
+    # and written once, the stencil rows and denominators read once, for 1/4 of the sites
+    tile_ms = W.wl_time_kernel(amg, W.WL_K_KACZ_TILE, 0, nrhs, prec, 80)
+    tile_bytes = n0 / 4 * (nrhs * 2 * 2 * eb * 2 + 36 * sb + 2 * (eb // 2))
+    achieved = tile_bytes / (tile_ms * 1e-3) / 1e9
+    roof_tile = {"kernel": "k_kacz_tile (fine level, one of 4 tile colours)", "bound": "hbm",
+                 "achieved": round(achieved, 1), "peak": hbm, "peak_source": src, "unit": "GB/s",
+                 "frac": round(achieved / hbm, 4), "traffic": TRAFFIC.get("k_kacz_tile"),
+                 "avg_launch_ms": round(tile_ms, 5), "algorithmic_bytes": int(tile_bytes)}
+    roof = roof_dot
+    roof_more = [roof_tile, roof_kacz] if w["kacz_order"] == 1 else [roof_kacz, roof_tile]
 
     out = {
         "metric": METRIC, "value": round(value, 3), "unit": "solves/s", "n_gpus": world,
@@ -316,11 +336,14 @@ def run_gb300(args, rank, world, local_rank):
         "dtype": "f32 cycle + f64 Krylov" if prec != W.WL_FP64 else "f64",
         "data": "synthetic (seeded U(1) Metropolis gauge, complex Gaussian right-hand sides)",
         "config": {"workload": "%s: %dx%d lattice, beta=%g, %d Metropolis sweeps, m=%.6f (smallest |eig| %g), "
-                               "%d grids, blocks %s, k=%d, %d RHS/step, %s(%d,%d) Kaczmarz cycle in %s, "
-                               "FGMRES(%d) with %d Gram-Schmidt pass(es) in FP64, tol %g"
+                               "%d grids, blocks %s, k=%d, %d RHS/step, %s(%d,%d) %s Kaczmarz cycle in %s, "
+                               "FGMRES(%d) with %d Gram-Schmidt pass(es) in FP64, Arnoldi matvec %s, "
+                               "FP64 true residual at restarts, tol %g"
                                % (args.workload, N, N, w["beta"], w["sweeps"], w["m"], w["target"],
                                   len(w["blocks"]) + 1, w["blocks"], w["k"], nrhs, w["cycle"], w["nu"], w["nu"],
-                                  ["fp64", "fp32", "fp32+bf16-storage"][prec], w["fgmres_m"], w["gs_passes"], TOL),
+                                  ["16-colour", "tile-coloured (8x8 tiles)"][w["kacz_order"]],
+                                  ["fp64", "fp32", "fp32+bf16-storage"][prec], w["fgmres_m"], w["gs_passes"],
+                                  "fp32" if w["arnoldi_matvec"] and prec != W.WL_FP64 else "fp64", TOL),
                    "nrhs": nrhs, "L": N, "precision": ["fp64", "fp32", "fp32_bf16"][prec],
                    "l2": "flushed (256 MB write) between timed steps", "parallelism": "replicas"},
         "iters_mean": round(sum(iters) / len(iters), 2), "iters_max": max(iters),
@@ -329,7 +352,7 @@ def run_gb300(args, rank, world, local_rank):
                                                                                          int(0.99 * len(times)))],
         "plain_fp64_single_rhs": {"value": round(1e3 / (sorted(p64)[1]), 3), "unit": "solves/s",
                                   "ms": sorted(p64)[1], "iters": inf64[0]["iters"]},
-        "e2e": e2e, "gpu_launches": int(launches), "roofline": roof, "roofline_kaczmarz": roof2, "clocks": clk,
+        "e2e": e2e, "gpu_launches": int(launches), "roofline": roof, "roofline_more": roof_more, "clocks": clk,
     }
     if not args.no_serving:
         out["serving"] = run_serving(args, rank, dev, W, torch)
@@ -382,7 +405,7 @@ def run_serving(args, rank, dev, W, torch):
             return {"unavailable": "no shift for %s" % nm}
         op = W.wilson_create(torch.from_numpy(w["U"]).to(dev), w["N"], w["m"])
         p = W.amg_params_default(k_r=w["k"], k_e=w["k"], seed=w["seed"], precision=W.WL_FP32, gs_passes=1,
-                                 nu_pre=4, nu_post=4)
+                                 nu_pre=4, nu_post=4, kacz_order=1, arnoldi_matvec=1)
         p.levels = len(w["blocks"]) + 1
         for l, b in enumerate(w["blocks"]):
             p.block[l] = b
@@ -442,7 +465,8 @@ def run_serving(args, rank, dev, W, torch):
             "closed-loop capacity)" % (rate, cap), "p50_ms": round(lats[len(lats) // 2], 2),
             "p99_ms": round(lats[min(len(lats) - 1, int(0.99 * len(lats)))], 2),
             "solves_per_s": round(solved / wall, 2), "true_relres_max": worst,
-            "cycle": "V(4,4) FP32, FGMRES(20) FP64, 1 Gram-Schmidt pass", "slots_per_config": slots,
+            "cycle": "V(4,4) FP32 tile-coloured Kaczmarz, FGMRES(20) FP64 (FP32 Arnoldi matvec), 1 Gram-Schmidt "
+                     "pass", "slots_per_config": slots,
             "hbm_budget_gb": args.serve_hbm_gb, "hbm_reserved_gb": round(reserved / (1 << 30), 2)}
 
 
@@ -469,6 +493,37 @@ def run_reference(args, rank, world):
                                        % res["setup_s"]},
             "e2e": {"value": round(value, 4), "unit": "solves/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
+
+
+def run_kernel_only(args):
+    """Set up the workload's hierarchy and time one kernel family on level 0
+    (three warm-up launches, then two inside the NVTX range 'cap')."""
+    import torch
+    from paper_1308_5992_gb300 import wilson_amg as W
+    from wl_inputs import workload
+    w = workload(args.workload)
+    if args.kacz_order >= 0:
+        w["kacz_order"] = args.kacz_order
+    dev = torch.device("cuda", 0)
+    N, nrhs = w["N"], max(1, args.nrhs or w["nrhs"])
+    prec = {"fp64": W.WL_FP64, "fp32": W.WL_FP32, "bf16": W.WL_FP32_BF16}[w["precision"]]
+    kind = {"dot": W.WL_K_GS_DOT, "axpy": W.WL_K_GS_AXPY, "kacz": W.WL_K_KACZ, "tile": W.WL_K_KACZ_TILE,
+            "dhat": W.WL_K_DHAT}[args.kernel_only]
+    op = W.wilson_create(torch.from_numpy(w["U"]).to(dev), N, w["m"])
+    p = W.amg_params_default(k_r=w["k"], k_e=w["k"], seed=w["seed"], zero_guess=1, precision=prec,
+                             kacz_order=w["kacz_order"])
+    p.levels = len(w["blocks"]) + 1
+    for l, b in enumerate(w["blocks"]):
+        p.block[l] = b
+    amg = W.amg_setup(op, p)
+    W.wl_time_kernel(amg, kind, 0, nrhs, prec, 3)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("cap")
+    ms = W.wl_time_kernel(amg, kind, 0, nrhs, prec, 2)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
+    print(json.dumps({"kernel_only": args.kernel_only, "workload": args.workload, "nrhs": nrhs,
+                      "avg_launch_ms": ms}))
 
 
 def run_study_rho(args):
@@ -555,6 +610,10 @@ def main():
         out = run_reference(args, rank, world)
         if out is not None:
             print(json.dumps(out))
+        return
+    if args.kernel_only:
+        if rank == 0:
+            run_kernel_only(args)
         return
     if args.study == "rho":
         if rank == 0:

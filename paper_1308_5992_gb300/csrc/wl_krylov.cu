@@ -72,37 +72,53 @@ static KS ks_layout(void *base, int m, int nrhs) {
 // thread t handles right-hand side t % R, so element e of a vector
 // ([n][2][nrhs] flattened) always belongs to rhs e % R.
 #define KCH 12  // dots per launch
-template <typename Tv>
-__global__ void k_mdot(const cx<Tv> *__restrict__ V, long vstride, int kc, const zd *__restrict__ w,
-                       long E, int R, zd *__restrict__ part) {
+// KC (the number of dots) is a template parameter: predicated-off FP64
+// FMAs still occupy the FP64 pipe, so a run-time count would cost every
+// launch the work of KCH dots
+template <typename Tv, int KC>
+__global__ void k_mdot(const cx<Tv> *__restrict__ V, long vstride, const zd *__restrict__ w, long E, int R,
+                       zd *__restrict__ part) {
   extern __shared__ unsigned char sm_raw[];
-  zd *sm = (zd *)sm_raw;  // [KCH][blockDim]
+  zd *sm = (zd *)sm_raw;  // [KC][blockDim]
   int t = threadIdx.x, nt = blockDim.x;
   int G = nt / R, q = t / R;
-  zd acc[KCH];
+  zd acc[KC];
 #pragma unroll
-  for (int k = 0; k < KCH; ++k) acc[k] = mk(0.0, 0.0);
+  for (int k = 0; k < KC; ++k) acc[k] = mk(0.0, 0.0);
   long stride = (long)gridDim.x * nt;
   for (long e = (long)blockIdx.x * nt + t; e < E; e += stride) {
     zd we = w[e];
-    zd v[KCH];
+    zd v[KC];
 #pragma unroll
-    for (int k = 0; k < KCH; ++k)
-      if (k < kc) v[k] = ccast<double>(V[k * vstride + e]);
+    for (int k = 0; k < KC; ++k) v[k] = ccast<double>(V[k * vstride + e]);
 #pragma unroll
-    for (int k = 0; k < KCH; ++k)
-      if (k < kc) cfmac(acc[k], v[k], we);
+    for (int k = 0; k < KC; ++k) cfmac(acc[k], v[k], we);
   }
 #pragma unroll
-  for (int k = 0; k < KCH; ++k) sm[k * nt + t] = acc[k];
+  for (int k = 0; k < KC; ++k) sm[k * nt + t] = acc[k];
   __syncthreads();
   for (int s = G >> 1; s > 0; s >>= 1) {
     if (q < s)
-      for (int k = 0; k < kc; ++k) sm[k * nt + t] = sm[k * nt + t] + sm[k * nt + t + s * R];
+#pragma unroll
+      for (int k = 0; k < KC; ++k) sm[k * nt + t] = sm[k * nt + t] + sm[k * nt + t + s * R];
     __syncthreads();
   }
   if (q == 0)
-    for (int k = 0; k < kc; ++k) part[((long)blockIdx.x * kc + k) * R + t] = sm[k * nt + t];
+#pragma unroll
+    for (int k = 0; k < KC; ++k) part[((long)blockIdx.x * KC + k) * R + t] = sm[k * nt + t];
+}
+
+template <typename Tv>
+static void launch_mdot(int kc, int nblk, int nt, size_t sm, cudaStream_t s, const cx<Tv> *V, long vstride,
+                        const zd *w, long E, int R, zd *part) {
+  switch (kc) {
+#define WL_MDOT(K) \
+  case K: k_mdot<Tv, K><<<nblk, nt, sm, s>>>(V, vstride, w, E, R, part); break;
+    WL_MDOT(1) WL_MDOT(2) WL_MDOT(3) WL_MDOT(4) WL_MDOT(5) WL_MDOT(6)
+    WL_MDOT(7) WL_MDOT(8) WL_MDOT(9) WL_MDOT(10) WL_MDOT(11) WL_MDOT(12)
+#undef WL_MDOT
+    default: break;
+  }
 }
 
 // out[r][k0 + k] (= or +=) sum over blocks of part[b][k][r]: one warp per
@@ -299,11 +315,13 @@ template <typename Tv>
 static int mdots(wl_amg *a, const cx<Tv> *V, long vstride, int kc, const zd *w, long E, int R, zd *out,
                  int ostride, int accumulate, zd *copy_to, cudaStream_t s) {
   RedCfg c = red_cfg(E, R);
-  size_t sm = sizeof(zd) * KCH * c.nt;
-  for (int k0 = 0; k0 < kc; k0 += KCH) {
-    int kk = std::min(KCH, kc - k0);
+  // as few launches as possible, their dot counts as even as possible
+  int nl = (kc + KCH - 1) / KCH;
+  for (int k0 = 0, l = 0, kk = 0; k0 < kc; k0 += kk, ++l) {
+    kk = (kc - k0 + (nl - l) - 1) / (nl - l);
+    size_t sm = sizeof(zd) * kk * c.nt;
     wl_count_launches(2);
-    k_mdot<Tv><<<c.nblk, c.nt, sm, s>>>(V + k0 * vstride, vstride, kk, w, E, R, a->red.as<zd>());
+    launch_mdot<Tv>(kk, c.nblk, c.nt, sm, s, V + k0 * vstride, vstride, w, E, R, a->red.as<zd>());
     k_mdot_final<<<WL_GRID(kk * R * 32, 256), 256, 0, s>>>(a->red.as<zd>(), c.nblk, kk, R, out, ostride, k0,
                                                            accumulate, copy_to);
   }

@@ -226,6 +226,29 @@ __device__ __forceinline__ void cp_async(void *smem, const void *gmem, int bytes
   else asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem));
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::); }
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+// two adjacent stored coefficients in one shared-memory load (16 bytes for
+// complex float, 8 for a bf16 pair; 2 x 16 for complex double)
+template <typename T>
+__device__ __forceinline__ void ld2(const zf *p, cx<T> &a0, cx<T> &a1) {
+  float4 v = *(const float4 *)p;
+  a0 = mk((T)v.x, (T)v.y);
+  a1 = mk((T)v.z, (T)v.w);
+}
+template <typename T>
+__device__ __forceinline__ void ld2(const zd *p, cx<T> &a0, cx<T> &a1) {
+  double2 u = *(const double2 *)p, v = *(const double2 *)(p + 1);
+  a0 = mk((T)u.x, (T)u.y);
+  a1 = mk((T)v.x, (T)v.y);
+}
+template <typename T>
+__device__ __forceinline__ void ld2(const zb *p, cx<T> &a0, cx<T> &a1) {
+  a0 = ld<T>(p);
+  a1 = ld<T>(p + 1);
+}
 
 // tile origin of block b for tile colour tc
 __device__ __forceinline__ void tile_origin(const Geo &g, int tc, int &A0, int &B0) {
@@ -254,26 +277,29 @@ __device__ __forceinline__ void tile_stage_rows(const Geo &g, int A0, int B0, co
 }
 
 // Several right-hand sides: a block of 4 R threads, thread (k, q) owns site k
-// of the current colour step and right-hand side r0 + q.  Shared memory: A
-// rows [64][36], den [64][2], r of tile + halo [100][2][R].  vec: r rows
-// start on 16-byte boundaries (16-byte copies), else one complex per copy.
+// of the current colour step and right-hand side r0 + q.  Shared memory: r
+// of tile + halo [100][2][R], den [64][2], and a ring of three colour steps'
+// stencil rows [3][4][36] filled by cp.async two steps ahead (so a block
+// needs about 55 KB at R = 32 and four blocks fit an SM).  vec: r rows start
+// on 16-byte boundaries (16-byte copies), else one complex per copy.
 template <typename T, typename S, int R>
 __global__ void __launch_bounds__(4 * R) k_kacz_tile(Geo g, int tc, const S *__restrict__ A,
                                                      const T *__restrict__ den, cx<T> *__restrict__ x,
                                                      cx<T> *__restrict__ r, int nrhs, int vec, T omega) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
-  S *As = (S *)sm_raw;
-  T *ds = (T *)(As + KT * KT * 36);
-  cx<T> *rs = (cx<T> *)(ds + KT * KT * 2);
+  cx<T> *rs = (cx<T> *)sm_raw;
+  T *ds = (T *)(rs + KTH * KTH * 2 * R);
+  S *Ar = (S *)(ds + KT * KT * 2);
   constexpr int NT = 4 * R;
   constexpr int E = 16 / (int)sizeof(cx<T>);  // complex numbers per 16-byte copy
   constexpr int CPR = R / E;                   // 16-byte pieces per staged row
+  constexpr int ROWC = 36 * (int)sizeof(S) / 16;  // 16-byte pieces of a stencil row
   int A0, B0;
   tile_origin(g, tc, A0, B0);
   int r0 = blockIdx.y * R;
   int Rc = min(R, nrhs - r0);
   int tid = threadIdx.x;
-  tile_stage_rows<T, S>(g, A0, B0, A, den, As, ds);
+  // group 0: r of tile + halo and the denominators
   if (vec) {
     for (int e = tid; e < KTH * KTH * 2 * CPR; e += NT) {
       int c = e % CPR, row = e / CPR, ls = row >> 1;
@@ -291,8 +317,27 @@ __global__ void __launch_bounds__(4 * R) k_kacz_tile(Geo g, int tc, const S *__r
       cp_async(rs + e, r + (h * 2 + (row & 1)) * nrhs + r0 + q, (int)sizeof(cx<T>));
     }
   }
-  cp_async_wait_all();
-  __syncthreads();
+  for (int e = tid; e < KT * KT * 2; e += NT) {
+    int ks = e >> 1;
+    int a = A0 + ks / KT, b = B0 + ks % KT;
+    long h = g.idx(a + b, a - b);
+    cp_async(ds + e, den + 2 * h + (e & 1), (int)sizeof(T));
+  }
+  cp_async_commit();
+  // stencil rows of colour step c (its four sites, quadrant order) -> ring slot c % 3
+  auto issue_rows = [&](int c) {
+    S *dst = Ar + (c % 3) * 4 * 36;
+    for (int e = tid; e < 4 * ROWC; e += NT) {
+      int kk = e / ROWC, c16 = e - kk * ROWC;
+      int i = (c >> 2) + 4 * (kk >> 1), j = (c & 3) + 4 * (kk & 1);
+      long h = g.idx(A0 + i + B0 + j, A0 + i - B0 - j);
+      cp_async((char *)(dst + kk * 36) + 16 * c16, (const char *)(A + h * 36) + 16 * c16, 16);
+    }
+  };
+  issue_rows(0);
+  cp_async_commit();
+  issue_rows(1);
+  cp_async_commit();
   const int k = tid / R, q = tid % R;
   const bool act = q < Rc;
   // thread (k, q) visits quadrant k of the tile, one site per colour step;
@@ -314,10 +359,15 @@ __global__ void __launch_bounds__(4 * R) k_kacz_tile(Geo g, int tc, const S *__r
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const int c = c0 + u;
+      // the slot of step c + 2 was last read in step c - 1, which ended with a barrier
+      if (c + 2 < 16) issue_rows(c + 2);
+      cp_async_commit();
+      cp_async_wait_group<2>();  // everything but the two newest groups: r, den, rows of step c
+      __syncthreads();
       int i = (c >> 2) + 4 * (k >> 1), j = (c & 3) + 4 * (k & 1);
       if (act) {
         int ks = i * KT + j;
-        const S *Ah = As + ks * 36;
+        const S *Ah = Ar + ((c % 3) * 4 + k) * 36;
         cx<T> rv[9][2];
 #pragma unroll
         for (int d = 0; d < 9; ++d) {
@@ -330,10 +380,7 @@ __global__ void __launch_bounds__(4 * R) k_kacz_tile(Geo g, int tc, const S *__r
         for (int t = 0; t < 2; ++t) {
           cx<T> a_[9][2];
 #pragma unroll
-          for (int d = 0; d < 9; ++d) {
-            a_[d][0] = ld<T>(Ah + d * 4 + t * 2 + 0);
-            a_[d][1] = ld<T>(Ah + d * 4 + t * 2 + 1);
-          }
+          for (int d = 0; d < 9; ++d) ld2<T>(Ah + d * 4 + t * 2, a_[d][0], a_[d][1]);
           cx<T> num = mk<T>(0, 0);
 #pragma unroll
           for (int d = 0; d < 9; ++d) {
@@ -346,9 +393,7 @@ __global__ void __launch_bounds__(4 * R) k_kacz_tile(Geo g, int tc, const S *__r
 #pragma unroll
           for (int d = 0; d < 9; ++d)
 #pragma unroll
-            for (int sp = 0; sp < 2; ++sp) {
-              r_sub(rv[d][sp], (sp == t) ? (T)1 : (T)-1, sv[t], a_[d][sp]);
-            }
+            for (int sp = 0; sp < 2; ++sp) r_sub(rv[d][sp], (sp == t) ? (T)1 : (T)-1, sv[t], a_[d][sp]);
         }
         long xo = x_at(c);
         x[xo] = xp[u][0] + sv[0];
@@ -656,10 +701,13 @@ static int launch_coop(const Level &L, const LevelOps &o, int sweeps, void *x, v
 // tile-coloured launch for tile colour tc (one quarter of a sweep)
 static bool tile_ok(int N) { return N >= 64 && N % (4 * KT) == 0; }
 
-// shared memory of a tile block: A rows, denominators and r of tile + halo
+// shared memory of a tile block.  One right-hand side: all 64 stencil rows,
+// denominators and r of tile + halo; several: r of tile + halo, denominators
+// and the three-step ring of stencil rows
 template <typename T, typename S>
 static size_t tile_smem(int R) {
-  return (size_t)KT * KT * 36 * sizeof(S) + (size_t)KT * KT * 2 * sizeof(T) + (size_t)KTH * KTH * 2 * R * sizeof(cx<T>);
+  size_t rows = R == 1 ? (size_t)KT * KT * 36 * sizeof(S) : (size_t)3 * 4 * 36 * sizeof(S);
+  return rows + (size_t)KT * KT * 2 * sizeof(T) + (size_t)KTH * KTH * 2 * R * sizeof(cx<T>);
 }
 
 template <typename T, typename S, int R>

@@ -722,6 +722,9 @@ extern "C" int amg_setup(wl_op *op, const amg_params *params, wl_amg **out) {
   a->op = op;
   wl::op_retain(op);
   a->prm = prm;
+  // the setup relaxes with the 16-colour ordering of Sec. 3.1 whatever
+  // ordering the solve phase uses (kacz_order is restored below)
+  a->prm.kacz_order = 0;
   a->L = prm.levels;
   a->cap = 0;
   a->h_small = nullptr;
@@ -767,6 +770,7 @@ extern "C" int amg_setup(wl_op *op, const amg_params *params, wl_amg **out) {
   if (!rc) rc = prm.setup_cycle == 1 ? visit_superv(S, 1, false, prm.setup_mu[1])
                                      : visit(S, 1, false, prm.setup_mu[1]);
   if (!rc) rc = interp_e(S, 0);
+  a->prm.kacz_order = prm.kacz_order;
   if (!rc) rc = wl::hier_finish(a);
   if (S.cs) cusolverDnDestroy(S.cs);
   cudaStreamSynchronize(S.s);

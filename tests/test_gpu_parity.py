@@ -346,6 +346,25 @@ def test_gpu_setup_quality(O, ops):
     assert info[0]["iters"] <= 2 * oi["iters"] + 5, (info, oi)
 
 
+def test_setup_independent_of_solve_options(ops, tmp_path):
+    """The setup relaxes with the 16-colour ordering whatever the solve
+    phase uses: hierarchies built with either Kaczmarz ordering, launch form
+    or Arnoldi matvec precision are byte-identical files."""
+    w, op = ops("T64")
+    files = []
+    for kw in (dict(), dict(kacz_order=1, arnoldi_matvec=1, sweep_kernel=1)):
+        p = W.amg_params_default(k_r=w["k"], k_e=w["k"], seed=w["seed"], **kw)
+        for l, b in enumerate(w["blocks"]):
+            p.block[l] = b
+        p.levels = len(w["blocks"]) + 1
+        amg = W.amg_setup(op, p)
+        path = str(tmp_path / ("h%d.wlh" % len(files)))
+        W.amg_export(amg, path)
+        files.append(open(path, "rb").read())
+        amg.close()
+    assert files[0] == files[1]
+
+
 def test_gpu_super_v_setup_quality(O, ops):
     """Sec. 4.2's super-V setup on the GPU: the stand-alone W(4,4) cycle
     converges and GMRES(32) needs iterations within the band of the oracle's

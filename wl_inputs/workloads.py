@@ -73,13 +73,15 @@ WORKLOADS["T64"] = dict(N=64, beta=6.0, sweeps=100, target=1e-2, seed=13, blocks
 
 
 # solve-cycle parameters (defaults: V(2,2), FGMRES(20), two Gram-Schmidt passes)
-_SOLVE = dict(nu=2, cycle="V", fgmres_m=20, gs_passes=2, kacz_order=0)
+_SOLVE = dict(nu=2, cycle="V", fgmres_m=20, gs_passes=2, kacz_order=0, arnoldi_matvec=0)
 for _name, _w in WORKLOADS.items():
     for _k, _v in _SOLVE.items():
         _w.setdefault(_k, _v)
-# the batched mixed-precision workload: smoothing and Gram-Schmidt passes are
-# not fixed by its description; chosen by measurement (one pass, V(4,4))
-WORKLOADS["C4"].update(nu=4, gs_passes=1)
+# the batched mixed-precision workload: smoothing, Gram-Schmidt passes, the
+# Kaczmarz ordering and the precision of the Arnoldi matvec are not fixed by
+# its description; chosen by measurement (V(4,4), one pass, tile-coloured
+# sweeps, FP32 matvec inside a restart cycle with FP64 true residuals)
+WORKLOADS["C4"].update(nu=4, gs_passes=1, kacz_order=1, arnoldi_matvec=1)
 
 
 def _shifts():
