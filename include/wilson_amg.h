@@ -191,9 +191,10 @@ int amg_fgmres(wl_amg *amg, const void *bhat, void *x, int nrhs, double tol, wl_
  * stopping nu (iters[r]).  rho, iters: host [nrhs]; hist: host
  * [nrhs][maxit + 1] or NULL, |e^k| for k <= iters[r] (rest untouched).
  * x (device, same layout) receives the error after the batch's last
- * iteration.  Returns WL_OK if every right-hand side met tol,
- * WL_NOT_CONVERGED otherwise; WL_EINVAL for nrhs outside 1..256, tol < 0
- * or maxit < 1; WL_NAN if a norm became non-finite. */
+ * iteration.  A right-hand side whose error norm overflows (a divergent
+ * cycle) stops there, keeping the ratio of its last two finite norms.
+ * Returns WL_OK if every right-hand side met tol, WL_NOT_CONVERGED
+ * otherwise; WL_EINVAL for nrhs outside 1..256, tol < 0 or maxit < 1. */
 int amg_rho(wl_amg *amg, const void *x0, void *x, int nrhs, double tol, int maxit, double *rho, int *iters,
             double *hist);
 

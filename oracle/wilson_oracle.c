@@ -984,7 +984,10 @@ int or_fgmres(const or_hier *h, const cplx *b, cplx *x, double tol, int mrestart
  * is the error, e^nu = (I - M A_0) e^{nu-1} with e^0 = x0.  rho is
  * |e^nu| / |e^{nu-1}| at the first nu with |e^nu| <= tol |e^0|, or at
  * nu = maxit.  hist (optional, maxit + 1 entries): |e^k| for k <= nu.
- * Returns 0 when the tolerance was met, 1 when maxit was reached. */
+ * Reading: a divergent iteration (the paper's definition presumes
+ * convergence) stops when the error norm overflows; rho is then the ratio of
+ * the last two finite norms and nu the last finite iteration.
+ * Returns 0 when the tolerance was met, 1 otherwise. */
 int or_rho(const or_hier *h, const cplx *x0, double tol, int maxit, int nu1, int nu2,
            int gamma, int order, double *rho_out, int *iters_out, double *hist) {
   int n = h->A[0].nrow;
@@ -1000,8 +1003,9 @@ int or_rho(const or_hier *h, const cplx *x0, double tol, int maxit, int nu1, int
     rc = or_cycle(h, 0, w, c, nu1, nu2, gamma, order);
     if (rc) break;
     for (int i = 0; i < n; ++i) e[i] -= c[i];   /* x + M(-A_0 x) = x - M(A_0 x) */
-    ++nu;
     double cur = vnorm(n, e);
+    if (!isfinite(cur)) break;                  /* diverged past overflow: keep the last ratio */
+    ++nu;
     if (hist) hist[nu] = cur;
     rho = prev > 0 ? cur / prev : 0;
     prev = cur;

@@ -560,7 +560,7 @@ extern "C" int amg_rho(wl_amg *a, const void *x0, void *x, int nrhs, double tol,
     iters[r] = 0;
     if (hist) hist[(size_t)r * (maxit + 1)] = n0[r];
   }
-  int left = nrhs;
+  int left = nrhs, diverged = 0;
   for (int nu = 1; nu <= maxit && left > 0; ++nu) {
     WL_TRY(wl::dhat_apply_dev(a->op, e, 0, w, nrhs, s));
     if (prec == WL_FP64) {
@@ -577,7 +577,12 @@ extern "C" int amg_rho(wl_amg *a, const void *x0, void *x, int nrhs, double tol,
     WL_TRY(wl::fg_norms(a, e, nrhs, cur.data()));
     for (int r = 0; r < nrhs; ++r) {
       if (done[r]) continue;
-      if (!std::isfinite(cur[r])) return WL_NAN;
+      if (!std::isfinite(cur[r])) {  // diverged past overflow: keep the last finite ratio
+        done[r] = 1;
+        --left;
+        ++diverged;
+        continue;
+      }
       rho[r] = prev[r] > 0 ? cur[r] / prev[r] : 0;
       iters[r] = nu;
       if (hist) hist[(size_t)r * (maxit + 1) + nu] = cur[r];
@@ -590,7 +595,7 @@ extern "C" int amg_rho(wl_amg *a, const void *x0, void *x, int nrhs, double tol,
   }
   WL_TRY(wl::from_internal(e, (zd *)x, n2, nrhs, WL_FP64, s));
   WL_CUDA(cudaStreamSynchronize(s));
-  return left ? WL_NOT_CONVERGED : WL_OK;
+  return (left || diverged) ? WL_NOT_CONVERGED : WL_OK;
 }
 
 extern "C" int amg_solve(wl_amg *a, const void *b, void *x, int nrhs, double tol, wl_info *info) {

@@ -278,7 +278,7 @@ __device__ __forceinline__ void tile_stage_rows(const Geo &g, int A0, int B0, co
 
 // Several right-hand sides: a block of 4 R threads, thread (k, q) owns site k
 // of the current colour step and right-hand side r0 + q.  Shared memory: r
-// of tile + halo [100][2][R], den [64][2], and a ring of three colour steps'
+// of tile + halo [100][2][R], omega / den [64][2], and a ring of three colour steps'
 // stencil rows [3][4][36] filled by cp.async two steps ahead (so a block
 // needs about 55 KB at R = 32 and four blocks fit an SM).  vec: r rows start
 // on 16-byte boundaries (16-byte copies), else one complex per copy.
@@ -299,7 +299,7 @@ __global__ void __launch_bounds__(4 * R) k_kacz_tile(Geo g, int tc, const S *__r
   int r0 = blockIdx.y * R;
   int Rc = min(R, nrhs - r0);
   int tid = threadIdx.x;
-  // group 0: r of tile + halo and the denominators
+  // group 0: r of tile + halo
   if (vec) {
     for (int e = tid; e < KTH * KTH * 2 * CPR; e += NT) {
       int c = e % CPR, row = e / CPR, ls = row >> 1;
@@ -321,7 +321,7 @@ __global__ void __launch_bounds__(4 * R) k_kacz_tile(Geo g, int tc, const S *__r
     int ks = e >> 1;
     int a = A0 + ks / KT, b = B0 + ks % KT;
     long h = g.idx(a + b, a - b);
-    cp_async(ds + e, den + 2 * h + (e & 1), (int)sizeof(T));
+    ds[e] = omega / den[2 * h + (e & 1)];  // the step scale, once per site and spin
   }
   cp_async_commit();
   // stencil rows of colour step c (its four sites, quadrant order) -> ring slot c % 3
@@ -381,15 +381,16 @@ __global__ void __launch_bounds__(4 * R) k_kacz_tile(Geo g, int tc, const S *__r
           cx<T> a_[9][2];
 #pragma unroll
           for (int d = 0; d < 9; ++d) ld2<T>(Ah + d * 4 + t * 2, a_[d][0], a_[d][1]);
-          cx<T> num = mk<T>(0, 0);
+          cx<T> n0 = mk<T>(0, 0), n1 = mk<T>(0, 0);  // two chains: independent FMAs in flight
 #pragma unroll
           for (int d = 0; d < 9; ++d) {
-            cfma(num, a_[d][0], rv[d][0]);
-            cfma(num, mk<T>(-a_[d][1].re, -a_[d][1].im), rv[d][1]);
+            cx<T> &nn = (d & 1) ? n1 : n0;
+            cfma(nn, a_[d][0], rv[d][0]);
+            cfma(nn, mk<T>(-a_[d][1].re, -a_[d][1].im), rv[d][1]);
           }
-          T sc = omega / ds[2 * ks + t];
+          T sc = ds[2 * ks + t];
           if (t) sc = -sc;
-          sv[t] = sc * num;
+          sv[t] = sc * (n0 + n1);
 #pragma unroll
           for (int d = 0; d < 9; ++d)
 #pragma unroll

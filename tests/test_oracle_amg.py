@@ -466,3 +466,16 @@ def test_super_v_setup(O, h64):
     _, iv = hs.fgmres(bh, tol=1e-8, m=32, max_restarts=5, nu1=4, nu2=4, gamma=2)
     _, iw = h.fgmres(bh, tol=1e-8, m=32, max_restarts=5, nu1=4, nu2=4, gamma=2)
     assert iv["status"] == 0 and iv["iters"] <= 2 * iw["iters"] + 5, (iv, iw, rho_v, rho_w)
+
+
+def test_rho_divergent_cycle_stops_at_overflow(O, h32):
+    """A cycle whose coarse correction is scaled up diverges; the estimate
+    stops at the last finite error norm and reports the ratio of the last two
+    (the definition in Sec. 4 presumes convergence)."""
+    Pw, As = h32.export()
+    hb = O.Hierarchy.from_arrays(h32.N, h32.U, h32.m, h32.Nl, h32.Bl[:-1], Pw, [a * 1e-6 for a in As])
+    x0 = cgauss(4, 1, h32.n(0))
+    rho, nu, hist, met = hb.rho(x0, tol=1e-8, maxit=100, nu1=1, nu2=1, gamma=1)
+    assert not met and 2 <= nu < 100
+    assert np.all(np.isfinite(hist)) and hist[-1] > 1e100
+    assert rho > 1e4 and rho == hist[-1] / hist[-2]
