@@ -274,10 +274,16 @@ int wl_time_kernel(wl_amg *amg, int kind, int level, int nrhs, int prec, int rep
 /* Kaczmarz launch form used on `level` (not the coarsest) for `nrhs`
  * right-hand sides in precision `prec`: form 0 = one launch per colour,
  * 1 = cooperative launch with *param blocks, 2 = tile-coloured kernel with
- * right-hand-side chunk *param; *us = the autotuner's measured time of one
+ * right-hand-side chunk (*param & 255) and right-hand sides per thread
+ * (*param >> 8); *us = the autotuner's measured time of one
  * sweep in microseconds, 0 when the form was not measured (explicit
  * sweep_kernel, or no cycle of that width yet).  Errors: WL_EINVAL. */
 int amg_sweep_form(wl_amg *amg, int level, int nrhs, int prec, int *form, int *param, float *us);
+/* amg_kaczmarz with an explicit launch form (form and param as reported by
+ * amg_sweep_form; the form must belong to the hierarchy's ordering on that
+ * level), for tests and measurements: every form of one ordering computes
+ * the same numbers.  Errors: WL_EINVAL (no such form). */
+int amg_kaczmarz_form(wl_amg *amg, int level, void *x, void *r, int nrhs, int sweeps, int prec, int form, int param);
 /* Number of kernels this library has launched in this process (a captured
  * graph counts each of its kernel nodes at every replay). */
 long long wl_launch_count(void);

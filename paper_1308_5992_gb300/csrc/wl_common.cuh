@@ -210,7 +210,7 @@ struct LevelOps {
 // launch form of a Kaczmarz sweep on one level, chosen by the autotuner
 // (measured) or by the heuristic: form 0 = one launch per colour, 1 = one
 // cooperative launch for all colours (param = blocks), 2 = tile-coloured
-// kernel (param = right-hand-side chunk R)
+// kernel (param = right-hand-side chunk R | right-hand sides per thread << 8)
 struct KTune {
   int nrhs, prec, form, param;
   float us;  // measured time of one sweep (0 if not measured)

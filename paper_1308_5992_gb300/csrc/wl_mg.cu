@@ -276,21 +276,25 @@ __device__ __forceinline__ void tile_stage_rows(const Geo &g, int A0, int B0, co
   }
 }
 
-// Several right-hand sides: a block of 4 R threads, thread (k, q) owns site k
-// of the current colour step and right-hand side r0 + q.  Shared memory: r
-// of tile + halo [100][2][R], omega / den [64][2], and a ring of three colour steps'
-// stencil rows [3][4][36] filled by cp.async two steps ahead (so a block
-// needs about 55 KB at R = 32 and four blocks fit an SM).  vec: r rows start
-// on 16-byte boundaries (16-byte copies), else one complex per copy.
-template <typename T, typename S, int R>
-__global__ void __launch_bounds__(4 * R) k_kacz_tile(Geo g, int tc, const S *__restrict__ A,
-                                                     const T *__restrict__ den, cx<T> *__restrict__ x,
-                                                     cx<T> *__restrict__ r, int nrhs, int vec, T omega) {
+// Several right-hand sides: a block of 4 R / RPT threads, thread (k, q) owns
+// site k of the current colour step and right-hand sides r0 + q + j R / RPT
+// (j < RPT), which share the stencil coefficients and the index arithmetic.
+// Shared memory: r of tile + halo [100][2][R], omega / den [64][2], and a
+// ring of three colour steps' stencil rows [3][4][36] filled by cp.async two
+// steps ahead (about 55 KB at R = 32, so four blocks fit an SM).  vec: r rows
+// start on 16-byte boundaries (16-byte copies), else one complex per copy.
+// Every right-hand side sees the same operations in the same order for any
+// RPT, so the variants agree bit for bit.
+template <typename T, typename S, int R, int RPT>
+__global__ void __launch_bounds__(4 * R / RPT) k_kacz_tile(Geo g, int tc, const S *__restrict__ A,
+                                                           const T *__restrict__ den, cx<T> *__restrict__ x,
+                                                           cx<T> *__restrict__ r, int nrhs, int vec, T omega) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   cx<T> *rs = (cx<T> *)sm_raw;
   T *ds = (T *)(rs + KTH * KTH * 2 * R);
   S *Ar = (S *)(ds + KT * KT * 2);
-  constexpr int NT = 4 * R;
+  constexpr int NT = 4 * R / RPT;
+  constexpr int RQ = R / RPT;                  // threads per site
   constexpr int E = 16 / (int)sizeof(cx<T>);  // complex numbers per 16-byte copy
   constexpr int CPR = R / E;                   // 16-byte pieces per staged row
   constexpr int ROWC = 36 * (int)sizeof(S) / 16;  // 16-byte pieces of a stencil row
@@ -338,23 +342,28 @@ __global__ void __launch_bounds__(4 * R) k_kacz_tile(Geo g, int tc, const S *__r
   cp_async_commit();
   issue_rows(1);
   cp_async_commit();
-  const int k = tid / R, q = tid % R;
-  const bool act = q < Rc;
+  const int k = tid / RQ, q0 = tid % RQ;
+  bool act[RPT];
+#pragma unroll
+  for (int m = 0; m < RPT; ++m) act[m] = q0 + m * RQ < Rc;
   // thread (k, q) visits quadrant k of the tile, one site per colour step;
   // x of the site four steps ahead is loaded while the current step runs
   // (a ring of four), so the HBM latency of x is off the step's critical path
   auto x_at = [&](int c) -> long {
     int i = (c >> 2) + 4 * (k >> 1), j = (c & 3) + 4 * (k & 1);
-    return (long)g.idx(A0 + i + B0 + j, A0 + i - B0 - j) * 2 * nrhs + r0 + q;
+    return (long)g.idx(A0 + i + B0 + j, A0 + i - B0 - j) * 2 * nrhs + r0 + q0;
   };
-  cx<T> xp[4][2];
+  cx<T> xp[4][RPT][2];
 #pragma unroll
-  for (int u = 0; u < 4; ++u)
-    if (act) {
-      long xo = x_at(u);
-      xp[u][0] = x[xo];
-      xp[u][1] = x[xo + nrhs];
-    }
+  for (int u = 0; u < 4; ++u) {
+    long xo = x_at(u);
+#pragma unroll
+    for (int m = 0; m < RPT; ++m)
+      if (act[m]) {
+        xp[u][m][0] = x[xo + m * RQ];
+        xp[u][m][1] = x[xo + m * RQ + nrhs];
+      }
+  }
   for (int c0 = 0; c0 < 16; c0 += 4) {
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
@@ -362,53 +371,66 @@ __global__ void __launch_bounds__(4 * R) k_kacz_tile(Geo g, int tc, const S *__r
       // the slot of step c + 2 was last read in step c - 1, which ended with a barrier
       if (c + 2 < 16) issue_rows(c + 2);
       cp_async_commit();
-      cp_async_wait_group<2>();  // everything but the two newest groups: r, den, rows of step c
+      cp_async_wait_group<2>();  // everything but the two newest groups: r, rows of step c
       __syncthreads();
       int i = (c >> 2) + 4 * (k >> 1), j = (c & 3) + 4 * (k & 1);
-      if (act) {
+      if (act[0]) {
         int ks = i * KT + j;
         const S *Ah = Ar + ((c % 3) * 4 + k) * 36;
-        cx<T> rv[9][2];
+        cx<T> rv[RPT][9][2];
 #pragma unroll
         for (int d = 0; d < 9; ++d) {
           int ls = (i + d / 3) * KTH + (j + d % 3);  // (i + da + 1, j + db + 1)
-          rv[d][0] = rs[(ls * 2) * R + q];
-          rv[d][1] = rs[(ls * 2 + 1) * R + q];
+#pragma unroll
+          for (int m = 0; m < RPT; ++m) {
+            rv[m][d][0] = rs[(ls * 2) * R + q0 + m * RQ];
+            rv[m][d][1] = rs[(ls * 2 + 1) * R + q0 + m * RQ];
+          }
         }
-        cx<T> sv[2];
+        cx<T> sv[RPT][2];
 #pragma unroll
         for (int t = 0; t < 2; ++t) {
           cx<T> a_[9][2];
 #pragma unroll
           for (int d = 0; d < 9; ++d) ld2<T>(Ah + d * 4 + t * 2, a_[d][0], a_[d][1]);
-          cx<T> n0 = mk<T>(0, 0), n1 = mk<T>(0, 0);  // two chains: independent FMAs in flight
-#pragma unroll
-          for (int d = 0; d < 9; ++d) {
-            cx<T> &nn = (d & 1) ? n1 : n0;
-            cfma(nn, a_[d][0], rv[d][0]);
-            cfma(nn, mk<T>(-a_[d][1].re, -a_[d][1].im), rv[d][1]);
-          }
           T sc = ds[2 * ks + t];
           if (t) sc = -sc;
-          sv[t] = sc * (n0 + n1);
 #pragma unroll
-          for (int d = 0; d < 9; ++d)
+          for (int m = 0; m < RPT; ++m) {
+            cx<T> n0 = mk<T>(0, 0), n1 = mk<T>(0, 0);  // two chains: independent FMAs in flight
 #pragma unroll
-            for (int sp = 0; sp < 2; ++sp) r_sub(rv[d][sp], (sp == t) ? (T)1 : (T)-1, sv[t], a_[d][sp]);
+            for (int d = 0; d < 9; ++d) {
+              cx<T> &nn = (d & 1) ? n1 : n0;
+              cfma(nn, a_[d][0], rv[m][d][0]);
+              cfma(nn, mk<T>(-a_[d][1].re, -a_[d][1].im), rv[m][d][1]);
+            }
+            sv[m][t] = sc * (n0 + n1);
+#pragma unroll
+            for (int d = 0; d < 9; ++d)
+#pragma unroll
+              for (int sp = 0; sp < 2; ++sp) r_sub(rv[m][d][sp], (sp == t) ? (T)1 : (T)-1, sv[m][t], a_[d][sp]);
+          }
         }
-        long xo = x_at(c);
-        x[xo] = xp[u][0] + sv[0];
-        x[xo + nrhs] = xp[u][1] + sv[1];
-        if (c + 4 < 16) {
-          long xn = x_at(c + 4);
-          xp[u][0] = x[xn];
-          xp[u][1] = x[xn + nrhs];
+        long xo = x_at(c), xn = c + 4 < 16 ? x_at(c + 4) : 0;
+#pragma unroll
+        for (int m = 0; m < RPT; ++m) {
+          if (!act[m]) continue;
+          x[xo + m * RQ] = xp[u][m][0] + sv[m][0];
+          x[xo + m * RQ + nrhs] = xp[u][m][1] + sv[m][1];
+          if (c + 4 < 16) {
+            xp[u][m][0] = x[xn + m * RQ];
+            xp[u][m][1] = x[xn + m * RQ + nrhs];
+          }
         }
 #pragma unroll
         for (int d = 0; d < 9; ++d) {
           int ls = (i + d / 3) * KTH + (j + d % 3);
-          rs[(ls * 2) * R + q] = rv[d][0];
-          rs[(ls * 2 + 1) * R + q] = rv[d][1];
+#pragma unroll
+          for (int m = 0; m < RPT; ++m)
+            if (act[m]) {
+              rs[(ls * 2) * R + q0 + m * RQ] = rv[m][d][0];
+              rs[(ls * 2 + 1) * R + q0 + m * RQ] = rv[m][d][1];
+            }
         }
       }
       __syncthreads();
@@ -711,24 +733,28 @@ static size_t tile_smem(int R) {
   return rows + (size_t)KT * KT * 2 * sizeof(T) + (size_t)KTH * KTH * 2 * R * sizeof(cx<T>);
 }
 
-template <typename T, typename S, int R>
+template <typename T, typename S, int R, int RPT>
 static int launch_tile_r(const Level &L, const LevelOps &o, int tc, void *x, void *r, int nrhs, double omega,
                          cudaStream_t s) {
   size_t smem = tile_smem<T, S>(R);
   // set once per instantiation (thread-safe static initialisation)
-  static const cudaError_t attr = cudaFuncSetAttribute((const void *)k_kacz_tile<T, S, R>,
+  static const cudaError_t attr = cudaFuncSetAttribute((const void *)k_kacz_tile<T, S, R, RPT>,
                                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   WL_CUDA(attr);
   int vec = ((uintptr_t)r % 16 == 0) && (sizeof(T) == 8 || nrhs % 2 == 0);
   dim3 grid((L.N / (2 * KT)) * (L.N / (4 * KT)), (nrhs + R - 1) / R);
-  k_kacz_tile<T, S, R><<<grid, 4 * R, smem, s>>>(L.geo, tc, o.A.as<S>(), o.den.as<T>(), (cx<T> *)x, (cx<T> *)r,
-                                                 nrhs, vec, (T)omega);
+  k_kacz_tile<T, S, R, RPT><<<grid, 4 * R / RPT, smem, s>>>(L.geo, tc, o.A.as<S>(), o.den.as<T>(), (cx<T> *)x,
+                                                            (cx<T> *)r, nrhs, vec, (T)omega);
   return WL_OK;
 }
 
-// right-hand-side chunk of the tile kernel: the smallest of 8, 16, 32
-// (FP64: 8, 16) that covers nrhs, so that few lanes idle and shared memory
-// stays below 64 KB (FP32) or 90 KB (FP64) per block
+// launch parameter of the tile kernel: R | RPT << 8 (right-hand-side chunk R,
+// right-hand sides per thread RPT; RPT = 0 reads as 1)
+static inline int tile_param(int R, int rpt) { return R | (rpt << 8); }
+
+// default chunk: the smallest of 8, 16, 32 (FP64: 8, 16) that covers nrhs,
+// so that few lanes idle and shared memory stays below 64 KB (FP32) or
+// 90 KB (FP64) per block; one right-hand side per thread
 static int tile_default_R(int nrhs, int prec) {
   if (nrhs <= 8) return 8;
   if (prec == WL_FP64 || nrhs <= 16) return 16;
@@ -737,23 +763,32 @@ static int tile_default_R(int nrhs, int prec) {
 
 template <typename T, typename S>
 static int launch_tile(const Level &L, const LevelOps &o, int tc, void *x, void *r, int nrhs, double omega,
-                       cudaStream_t s, int R) {
+                       cudaStream_t s, int param) {
   if (nrhs == 1) {
     size_t smem = tile_smem<T, S>(1);
     k_kacz_tile1<T, S><<<(L.N / (2 * KT)) * (L.N / (4 * KT)), 128, smem, s>>>(
         L.geo, tc, o.A.as<S>(), o.den.as<T>(), (cx<T> *)x, (cx<T> *)r, (T)omega);
     return WL_OK;
   }
-  if (R == 8) return launch_tile_r<T, S, 8>(L, o, tc, x, r, nrhs, omega, s);
-  if (R == 16 || sizeof(T) == 8) return launch_tile_r<T, S, 16>(L, o, tc, x, r, nrhs, omega, s);
-  return launch_tile_r<T, S, (sizeof(T) == 8 ? 16 : 32)>(L, o, tc, x, r, nrhs, omega, s);
+  int R = param & 255, rpt = std::max(1, param >> 8);
+  if (R == 8) return launch_tile_r<T, S, 8, 1>(L, o, tc, x, r, nrhs, omega, s);
+  if constexpr (sizeof(T) == 8) {  // FP64: chunks up to 16, one right-hand side per thread
+    return launch_tile_r<T, S, 16, 1>(L, o, tc, x, r, nrhs, omega, s);
+  } else {
+    if (R == 16) {
+      if (rpt == 2) return launch_tile_r<T, S, 16, 2>(L, o, tc, x, r, nrhs, omega, s);
+      return launch_tile_r<T, S, 16, 1>(L, o, tc, x, r, nrhs, omega, s);
+    }
+    if (rpt == 2) return launch_tile_r<T, S, 32, 2>(L, o, tc, x, r, nrhs, omega, s);
+    return launch_tile_r<T, S, 32, 1>(L, o, tc, x, r, nrhs, omega, s);
+  }
 }
 
 int kaczmarz_tile(wl_amg *a, int l, int prec, void *x, void *r, int nrhs, int tc, cudaStream_t s, int R) {
   const Level &L = a->lev[l];
   if (!tile_ok(L.N)) return WL_EINVAL;
   const LevelOps &o = ops_of(L, prec);
-  if (R <= 0) R = tile_default_R(nrhs, prec);
+  if (R <= 0) R = tile_param(tile_default_R(nrhs, prec), 1);
   wl_count_launches(1);
   if (prec == WL_FP64) return launch_tile<double, zd>(L, o, tc, x, r, nrhs, a->prm.omega, s, R);
   if (prec == WL_FP32) return launch_tile<float, zf>(L, o, tc, x, r, nrhs, a->prm.omega, s, R);
@@ -807,7 +842,7 @@ KTune sweep_form_of(wl_amg *a, int l, int prec, int nrhs) {
       if (k.nrhs == nrhs && k.prec == prec && (k.form == 2) == tile) return k;
   if (tile) {
     t.form = 2;
-    t.param = tile_default_R(nrhs, prec);
+    t.param = tile_param(tile_default_R(nrhs, prec), 1);
     return t;
   }
   int maxb = coop_max_blocks(prec);
@@ -846,12 +881,14 @@ int autotune_sweeps(wl_amg *a, int nrhs, int prec, cudaStream_t s) {
     if (have) continue;
     std::vector<KTune> cand;
     if (tile) {
-      for (int R : {8, 16, 32}) {
-        if (prec == WL_FP64 && R > 16) continue;
-        if (nrhs > 1 && R / 2 >= nrhs && R > 8) continue;  // mostly idle lanes
-        cand.push_back(KTune{nrhs, prec, 2, nrhs == 1 ? 1 : R, 0.f});
-        if (nrhs == 1) break;
-      }
+      if (nrhs == 1) cand.push_back(KTune{nrhs, prec, 2, 1, 0.f});
+      else
+        for (int R : {8, 16, 32}) {
+          if (prec == WL_FP64 && R > 16) continue;
+          if (R / 2 >= nrhs && R > 8) continue;  // mostly idle lanes
+          cand.push_back(KTune{nrhs, prec, 2, tile_param(R, 1), 0.f});
+          if (R >= 16 && prec != WL_FP64) cand.push_back(KTune{nrhs, prec, 2, tile_param(R, 2), 0.f});
+        }
     } else {
       cand.push_back(KTune{nrhs, prec, 0, 0, 0.f});
       int maxb = coop_max_blocks(prec);
@@ -1054,11 +1091,25 @@ extern "C" int amg_level_apply(wl_amg *a, int level, const void *x, void *y, int
   return WL_OK;
 }
 
-extern "C" int amg_kaczmarz(wl_amg *a, int level, void *x, void *r, int nrhs, int sweeps, int prec) {
-  WL_TRY(check_amg(a, level, nrhs, prec, "amg_kaczmarz"));
+// form < 0: the solver's own choice; else an explicit launch form (KTune)
+static int kaczmarz_entry(wl_amg *a, int level, void *x, void *r, int nrhs, int sweeps, int prec, int form,
+                          int param, const char *who) {
+  WL_TRY(check_amg(a, level, nrhs, prec, who));
   if (!x || !r || sweeps < 0 || level == a->L - 1) {
-    wl_set_error("amg_kaczmarz: invalid argument (the coarsest level is not relaxed)");
+    wl_set_error("%s: invalid argument (the coarsest level is not relaxed)", who);
     return WL_EINVAL;
+  }
+  if (form >= 0) {
+    const Level &L = a->lev[level];
+    bool tile = a->prm.kacz_order == 1 && wl::tile_ok(L.N);
+    int R = param & 255, rpt = std::max(1, param >> 8);
+    bool ok = tile ? (form == 2 && (nrhs == 1 || ((R == 8 && rpt == 1) || ((R == 16 || R == 32) && rpt <= 2))) &&
+                      !(prec == WL_FP64 && (R > 16 || rpt > 1)))
+                   : ((form == 0) || (form == 1 && param >= 1));
+    if (!ok) {
+      wl_set_error("%s: launch form %d / %d does not exist for this level and ordering", who, form, param);
+      return WL_EINVAL;
+    }
   }
   cudaStream_t s = a->op->stream;
   int n2 = a->lev[level].n * 2;
@@ -1069,11 +1120,29 @@ extern "C" int amg_kaczmarz(wl_amg *a, int level, void *x, void *r, int nrhs, in
   WL_TRY(sb.b[1].alloc(vb));
   WL_TRY(wl::to_internal((const zd *)x, sb.b[0].p, n2, nrhs, pin, s));
   WL_TRY(wl::to_internal((const zd *)r, sb.b[1].p, n2, nrhs, pin, s));
-  WL_TRY(wl::kaczmarz_sweeps(a, level, prec, sb.b[0].p, sb.b[1].p, nrhs, sweeps, s));
+  if (form < 0) {
+    WL_TRY(wl::kaczmarz_sweeps(a, level, prec, sb.b[0].p, sb.b[1].p, nrhs, sweeps, s));
+  } else if (sweeps > 0) {
+    KTune t{nrhs, prec, form, param, 0.f};
+    WL_TRY(wl::run_sweeps(a, level, prec, sb.b[0].p, sb.b[1].p, nrhs, sweeps, t, s));
+  }
   WL_TRY(wl::from_internal(sb.b[0].p, (zd *)x, n2, nrhs, pin, s));
   WL_TRY(wl::from_internal(sb.b[1].p, (zd *)r, n2, nrhs, pin, s));
   WL_CUDA(cudaStreamSynchronize(s));
   return WL_OK;
+}
+
+extern "C" int amg_kaczmarz(wl_amg *a, int level, void *x, void *r, int nrhs, int sweeps, int prec) {
+  return kaczmarz_entry(a, level, x, r, nrhs, sweeps, prec, -1, 0, "amg_kaczmarz");
+}
+
+extern "C" int amg_kaczmarz_form(wl_amg *a, int level, void *x, void *r, int nrhs, int sweeps, int prec, int form,
+                                 int param) {
+  if (form < 0) {
+    wl_set_error("amg_kaczmarz_form: form must be 0, 1 or 2");
+    return WL_EINVAL;
+  }
+  return kaczmarz_entry(a, level, x, r, nrhs, sweeps, prec, form, param, "amg_kaczmarz_form");
 }
 
 extern "C" int amg_restrict(wl_amg *a, int level, const void *r, void *fc, int nrhs, int prec) {

@@ -84,6 +84,7 @@ def lib():
             "amg_fgmres": (i, [P, P, P, i, d, C.POINTER(wl_info)]),
             "amg_rho": (i, [P, P, P, i, d, i, P, P, P]),
             "amg_sweep_form": (i, [P, i, i, i, P, P, P]),
+            "amg_kaczmarz_form": (i, [P, i, P, P, i, i, i, i, i]),
             "wl_last_error": (C.c_char_p, []),
             "wl_time_kernel": (i, [P, i, i, i, i, i, C.POINTER(d)]),
             "wl_dhat_apply_noalloc": (i, [P, P, P, i]),
@@ -291,7 +292,7 @@ def amg_rho(amg, x0, x, nrhs, tol=1e-8, maxit=100, hist=False):
 
 def amg_sweep_form(amg, level, nrhs, prec):
     """(form, param, us) of the Kaczmarz sweep on `level`: form 0 per-colour
-    launches, 1 cooperative (param blocks), 2 tile kernel (param RHS chunk);
+    launches, 1 cooperative (param blocks), 2 tile kernel (param = RHS chunk | RHS per thread << 8);
     us = measured time of one sweep (0 if not measured)."""
     f, p, u = C.c_int(), C.c_int(), C.c_float()
     _chk(lib().amg_sweep_form(amg.handle, level, nrhs, prec, C.byref(f), C.byref(p), C.byref(u)),
@@ -307,6 +308,11 @@ def amg_level_apply(amg, level, x, y, nrhs, prec=WL_FP64):
 def amg_kaczmarz(amg, level, x, r, nrhs, sweeps=1, prec=WL_FP64):
     return _chk(lib().amg_kaczmarz(amg.handle, level, _ptr(x), _ptr(r), nrhs, sweeps, prec),
                 "amg_kaczmarz")
+
+
+def amg_kaczmarz_form(amg, level, x, r, nrhs, sweeps, prec, form, param):
+    return _chk(lib().amg_kaczmarz_form(amg.handle, level, _ptr(x), _ptr(r), nrhs, sweeps, prec, form, param),
+                "amg_kaczmarz_form")
 
 
 def amg_restrict(amg, level, r, fc, nrhs, prec=WL_FP64):

@@ -1,0 +1,50 @@
+"""Full-size parity on the benchmark workload: C4 (512x512, beta = 10, four
+grids with 4x4, 4x4, 2x2 cells, k = 12), 64 right-hand sides in one call, in
+the launch configuration bench.py times (FP32 V(4,4) tile-coloured cycle,
+FGMRES(20) with one Gram-Schmidt pass, FP32 Arnoldi matvec, FP64 restarts).
+The hierarchy is the oracle's (shared file), so the solve phase is compared
+on the same operators.  Checked: every right-hand side's full-system residual
+|b - D psi| / |b|, recomputed with the oracle's FP64 D, stays at the
+tolerance's level (a property that holds at any size); two sampled
+right-hand sides match the oracle's own FP64 solve to 1e-8 relative error
+(condition number times tolerance)."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover - collected only on GPU machines
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_1308_5992_gb300 import wilson_amg as W  # noqa: E402
+from wl_inputs import workload, rhs_batch  # noqa: E402
+
+DEV = torch.device("cuda:0")
+
+
+def test_c4_full_size_batch(O, tmp_path):
+    from oracle.hierfile import write_hierarchy
+    w = workload("C4")
+    N, U, m = w["N"], w["U"], w["m"]
+    h = O.Hierarchy.setup(N, U, m, O.setup_params(w["blocks"], k_r=w["k"], k_e=w["k"], seed=w["seed"]))
+    path = str(tmp_path / "c4.wlh")
+    write_hierarchy(path, h)
+    op = W.wilson_create(torch.from_numpy(U).to(DEV), N, m)
+    p = W.amg_params_default(zero_guess=1, precision=W.WL_FP32, nu_pre=w["nu"], nu_post=w["nu"],
+                             fgmres_m=w["fgmres_m"], gs_passes=w["gs_passes"], kacz_order=w["kacz_order"],
+                             arnoldi_matvec=w["arnoldi_matvec"])
+    amg = W.amg_import(op, path, p)
+    nrhs = 64
+    b = rhs_batch(N, nrhs, 100)
+    psi = torch.zeros((nrhs, N, N, 2), dtype=torch.complex128, device=DEV)
+    rc, info = W.amg_solve(amg, torch.from_numpy(b).to(DEV), psi, nrhs, 1e-10)
+    assert rc == W.WL_OK
+    x = psi.cpu().numpy()
+    for r in range(nrhs):
+        assert info[r]["true_relres"] <= 1e-10
+        res = b[r].reshape(-1) - O.wilson_apply(N, U, m, x[r].reshape(-1))
+        assert np.linalg.norm(res) / np.linalg.norm(b[r]) <= 1e-9, r
+    for r in (0, nrhs - 1):
+        ref, _ = h.solve(b[r], tol=1e-13)
+        assert np.linalg.norm(x[r] - ref) / np.linalg.norm(ref) <= 1e-8, r

@@ -188,6 +188,36 @@ def test_sweep_forms_agree_and_autotuner(O, shared, order):
             assert np.array_equal(xa, xb) and np.array_equal(ra, rb), (sk, l)
 
 
+@pytest.mark.parametrize("order,nrhs", [(0, 5), (1, 5), (1, 40)])
+def test_every_launch_form_agrees_bitwise(shared, order, nrhs):
+    """Each launch form of the sweep (per-colour, cooperative with several
+    block counts; tile kernel with right-hand-side chunks 8 / 16 / 32 and one
+    or two right-hand sides per thread) gives bit-identical x and r."""
+    w, op, h, _, path = shared("C2")
+    prec = W.WL_FP32
+    amg = W.amg_import(op, path, W.amg_params_default(zero_guess=1, kacz_order=order, precision=prec))
+    if order == 0:
+        forms = [(0, 0), (1, 1), (1, 7), (1, 64)]
+    else:
+        forms = [(2, 8), (2, 16), (2, 16 | 2 << 8), (2, 32), (2, 32 | 2 << 8)]
+    for l in range(h.L - 1):
+        if order == 1 and h.Nl[l] < 64:
+            continue
+        n = h.n(l)
+        x0 = 0.1 * np.stack([cgauss(210 + l, r, n) for r in range(nrhs)])
+        r0 = np.stack([cgauss(220 + l, r, n) for r in range(nrhs)])
+        outs = []
+        for form, param in forms:
+            xg, rg = T(x0), T(r0)
+            W.amg_kaczmarz_form(amg, l, xg, rg, nrhs, 2, prec, form, param)
+            outs.append((H(xg), H(rg)))
+        for f, (xa, ra) in zip(forms[1:], outs[1:]):
+            assert np.array_equal(xa, outs[0][0]) and np.array_equal(ra, outs[0][1]), (l, f)
+    z = np.zeros((nrhs, h.n(0)))
+    with pytest.raises(W.WilsonAMGError):  # a form of the other ordering
+        W.amg_kaczmarz_form(amg, 0, T(z), T(z), nrhs, 1, prec, 2 if order == 0 else 0, 8)
+
+
 def test_tile_ordered_solve(O, shared):
     w, op, h, _, path = shared("C2")
     amg = W.amg_import(op, path, W.amg_params_default(zero_guess=1, kacz_order=1))
