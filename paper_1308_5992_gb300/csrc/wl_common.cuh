@@ -123,6 +123,8 @@ __device__ __forceinline__ cx<T> ld(const zb *p) {
 // site h <-> (x, y): y = h / (N/2), x = 2 (h mod N/2) + (y mod 2).
 // Rotated coordinates a = (x+y)/2, b = (x-y)/2; stencil offset
 // d = 3 (da+1) + (db+1), (dx, dy) = (da+db, da-db).
+#define WL_MAX_DEVICES 64
+
 struct Geo {
   int N, lg;  // N = 1 << lg
   __host__ __device__ __forceinline__ int half() const { return N >> 1; }

@@ -10,6 +10,8 @@
 
 #include <algorithm>
 
+#include <atomic>
+
 #include "wl_common.cuh"
 
 namespace cg = cooperative_groups;
@@ -677,18 +679,32 @@ int kaczmarz_colour(wl_amg *a, int l, int prec, void *x, void *r, int nrhs, int 
 // kernel instance)
 template <typename T, typename S>
 static int coop_blocks() {
-  static int cached = -1;
-  if (cached < 0) {
-    int dev = 0, sms = 0, per = 0;
-    cudaGetDevice(&dev);
+  static std::atomic<int> cached[WL_MAX_DEVICES];  // per device, 0 = not yet known
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= WL_MAX_DEVICES) return 0;
+  int v = cached[dev].load(std::memory_order_relaxed);
+  if (v <= 0) {
+    int sms = 0, p0 = 0, p1 = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int p0 = 0, p1 = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p0, k_kacz_coop<T, S, 0>, 128, 0);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p1, k_kacz_coop<T, S, 1>, 128, 0);
-    per = std::min(p0, p1);
-    cached = sms * per;
+    v = sms * std::min(p0, p1);
+    cached[dev].store(v, std::memory_order_relaxed);
   }
-  return cached;
+  return v;
+}
+
+// raise a kernel's dynamic shared-memory limit once per device
+static int set_smem_limit(const void *fn, size_t bytes, std::atomic<unsigned long long> &done) {
+  int dev = 0;
+  WL_CUDA(cudaGetDevice(&dev));
+  unsigned long long bit = 1ull << (dev & 63);
+  if (!(done.load(std::memory_order_acquire) & bit)) {
+    WL_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    done.fetch_or(bit, std::memory_order_acq_rel);
+  }
+  return WL_OK;
 }
 
 template <typename T, typename S>
@@ -737,10 +753,8 @@ template <typename T, typename S, int R, int RPT>
 static int launch_tile_r(const Level &L, const LevelOps &o, int tc, void *x, void *r, int nrhs, double omega,
                          cudaStream_t s) {
   size_t smem = tile_smem<T, S>(R);
-  // set once per instantiation (thread-safe static initialisation)
-  static const cudaError_t attr = cudaFuncSetAttribute((const void *)k_kacz_tile<T, S, R, RPT>,
-                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  WL_CUDA(attr);
+  static std::atomic<unsigned long long> limit_set{0};  // devices whose limit is raised
+  WL_TRY(set_smem_limit((const void *)k_kacz_tile<T, S, R, RPT>, smem, limit_set));
   int vec = ((uintptr_t)r % 16 == 0) && (sizeof(T) == 8 || nrhs % 2 == 0);
   dim3 grid((L.N / (2 * KT)) * (L.N / (4 * KT)), (nrhs + R - 1) / R);
   k_kacz_tile<T, S, R, RPT><<<grid, 4 * R / RPT, smem, s>>>(L.geo, tc, o.A.as<S>(), o.den.as<T>(), (cx<T> *)x,

@@ -440,3 +440,36 @@ def test_hierarchy_roundtrip_and_errors(shared, ops, tmp_path):
     with pytest.raises(W.WilsonAMGError) as e:
         W.amg_kaczmarz(amg, len(h.Nl) - 1, T(np.zeros(1)), T(np.zeros(1)), 1)
     assert e.value.code == W.WL_EINVAL
+
+
+def test_degenerate_inputs(O, shared, ops):
+    """Degenerate cases: a zero right-hand side in a batch converges at once
+    to x = 0 without disturbing its batch mates; an initial guess that is
+    already the solution stops with no iteration; empty or oversized
+    batches and a vanishing diagonal c = m + 2 are rejected."""
+    w, op, h, amg, path = shared("T64")
+    N = w["N"]
+    b = rhs_batch(N, 3, 31)
+    b[1] = 0
+    psi = torch.zeros_like(T(b))
+    rc, info = W.amg_solve(amg, T(b), psi, 3, 1e-12)
+    assert rc == W.WL_OK
+    assert np.all(H(psi[1]) == 0) and info[1]["iters"] == 0 and info[1]["true_relres"] == 0
+    for q in (0, 2):
+        ref, _ = h.solve(b[q], tol=1e-13)
+        assert np.linalg.norm(H(psi[q]) - ref) / np.linalg.norm(ref) <= 1e-10
+    # the solution as initial guess: no iteration
+    amg_g = W.amg_import(op, path, W.amg_params_default(zero_guess=0))
+    ref, _ = h.solve(b[0], tol=1e-14)
+    x0 = T(ref[None])
+    rc, info = W.amg_solve(amg_g, T(b[:1]), x0, 1, 1e-10)
+    assert rc == W.WL_OK and info[0]["iters"] == 0
+    with pytest.raises(W.WilsonAMGError) as e:
+        W.amg_solve(amg, T(b[:1]), psi[:1], 0, 1e-10)
+    assert e.value.code == W.WL_EINVAL
+    with pytest.raises(W.WilsonAMGError) as e:
+        W.amg_rho(amg, T(np.zeros((1, h.n(0)))), T(np.zeros((1, h.n(0)))), 257, 1e-8, 10)
+    assert e.value.code == W.WL_EINVAL
+    with pytest.raises(W.WilsonAMGError) as e:
+        W.wilson_create(T(w["U"]), N, -2.0)
+    assert e.value.code == W.WL_EINVAL
