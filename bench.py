@@ -33,7 +33,7 @@ METRIC = "Wilson-AMG solves/s at 1e-10 rel err (mixed+batched vs plain FP64); p9
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the kernels the
 # roofline reports, from ncu captures of the C4 workload at 64 right-hand sides
 # (profiles/traffic_c4_512x512_64rhs.md); None until captured for the current kernel
-TRAFFIC = {"k_mdot": 3228150000, "k_kacz_tile": 126950000}
+TRAFFIC = {"k_mdot": 3228150000, "k_kacz_tile": 127790000}
 TOL = 1e-10
 
 
@@ -303,10 +303,10 @@ def run_gb300(args, rank, world, local_rank):
         torch.cuda.synchronize()
         p64.append(e0.elapsed_time(e1))
 
-    # Roofline.  The launch list of this workload (profiles/launches_c4_512x512_64rhs.md) ranks
-    # the tile-coloured Kaczmarz kernel first (38% of kernel time), then the FP64 Gram-Schmidt
-    # update k_maxpy and the multi-dots k_mdot; with the 16-colour ordering k_mdot and the
-    # colour passes lead.
+    # Roofline.  The launch list of this workload (profiles/launches_c4_512x512_64rhs.md)
+    # ranks the tile-coloured Kaczmarz kernel first (44% of kernel time over levels 0 and
+    # 1), then the FP64 Gram-Schmidt update k_maxpy and the multi-dots k_mdot; with the
+    # 16-colour ordering k_mdot and the colour passes lead.
     n0 = N * N // 2
     E = 2 * n0 * nrhs
     hbm, src = peaks()
@@ -341,10 +341,20 @@ def run_gb300(args, rank, world, local_rank):
                  "achieved": round(achieved, 1), "peak": hbm, "peak_source": src, "unit": "GB/s",
                  "frac": round(achieved / hbm, 4), "traffic": TRAFFIC.get("k_kacz_tile"),
                  "avg_launch_ms": round(tile_ms, 5), "algorithmic_bytes": int(tile_bytes)}
+    # k_stencil on level 0 (residual f - A x with the 9-point Dhat stencil; the same gather
+    # computes the FP32 Arnoldi matvec): x read once (its 9 neighbours come from cache), f
+    # read, y written, the stencil row (36 complex) read once per site
+    st_ms = W.wl_time_kernel(amg, W.WL_K_STENCIL, 0, nrhs, prec, 40)
+    st_bytes = n0 * (nrhs * 2 * 3 * eb + 36 * sb)
+    achieved = st_bytes / (st_ms * 1e-3) / 1e9
+    roof_st = {"kernel": "k_stencil (fine level, residual f - Dhat x)", "bound": "hbm",
+               "achieved": round(achieved, 1), "peak": hbm, "peak_source": src, "unit": "GB/s",
+               "frac": round(achieved / hbm, 4), "traffic": None, "avg_launch_ms": round(st_ms, 5),
+               "algorithmic_bytes": int(st_bytes)}
     if w["kacz_order"] == 1:
-        roof, roof_more = roof_tile, [roof_dot, roof_kacz]
+        roof, roof_more = roof_tile, [roof_dot, roof_kacz, roof_st]
     else:
-        roof, roof_more = roof_dot, [roof_kacz, roof_tile]
+        roof, roof_more = roof_dot, [roof_kacz, roof_tile, roof_st]
 
     out = {
         "metric": METRIC, "value": round(value, 3), "unit": "solves/s", "n_gpus": world,

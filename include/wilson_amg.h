@@ -90,9 +90,10 @@ typedef struct {
                              N >= 64; smaller grids keep order 0).  Both are forward
                              sweeps over a permutation of the variables (Sec. 3.1). */
   int arnoldi_matvec;     /* precision of the Arnoldi matvec w = Dhat z_j inside a
-                             restart cycle: 0 = FP64, 1 = the cycle precision when it is
-                             FP32 or BF16 (FP32 arithmetic, result widened to FP64 for
-                             the Gram-Schmidt).  The true residual at every restart
+                             restart cycle: 0 = FP64 (matrix-free from the links), 1 =
+                             FP32 when the cycle is FP32 or BF16 (the FP32 copy of the
+                             9-point Dhat stencil, result widened to FP64 for the
+                             Gram-Schmidt).  The true residual at every restart
                              stays FP64, so the accuracy is unchanged; a cycle whose
                              Arnoldi relation holds to FP32 rounding may need one more
                              restart. */
@@ -275,7 +276,8 @@ int wl_time_kernel(wl_amg *amg, int kind, int level, int nrhs, int prec, int rep
  * right-hand sides in precision `prec`: form 0 = one launch per colour,
  * 1 = cooperative launch with *param blocks, 2 = tile-coloured kernel with
  * right-hand-side chunk (*param & 255) and right-hand sides per thread
- * (*param >> 8); *us = the autotuner's measured time of one
+ * (*param >> 8), 3 = one launch for all colours with a block per *param
+ * right-hand sides (small levels, x and r in shared memory); *us = the autotuner's measured time of one
  * sweep in microseconds, 0 when the form was not measured (explicit
  * sweep_kernel, or no cycle of that width yet).  Errors: WL_EINVAL. */
 int amg_sweep_form(wl_amg *amg, int level, int nrhs, int prec, int *form, int *param, float *us);

@@ -212,7 +212,8 @@ struct LevelOps {
 // launch form of a Kaczmarz sweep on one level, chosen by the autotuner
 // (measured) or by the heuristic: form 0 = one launch per colour, 1 = one
 // cooperative launch for all colours (param = blocks), 2 = tile-coloured
-// kernel (param = right-hand-side chunk R | right-hand sides per thread << 8)
+// kernel (param = right-hand-side chunk R | right-hand sides per thread << 8),
+// 3 = block-resident sweeps of a small level (param = right-hand sides per block)
 struct KTune {
   int nrhs, prec, form, param;
   float us;  // measured time of one sweep (0 if not measured)
@@ -271,7 +272,7 @@ int cycle_run(wl_amg *a, int nrhs, int prec, cudaStream_t s);  // lev[0].f -> le
 int cycle_prepare(wl_amg *a, int nrhs, int prec, cudaStream_t s, const wl_amg::G **out);  // capture only
 int cycle_direct(wl_amg *a, int nrhs, int prec, cudaStream_t s);
 int dhat_apply_dev(wl_op *op, const void *x, int x_is_f32, zd *y, int nrhs, cudaStream_t s);
-int dhat_apply_dev32(wl_op *op, const zf *x, zd *y, int nrhs, cudaStream_t s);
+int stencil_apply32_to64(wl_amg *a, const void *x, zd *y, int nrhs, cudaStream_t s);
 int stencil_apply(wl_amg *a, int l, int prec, const void *x, void *y, const void *f, int nrhs,
                   cudaStream_t s);
 int kaczmarz_sweeps(wl_amg *a, int l, int prec, void *x, void *r, int nrhs, int sweeps,

@@ -439,7 +439,7 @@ int fg_cycle(wl_amg *a, const zd *bnorm_h, zd *xh, int nrhs, double tol, const i
     WL_TRY(cycle_run(a, nrhs, prec, s));
     WL_CUDA(cudaMemcpyAsync(zj, a->lev[0].x.p, zb_ * E, cudaMemcpyDeviceToDevice, s));
     // w = Dhat z_j (FP64)
-    if (prec != WL_FP64 && a->prm.arnoldi_matvec == 1) WL_TRY(dhat_apply_dev32(op, (const zf *)zj, w, nrhs, s));
+    if (prec != WL_FP64 && a->prm.arnoldi_matvec == 1) WL_TRY(stencil_apply32_to64(a, zj, w, nrhs, s));
     else WL_TRY(dhat_apply_dev(op, zj, prec != WL_FP64, w, nrhs, s));
     // Gram-Schmidt against v_0 .. v_j
     k_zero_hcol<<<WL_GRID(nrhs, 128), 128, 0, s>>>(k);

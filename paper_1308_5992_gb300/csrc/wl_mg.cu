@@ -18,10 +18,11 @@ namespace cg = cooperative_groups;
 
 
 // ------------------------------------------------------------ stencil apply
-// y = A x, or y = f - A x when f != nullptr (y may alias f).
-template <typename T, typename S>
+// y = A x, or y = f - A x when f != nullptr (y may alias f); arithmetic in T,
+// y stored as To (the Arnoldi matvec widens an FP32 result to FP64).
+template <typename T, typename S, typename To = T>
 __global__ void __launch_bounds__(256) k_stencil(Geo g, const S *__restrict__ A, const cx<T> *__restrict__ x,
-                                                 const cx<T> *f, cx<T> *y, int nrhs) {
+                                                 const cx<To> *f, cx<To> *y, int nrhs) {
   long tid = (long)blockIdx.x * blockDim.x + threadIdx.x;
   int n = g.nsites();
   if (tid >= (long)n * nrhs) return;
@@ -40,12 +41,13 @@ __global__ void __launch_bounds__(256) k_stencil(Geo g, const S *__restrict__ A,
     cfma(y1, ld<T>(Ah + d * 4 + 3), x1);
   }
   long o = (long)h * 2 * nrhs + r;
+  cx<To> z0 = widen<To>(y0), z1 = widen<To>(y1);
   if (f) {
-    y0 = f[o] - y0;
-    y1 = f[o + nrhs] - y1;
+    z0 = f[o] - z0;
+    z1 = f[o + nrhs] - z1;
   }
-  y[o] = y0;
-  y[o + nrhs] = y1;
+  y[o] = z0;
+  y[o + nrhs] = z1;
 }
 
 // ---------------------------------------------------------------- Kaczmarz
@@ -183,6 +185,46 @@ __global__ void __launch_bounds__(128) k_kacz_warp(Geo g, int colour, const S *_
   kacz_site_warp<T, S>(g, colour, q, threadIdx.x & 31, A, den, x, r, omega);
 }
 
+// Small levels: all colours of `sweeps` sweeps in one launch, a block per
+// chunk of RC right-hand sides.  Right-hand sides do not interact, so a block
+// owning whole right-hand sides needs only block barriers between colours;
+// x and r of its chunk live in shared memory ([n][2][RC] each), the stencil
+// rows come through the cache.  The per-item arithmetic is kacz_item's, so
+// the result equals the other launch forms bit for bit.
+template <typename T, typename S>
+__global__ void __launch_bounds__(256) k_kacz_block(Geo g, int sweeps, int RC, const S *__restrict__ A,
+                                                    const T *__restrict__ den, cx<T> *__restrict__ x,
+                                                    cx<T> *__restrict__ r, int nrhs, T omega) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  int n = g.nsites();
+  cx<T> *xs = (cx<T> *)sm_raw, *rs = xs + (long)n * 2 * RC;
+  int r0 = blockIdx.x * RC, rc = min(RC, nrhs - r0);
+  int tid = threadIdx.x, nt = blockDim.x;
+  for (int e = tid; e < n * 2 * RC; e += nt) {
+    int j = e % RC, row = e / RC;
+    bool in = j < rc;
+    xs[e] = in ? x[(long)row * nrhs + r0 + j] : mk<T>(0, 0);
+    rs[e] = in ? r[(long)row * nrhs + r0 + j] : mk<T>(0, 0);
+  }
+  __syncthreads();
+  int n16 = n >> 4;
+  for (int sw = 0; sw < sweeps; ++sw)
+    for (int c = 0; c < 16; ++c) {
+      for (int it = tid; it < n16 * RC; it += nt) {
+        int q = it / RC, j = it - q * RC;
+        if (j < rc) kacz_item<T, S>(g, c, q, j, A, den, xs, rs, RC, omega);
+      }
+      __syncthreads();
+    }
+  for (int e = tid; e < n * 2 * RC; e += nt) {
+    int j = e % RC, row = e / RC;
+    if (j < rc) {
+      x[(long)row * nrhs + r0 + j] = xs[e];
+      r[(long)row * nrhs + r0 + j] = rs[e];
+    }
+  }
+}
+
 // All colours of `sweeps` sweeps in one cooperative launch; a grid-wide
 // barrier separates the colours.  wpi = 1: one warp per site (nrhs = 1).
 template <typename T, typename S, int WPI>
@@ -281,9 +323,10 @@ __device__ __forceinline__ void tile_stage_rows(const Geo &g, int A0, int B0, co
 // Several right-hand sides: a block of 4 R / RPT threads, thread (k, q) owns
 // site k of the current colour step and right-hand sides r0 + q + j R / RPT
 // (j < RPT), which share the stencil coefficients and the index arithmetic.
-// Shared memory: r of tile + halo [100][2][R], omega / den [64][2], and a
-// ring of three colour steps' stencil rows [3][4][36] filled by cp.async two
-// steps ahead (about 55 KB at R = 32, so four blocks fit an SM).  vec: r rows
+// Shared memory: r of tile + halo [100][2][R], omega / den [64][2], a ring
+// of three colour steps' stencil rows [3][4][36] filled by cp.async two
+// steps ahead, and the site indices of tile + halo [100] (about 55 KB at
+// R = 32, so four blocks fit an SM).  vec: r rows
 // start on 16-byte boundaries (16-byte copies), else one complex per copy.
 // Every right-hand side sees the same operations in the same order for any
 // RPT, so the variants agree bit for bit.
@@ -295,6 +338,7 @@ __global__ void __launch_bounds__(4 * R / RPT) k_kacz_tile(Geo g, int tc, const 
   cx<T> *rs = (cx<T> *)sm_raw;
   T *ds = (T *)(rs + KTH * KTH * 2 * R);
   S *Ar = (S *)(ds + KT * KT * 2);
+  int *hs = (int *)(Ar + 3 * 4 * 36);  // site index of tile + halo site ls = KTH (i + 1) + (j + 1)
   constexpr int NT = 4 * R / RPT;
   constexpr int RQ = R / RPT;                  // threads per site
   constexpr int E = 16 / (int)sizeof(cx<T>);  // complex numbers per 16-byte copy
@@ -305,28 +349,30 @@ __global__ void __launch_bounds__(4 * R / RPT) k_kacz_tile(Geo g, int tc, const 
   int r0 = blockIdx.y * R;
   int Rc = min(R, nrhs - r0);
   int tid = threadIdx.x;
+  for (int ls = tid; ls < KTH * KTH; ls += NT) {
+    int a = A0 + ls / KTH - 1, b = B0 + ls % KTH - 1;
+    hs[ls] = g.idx(a + b, a - b);
+  }
+  __syncthreads();
   // group 0: r of tile + halo
   if (vec) {
     for (int e = tid; e < KTH * KTH * 2 * CPR; e += NT) {
-      int c = e % CPR, row = e / CPR, ls = row >> 1;
+      int c = e % CPR, row = e / CPR;
       if (c * E >= Rc) continue;
-      int a = A0 + ls / KTH - 1, b = B0 + ls % KTH - 1;
-      long h = g.idx(a + b, a - b);
+      long h = hs[row >> 1];
       cp_async(rs + row * R + c * E, r + (h * 2 + (row & 1)) * nrhs + r0 + c * E, 16);
     }
   } else {
     for (int e = tid; e < KTH * KTH * 2 * R; e += NT) {
-      int q = e % R, row = e / R, ls = row >> 1;
+      int q = e % R, row = e / R;
       if (q >= Rc) continue;
-      int a = A0 + ls / KTH - 1, b = B0 + ls % KTH - 1;
-      long h = g.idx(a + b, a - b);
+      long h = hs[row >> 1];
       cp_async(rs + e, r + (h * 2 + (row & 1)) * nrhs + r0 + q, (int)sizeof(cx<T>));
     }
   }
   for (int e = tid; e < KT * KT * 2; e += NT) {
     int ks = e >> 1;
-    int a = A0 + ks / KT, b = B0 + ks % KT;
-    long h = g.idx(a + b, a - b);
+    long h = hs[(ks / KT + 1) * KTH + ks % KT + 1];
     ds[e] = omega / den[2 * h + (e & 1)];  // the step scale, once per site and spin
   }
   cp_async_commit();
@@ -336,7 +382,7 @@ __global__ void __launch_bounds__(4 * R / RPT) k_kacz_tile(Geo g, int tc, const 
     for (int e = tid; e < 4 * ROWC; e += NT) {
       int kk = e / ROWC, c16 = e - kk * ROWC;
       int i = (c >> 2) + 4 * (kk >> 1), j = (c & 3) + 4 * (kk & 1);
-      long h = g.idx(A0 + i + B0 + j, A0 + i - B0 - j);
+      long h = hs[(i + 1) * KTH + j + 1];
       cp_async((char *)(dst + kk * 36) + 16 * c16, (const char *)(A + h * 36) + 16 * c16, 16);
     }
   };
@@ -353,7 +399,7 @@ __global__ void __launch_bounds__(4 * R / RPT) k_kacz_tile(Geo g, int tc, const 
   // (a ring of four), so the HBM latency of x is off the step's critical path
   auto x_at = [&](int c) -> long {
     int i = (c >> 2) + 4 * (k >> 1), j = (c & 3) + 4 * (k & 1);
-    return (long)g.idx(A0 + i + B0 + j, A0 + i - B0 - j) * 2 * nrhs + r0 + q0;
+    return (long)hs[(i + 1) * KTH + j + 1] * 2 * nrhs + r0 + q0;
   };
   cx<T> xp[4][RPT][2];
 #pragma unroll
@@ -441,18 +487,16 @@ __global__ void __launch_bounds__(4 * R / RPT) k_kacz_tile(Geo g, int tc, const 
   // write r back (tile and halo)
   if (vec) {
     for (int e = tid; e < KTH * KTH * 2 * CPR; e += NT) {
-      int c = e % CPR, row = e / CPR, ls = row >> 1;
+      int c = e % CPR, row = e / CPR;
       if (c * E >= Rc) continue;
-      int a = A0 + ls / KTH - 1, b = B0 + ls % KTH - 1;
-      long h = g.idx(a + b, a - b);
+      long h = hs[row >> 1];
       *(int4 *)(r + (h * 2 + (row & 1)) * nrhs + r0 + c * E) = *(const int4 *)(rs + row * R + c * E);
     }
   } else {
     for (int e = tid; e < KTH * KTH * 2 * R; e += NT) {
-      int q2 = e % R, row = e / R, ls = row >> 1;
+      int q2 = e % R, row = e / R;
       if (q2 >= Rc) continue;
-      int a = A0 + ls / KTH - 1, b = B0 + ls % KTH - 1;
-      long h = g.idx(a + b, a - b);
+      long h = hs[row >> 1];
       r[(h * 2 + (row & 1)) * nrhs + r0 + q2] = rs[e];
     }
   }
@@ -633,23 +677,6 @@ static const LevelOps &ops_of(const Level &L, int prec) {
   return prec == WL_FP64 ? L.op64 : prec == WL_FP32 ? L.op32 : L.opbf;
 }
 
-int stencil_apply(wl_amg *a, int l, int prec, const void *x, void *y, const void *f, int nrhs,
-                  cudaStream_t s) {
-  const Level &L = a->lev[l];
-  const LevelOps &o = ops_of(L, prec);
-  long tot = (long)L.n * nrhs;
-  unsigned grid = WL_GRID(tot, 256);
-  wl_count_launches(1);
-  if (prec == WL_FP64)
-    k_stencil<double, zd><<<grid, 256, 0, s>>>(L.geo, o.A.as<zd>(), (const zd *)x, (const zd *)f, (zd *)y, nrhs);
-  else if (prec == WL_FP32)
-    k_stencil<float, zf><<<grid, 256, 0, s>>>(L.geo, o.A.as<zf>(), (const zf *)x, (const zf *)f, (zf *)y, nrhs);
-  else
-    k_stencil<float, zb><<<grid, 256, 0, s>>>(L.geo, o.A.as<zb>(), (const zf *)x, (const zf *)f, (zf *)y, nrhs);
-  WL_CUDA(cudaGetLastError());
-  return WL_OK;
-}
-
 int kaczmarz_colour(wl_amg *a, int l, int prec, void *x, void *r, int nrhs, int c, cudaStream_t s) {
   const Level &L = a->lev[l];
   const LevelOps &o = ops_of(L, prec);
@@ -737,6 +764,182 @@ static int launch_coop(const Level &L, const LevelOps &o, int sweeps, void *x, v
   return WL_OK;
 }
 
+// Fine-grid stencil apply with shared-memory tiles: a block owns an 8 x 8
+// tile in (a, b) and a chunk of R right-hand sides; x of tile + halo and the
+// tile's stencil rows are staged once (cp.async), so each x value crosses
+// L2 once per tile instead of once per neighbour.  Same arithmetic, in the
+// same order, as k_stencil.  x must not alias y.
+template <typename T, typename S, typename To, int R, int WF>
+__global__ void __launch_bounds__(256) k_stencil_tile(Geo g, const S *__restrict__ A, const cx<T> *__restrict__ x,
+                                                      const cx<To> *f, cx<To> *y, int nrhs, int vec) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  cx<T> *xs = (cx<T> *)sm_raw;                  // [100][2][R]
+  S *As = (S *)(xs + KTH * KTH * 2 * R);        // [64][36]
+  int *hs = (int *)(As + KT * KT * 36);         // [100] site indices of tile + halo
+  constexpr int NT = 256;
+  constexpr int E = 16 / (int)sizeof(cx<T>);
+  constexpr int CPR = R / E;
+  constexpr int ROWC = 36 * (int)sizeof(S) / 16;
+  int nbt = g.N / (2 * KT);  // tiles along b
+  int A0 = (blockIdx.x / nbt) * KT, B0 = (blockIdx.x % nbt) * KT;
+  int r0 = blockIdx.y * R, Rc = min(R, nrhs - r0);
+  int tid = threadIdx.x;
+  for (int ls = tid; ls < KTH * KTH; ls += NT) {
+    int a = A0 + ls / KTH - 1, b = B0 + ls % KTH - 1;
+    hs[ls] = g.idx(a + b, a - b);
+  }
+  __syncthreads();
+  if (vec) {
+    for (int e = tid; e < KTH * KTH * 2 * CPR; e += NT) {
+      int c = e % CPR, row = e / CPR;
+      if (c * E >= Rc) continue;
+      long h = hs[row >> 1];
+      cp_async(xs + row * R + c * E, x + (h * 2 + (row & 1)) * nrhs + r0 + c * E, 16);
+    }
+  } else {
+    for (int e = tid; e < KTH * KTH * 2 * R; e += NT) {
+      int q = e % R, row = e / R;
+      if (q >= Rc) continue;
+      long h = hs[row >> 1];
+      cp_async(xs + e, x + (h * 2 + (row & 1)) * nrhs + r0 + q, (int)sizeof(cx<T>));
+    }
+  }
+  for (int e = tid; e < KT * KT * ROWC; e += NT) {
+    int ks = e / ROWC, c16 = e - ks * ROWC;
+    long h = hs[(ks / KT + 1) * KTH + ks % KT + 1];
+    cp_async((char *)(As + ks * 36) + 16 * c16, (const char *)(A + h * 36) + 16 * c16, 16);
+  }
+  // f of this thread's outputs is loaded while the staging copies fly
+  constexpr int PER = KT * KT * R / NT;  // outputs per thread
+  cx<To> fv[WF ? PER : 1][2];
+  if (WF) {
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      int it = tid + u * NT, q = it % R, ks = it / R;
+      if (q < Rc) {
+        long o = (long)hs[(ks / KT + 1) * KTH + ks % KT + 1] * 2 * nrhs + r0 + q;
+        fv[u][0] = f[o];
+        fv[u][1] = f[o + nrhs];
+      }
+    }
+  }
+  cp_async_wait_all();
+  __syncthreads();
+#pragma unroll
+  for (int u = 0; u < PER; ++u) {
+    int it = tid + u * NT;
+    int q = it % R, ks = it / R;
+    if (q >= Rc) continue;
+    int i = ks / KT, j = ks % KT;
+    const S *Ah = As + ks * 36;
+    cx<T> y0 = mk<T>(0, 0), y1 = mk<T>(0, 0);
+#pragma unroll
+    for (int d = 0; d < 9; ++d) {
+      int ls = (i + d / 3) * KTH + (j + d % 3);  // (i + da + 1, j + db + 1)
+      cx<T> x0 = xs[(ls * 2) * R + q], x1 = xs[(ls * 2 + 1) * R + q];
+      cfma(y0, ld<T>(Ah + d * 4 + 0), x0);
+      cfma(y0, ld<T>(Ah + d * 4 + 1), x1);
+      cfma(y1, ld<T>(Ah + d * 4 + 2), x0);
+      cfma(y1, ld<T>(Ah + d * 4 + 3), x1);
+    }
+    long o = (long)hs[(i + 1) * KTH + j + 1] * 2 * nrhs + r0 + q;
+    cx<To> z0 = widen<To>(y0), z1 = widen<To>(y1);
+    if (WF) {
+      z0 = fv[WF ? u : 0][0] - z0;
+      z1 = fv[WF ? u : 0][1] - z1;
+    }
+    y[o] = z0;
+    y[o + nrhs] = z1;
+  }
+}
+
+template <typename T, typename S>
+static size_t stencil_tile_smem(int R) {
+  return (size_t)KTH * KTH * 2 * R * sizeof(cx<T>) + (size_t)KT * KT * 36 * sizeof(S) + KTH * KTH * sizeof(int);
+}
+
+template <typename T, typename S, typename To, int R>
+static int launch_stencil_tile_r(const Level &L, const S *A, const void *x, const void *f, void *y, int nrhs,
+                                 cudaStream_t s) {
+  size_t smem = stencil_tile_smem<T, S>(R);
+  static std::atomic<unsigned long long> limit_set[2];
+  int vec = ((uintptr_t)x % 16 == 0) && (sizeof(T) == 8 || nrhs % 2 == 0);
+  dim3 grid((L.N / KT) * (L.N / (2 * KT)), (nrhs + R - 1) / R);
+  if (f) {
+    WL_TRY(set_smem_limit((const void *)k_stencil_tile<T, S, To, R, 1>, smem, limit_set[1]));
+    k_stencil_tile<T, S, To, R, 1><<<grid, 256, smem, s>>>(L.geo, A, (const cx<T> *)x, (const cx<To> *)f,
+                                                            (cx<To> *)y, nrhs, vec);
+  } else {
+    WL_TRY(set_smem_limit((const void *)k_stencil_tile<T, S, To, R, 0>, smem, limit_set[0]));
+    k_stencil_tile<T, S, To, R, 0><<<grid, 256, smem, s>>>(L.geo, A, (const cx<T> *)x, nullptr, (cx<To> *)y, nrhs,
+                                                            vec);
+  }
+  return WL_OK;
+}
+
+// the tiled form for grids the tiling covers and batches of at least 8
+template <typename T, typename S, typename To>
+static bool launch_stencil_tile(const Level &L, const S *A, const void *x, const void *f, void *y, int nrhs,
+                                cudaStream_t s, int *rc) {
+  if (L.N < 64 || L.N % (4 * KT) || nrhs < 8) return false;
+  if constexpr (sizeof(T) == 4) {
+    if (nrhs >= 32) {
+      *rc = launch_stencil_tile_r<T, S, To, 32>(L, A, x, f, y, nrhs, s);
+      return true;
+    }
+  }
+  if (nrhs >= 16) *rc = launch_stencil_tile_r<T, S, To, 16>(L, A, x, f, y, nrhs, s);
+  else *rc = launch_stencil_tile_r<T, S, To, 8>(L, A, x, f, y, nrhs, s);
+  return true;
+}
+
+int stencil_apply(wl_amg *a, int l, int prec, const void *x, void *y, const void *f, int nrhs,
+                  cudaStream_t s) {
+  const Level &L = a->lev[l];
+  const LevelOps &o = ops_of(L, prec);
+  long tot = (long)L.n * nrhs;
+  unsigned grid = WL_GRID(tot, 256);
+  wl_count_launches(1);
+  int rc = WL_OK;
+  if (prec == WL_FP64) {
+    if (!launch_stencil_tile<double, zd, double>(L, o.A.as<zd>(), x, f, y, nrhs, s, &rc))
+      k_stencil<double, zd><<<grid, 256, 0, s>>>(L.geo, o.A.as<zd>(), (const zd *)x, (const zd *)f, (zd *)y, nrhs);
+  } else if (prec == WL_FP32) {
+    if (!launch_stencil_tile<float, zf, float>(L, o.A.as<zf>(), x, f, y, nrhs, s, &rc))
+      k_stencil<float, zf><<<grid, 256, 0, s>>>(L.geo, o.A.as<zf>(), (const zf *)x, (const zf *)f, (zf *)y, nrhs);
+  } else {
+    if (!launch_stencil_tile<float, zb, float>(L, o.A.as<zb>(), x, f, y, nrhs, s, &rc))
+      k_stencil<float, zb><<<grid, 256, 0, s>>>(L.geo, o.A.as<zb>(), (const zf *)x, (const zf *)f, (zf *)y, nrhs);
+  }
+  WL_TRY(rc);
+  WL_CUDA(cudaGetLastError());
+  return WL_OK;
+}
+
+// block-resident sweeps of a small level: RC right-hand sides per block
+#define WL_BLOCK_SMEM_MAX (200 * 1024)
+template <typename T>
+static size_t block_smem(const Level &L, int RC) {
+  return (size_t)L.n * 2 * RC * sizeof(cx<T>) * 2;
+}
+static bool block_fits(const Level &L, int RC, int prec) {
+  size_t b = prec == WL_FP64 ? block_smem<double>(L, RC) : block_smem<float>(L, RC);
+  return RC >= 1 && b <= WL_BLOCK_SMEM_MAX;
+}
+
+template <typename T, typename S>
+static int launch_block(const Level &L, const LevelOps &o, int sweeps, void *x, void *r, int nrhs, double omega,
+                        cudaStream_t s, int RC) {
+  static std::atomic<unsigned long long> limit_set{0};
+  WL_TRY(set_smem_limit((const void *)k_kacz_block<T, S>, WL_BLOCK_SMEM_MAX, limit_set));
+  long items = (long)(L.n >> 4) * RC;
+  int nt = (int)std::min<long>(256, std::max<long>(32, (items + 31) / 32 * 32));
+  k_kacz_block<T, S><<<(nrhs + RC - 1) / RC, nt, block_smem<T>(L, RC), s>>>(L.geo, sweeps, RC, o.A.as<S>(),
+                                                                          o.den.as<T>(), (cx<T> *)x, (cx<T> *)r,
+                                                                          nrhs, (T)omega);
+  return WL_OK;
+}
+
 // tile-coloured launch for tile colour tc (one quarter of a sweep)
 static bool tile_ok(int N) { return N >= 64 && N % (4 * KT) == 0; }
 
@@ -746,7 +949,8 @@ static bool tile_ok(int N) { return N >= 64 && N % (4 * KT) == 0; }
 template <typename T, typename S>
 static size_t tile_smem(int R) {
   size_t rows = R == 1 ? (size_t)KT * KT * 36 * sizeof(S) : (size_t)3 * 4 * 36 * sizeof(S);
-  return rows + (size_t)KT * KT * 2 * sizeof(T) + (size_t)KTH * KTH * 2 * R * sizeof(cx<T>);
+  size_t index = R == 1 ? 0 : (size_t)KTH * KTH * sizeof(int);  // site-index table
+  return rows + index + (size_t)KT * KT * 2 * sizeof(T) + (size_t)KTH * KTH * 2 * R * sizeof(cx<T>);
 }
 
 template <typename T, typename S, int R, int RPT>
@@ -834,6 +1038,15 @@ static int run_sweeps(wl_amg *a, int l, int prec, void *x, void *r, int nrhs, in
     else if (prec == WL_FP32) rc = launch_coop<float, zf>(L, o, sweeps, x, r, nrhs, a->prm.omega, s, t.param);
     else rc = launch_coop<float, zb>(L, o, sweeps, x, r, nrhs, a->prm.omega, s, t.param);
     WL_TRY(rc);
+  } else if (t.form == 3) {
+    if (!block_fits(L, t.param, prec) || nrhs < 2) return WL_EINVAL;
+    const LevelOps &o = ops_of(L, prec);
+    wl_count_launches(1);
+    int rc;
+    if (prec == WL_FP64) rc = launch_block<double, zd>(L, o, sweeps, x, r, nrhs, a->prm.omega, s, t.param);
+    else if (prec == WL_FP32) rc = launch_block<float, zf>(L, o, sweeps, x, r, nrhs, a->prm.omega, s, t.param);
+    else rc = launch_block<float, zb>(L, o, sweeps, x, r, nrhs, a->prm.omega, s, t.param);
+    WL_TRY(rc);
   } else {
     for (int sw = 0; sw < sweeps; ++sw)
       for (int c = 0; c < 16; ++c) WL_TRY(kaczmarz_colour(a, l, prec, x, r, nrhs, c, s));
@@ -905,6 +1118,9 @@ int autotune_sweeps(wl_amg *a, int nrhs, int prec, cudaStream_t s) {
         }
     } else {
       cand.push_back(KTune{nrhs, prec, 0, 0, 0.f});
+      if (nrhs > 1)  // block-resident sweeps (thread per item, as forms 0 and 1 at nrhs > 1)
+        for (int RC : {1, 2, 4, 8})
+          if (RC <= nrhs && block_fits(L, RC, prec)) cand.push_back(KTune{nrhs, prec, 3, RC, 0.f});
       int maxb = coop_max_blocks(prec);
       long need = colour_blocks(L, nrhs);
       if (need <= 4L * maxb)
@@ -941,6 +1157,21 @@ int autotune_sweeps(wl_amg *a, int nrhs, int prec, cudaStream_t s) {
   cudaEventDestroy(e1);
   if (rc == WL_ECUDA) wl_set_error("autotune_sweeps: CUDA error while timing");
   return rc;
+}
+
+// y = A_0 x in FP32 arithmetic from the FP32 copy of the level-0 stencil
+// (Dhat), x float, y widened to double: the Arnoldi matvec of an FP32 cycle
+int stencil_apply32_to64(wl_amg *a, const void *x, zd *y, int nrhs, cudaStream_t s) {
+  const Level &L = a->lev[0];
+  long tot = (long)L.n * nrhs;
+  wl_count_launches(1);
+  int rc = WL_OK;
+  if (!launch_stencil_tile<float, zf, double>(L, L.op32.A.as<zf>(), x, nullptr, y, nrhs, s, &rc))
+    k_stencil<float, zf, double><<<WL_GRID(tot, 256), 256, 0, s>>>(L.geo, L.op32.A.as<zf>(), (const zf *)x, nullptr,
+                                                                   y, nrhs);
+  WL_TRY(rc);
+  WL_CUDA(cudaGetLastError());
+  return WL_OK;
 }
 
 int restrict_op(wl_amg *a, int l, int prec, const void *r, void *fc, int nrhs, cudaStream_t s) {
@@ -1119,7 +1350,8 @@ static int kaczmarz_entry(wl_amg *a, int level, void *x, void *r, int nrhs, int 
     int R = param & 255, rpt = std::max(1, param >> 8);
     bool ok = tile ? (form == 2 && (nrhs == 1 || ((R == 8 && rpt == 1) || ((R == 16 || R == 32) && rpt <= 2))) &&
                       !(prec == WL_FP64 && (R > 16 || rpt > 1)))
-                   : ((form == 0) || (form == 1 && param >= 1));
+                   : ((form == 0) || (form == 1 && param >= 1) ||
+                      (form == 3 && nrhs > 1 && wl::block_fits(L, param, prec)));
     if (!ok) {
       wl_set_error("%s: launch form %d / %d does not exist for this level and ordering", who, form, param);
       return WL_EINVAL;

@@ -402,21 +402,6 @@ int dhat_apply_dev(wl_op *op, const void *x, int x_is_f32, zd *y, int nrhs, cuda
   return WL_OK;
 }
 
-// y = Dhat x in FP32 arithmetic (FP32 links, x float), y widened to double
-int dhat_apply_dev32(wl_op *op, const zf *x, zd *y, int nrhs, cudaStream_t s) {
-  Geo g = op->geo;
-  long n = g.nsites();
-  WL_TRY(op->scratch.alloc(sizeof(zd) * n * 2 * nrhs));
-  zf *t = op->scratch.as<zf>();
-  unsigned grid = WL_GRID(n * nrhs, 256);
-  const zf *V = op->Uf32.as<zf>();
-  wl_count_launches(2);
-  k_hop<float, float, float, float><<<grid, 256, 0, s>>>(g, V, 1, x, nullptr, t, nrhs);
-  k_hop<float, float, float, double><<<grid, 256, 0, s>>>(g, V, 0, t, x, y, nrhs);
-  WL_CUDA(cudaGetLastError());
-  return WL_OK;
-}
-
 int build_dhat_stencil(wl_op *op, zd *A, cudaStream_t s) {
   Geo g = op->geo;
   k_build_dhat<<<WL_GRID(g.nsites(), 128), 128, 0, s>>>(g, op->Uf64.as<zd>(), A);

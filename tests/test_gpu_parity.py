@@ -99,17 +99,26 @@ def test_eo_reduce_reconstruct(O, ops, name, nrhs):
 
 
 # ------------------------------------------------- per-level cycle steps
-@pytest.mark.parametrize("name", ["T64", "C1"])
-def test_level_apply(shared, name):
+@pytest.mark.parametrize("name,nrhs", [("T64", 2), ("C1", 2), ("T64", 16), ("C2", 8), ("C2", 37)])
+def test_level_apply(shared, name, nrhs):
+    """Level operators against the oracle; batches of 8 or more on grids of
+    64 and up take the shared-memory tiled stencil (chunks of 8 / 16 / 32,
+    ragged and odd counts), which must equal the one-site-per-thread kernel
+    bit for bit (checked against single right-hand-side applies)."""
     w, op, h, amg, _ = shared(name)
     for l in range(h.L):
         n = h.n(l)
-        x = np.stack([cgauss(40 + l, r, n) for r in range(2)])
-        ref = np.stack([h.apply(l, x[r]) for r in range(2)])
+        x = np.stack([cgauss(40 + l, r, n) for r in range(nrhs)])
+        ref = np.stack([h.apply(l, x[r]) for r in range(nrhs)])
         for prec, tol in ((W.WL_FP64, 1e-14), (W.WL_FP32, 1e-6)):
             y = torch.zeros_like(T(x))
-            W.amg_level_apply(amg, l, T(x), y, 2, prec)
+            W.amg_level_apply(amg, l, T(x), y, nrhs, prec)
             assert rel(H(y), ref) <= tol, (l, prec, rel(H(y), ref))
+            if nrhs >= 8:
+                for r in (0, nrhs - 1):
+                    y1 = torch.zeros_like(T(x[r:r + 1]))
+                    W.amg_level_apply(amg, l, T(x[r:r + 1]), y1, 1, prec)
+                    assert np.array_equal(H(y1)[0], H(y)[r]), (l, prec, r)
 
 
 @pytest.mark.parametrize("name,nrhs,form", [("T64", 3, 1), ("T64", 3, 2), ("T64", 1, 1), ("T64", 1, 2),
@@ -171,7 +180,7 @@ def test_sweep_forms_agree_and_autotuner(O, shared, order):
             W.amg_cycle(amg, f, torch.zeros_like(f), nrhs, prec)
             for l in range(h.L - 1):
                 form, param, us = W.amg_sweep_form(amg, l, nrhs, prec)
-                assert us > 0 and form in (0, 1, 2), (l, form, param, us)
+                assert us > 0 and form in (0, 1, 2, 3), (l, form, param, us)
                 assert (form == 2) == (order == 1 and h.Nl[l] >= 64)
         res = []
         for l in range(h.L - 1):
@@ -191,19 +200,22 @@ def test_sweep_forms_agree_and_autotuner(O, shared, order):
 @pytest.mark.parametrize("order,nrhs", [(0, 5), (1, 5), (1, 40)])
 def test_every_launch_form_agrees_bitwise(shared, order, nrhs):
     """Each launch form of the sweep (per-colour, cooperative with several
-    block counts; tile kernel with right-hand-side chunks 8 / 16 / 32 and one
-    or two right-hand sides per thread) gives bit-identical x and r."""
+    block counts, block-resident on small levels; tile kernel with
+    right-hand-side chunks 8 / 16 / 32 and one or two right-hand sides per
+    thread) gives bit-identical x and r."""
     w, op, h, _, path = shared("C2")
     prec = W.WL_FP32
     amg = W.amg_import(op, path, W.amg_params_default(zero_guess=1, kacz_order=order, precision=prec))
-    if order == 0:
-        forms = [(0, 0), (1, 1), (1, 7), (1, 64)]
-    else:
-        forms = [(2, 8), (2, 16), (2, 16 | 2 << 8), (2, 32), (2, 32 | 2 << 8)]
     for l in range(h.L - 1):
         if order == 1 and h.Nl[l] < 64:
             continue
         n = h.n(l)
+        if order == 0:
+            forms = [(0, 0), (1, 1), (1, 7), (1, 64)]
+            # block-resident sweeps where x and r of the chunk fit 200 KB of shared memory
+            forms += [(3, rc) for rc in (1, 2, 4) if rc <= nrhs and n * 2 * 8 * rc <= 200 * 1024]
+        else:
+            forms = [(2, 8), (2, 16), (2, 16 | 2 << 8), (2, 32), (2, 32 | 2 << 8)]
         x0 = 0.1 * np.stack([cgauss(210 + l, r, n) for r in range(nrhs)])
         r0 = np.stack([cgauss(220 + l, r, n) for r in range(nrhs)])
         outs = []
