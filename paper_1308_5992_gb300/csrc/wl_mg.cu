@@ -11,6 +11,7 @@
 #include <algorithm>
 
 #include <atomic>
+#include <type_traits>
 
 #include "wl_common.cuh"
 
@@ -502,6 +503,175 @@ __global__ void __launch_bounds__(4 * R / RPT) k_kacz_tile(Geo g, int tc, const 
   }
 }
 
+// FP32, complex-float stencil, two adjacent right-hand sides per thread in
+// packed pairs: every FMA of the RPT = 1 kernel is done for both right-hand
+// sides by one paired FMA (__ffma2_rn, sm_100 and later) in the same order,
+// so the result is bit-identical.  In shared memory each 16-byte piece of a
+// row of r holds (re_q, re_q+1, im_q, im_q+1) instead of the global order
+// (re_q, im_q, re_q+1, im_q+1).  Needs 16-byte aligned rows (vec).
+__device__ __forceinline__ float2 bc2(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float2 neg2(float2 v) { return make_float2(-v.x, -v.y); }
+
+template <int R>
+__global__ void __launch_bounds__(2 * R) k_kacz_tile_pk(Geo g, int tc, const zf *__restrict__ A,
+                                                        const float *__restrict__ den, zf *__restrict__ x,
+                                                        zf *__restrict__ r, int nrhs, float omega) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  float4 *rs4 = (float4 *)sm_raw;                       // [100][2][R / 2] pieces
+  float *ds = (float *)(rs4 + KTH * KTH * 2 * (R / 2));
+  zf *Ar = (zf *)(ds + KT * KT * 2);
+  int *hs = (int *)(Ar + 3 * 4 * 36);
+  constexpr int NT = 2 * R;
+  constexpr int RP = R / 2;                             // right-hand-side pairs (threads per site)
+  constexpr int ROWC = 36 * (int)sizeof(zf) / 16;
+  int A0, B0;
+  tile_origin(g, tc, A0, B0);
+  int r0 = blockIdx.y * R;
+  int Rc = min(R, nrhs - r0);  // even (nrhs even, R even)
+  int tid = threadIdx.x;
+  for (int ls = tid; ls < KTH * KTH; ls += NT) {
+    int a = A0 + ls / KTH - 1, b = B0 + ls % KTH - 1;
+    hs[ls] = g.idx(a + b, a - b);
+  }
+  __syncthreads();
+  for (int e = tid; e < KTH * KTH * 2 * RP; e += NT) {
+    int c = e % RP, row = e / RP;
+    if (2 * c >= Rc) continue;
+    long h = hs[row >> 1];
+    cp_async(rs4 + e, r + (h * 2 + (row & 1)) * nrhs + r0 + 2 * c, 16);
+  }
+  for (int e = tid; e < KT * KT * 2; e += NT) {
+    int ks = e >> 1;
+    long h = hs[(ks / KT + 1) * KTH + ks % KT + 1];
+    ds[e] = omega / den[2 * h + (e & 1)];
+  }
+  cp_async_commit();
+  auto issue_rows = [&](int c) {
+    zf *dst = Ar + (c % 3) * 4 * 36;
+    for (int e = tid; e < 4 * ROWC; e += NT) {
+      int kk = e / ROWC, c16 = e - kk * ROWC;
+      int i = (c >> 2) + 4 * (kk >> 1), j = (c & 3) + 4 * (kk & 1);
+      long h = hs[(i + 1) * KTH + j + 1];
+      cp_async((char *)(dst + kk * 36) + 16 * c16, (const char *)(A + h * 36) + 16 * c16, 16);
+    }
+  };
+  issue_rows(0);
+  cp_async_commit();
+  issue_rows(1);
+  cp_async_commit();
+  // r has landed (all but the two newest groups): regroup each piece into pairs
+  cp_async_wait_group<2>();
+  __syncthreads();
+  for (int e = tid; e < KTH * KTH * 2 * RP; e += NT) {
+    float4 v = rs4[e];
+    rs4[e] = make_float4(v.x, v.z, v.y, v.w);
+  }
+  const int k = tid / RP, p = tid % RP;
+  const bool act = 2 * p < Rc;
+  auto x_at = [&](int c) -> long {
+    int i = (c >> 2) + 4 * (k >> 1), j = (c & 3) + 4 * (k & 1);
+    return (long)hs[(i + 1) * KTH + j + 1] * 2 * nrhs + r0 + 2 * p;
+  };
+  float4 xp[4][2];  // x of (q, q+1) in the global order, spin 0 and 1
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+    if (act) {
+      long xo = x_at(u);
+      xp[u][0] = *(const float4 *)(x + xo);
+      xp[u][1] = *(const float4 *)(x + xo + nrhs);
+    }
+  for (int c0 = 0; c0 < 16; c0 += 4) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int c = c0 + u;
+      if (c + 2 < 16) issue_rows(c + 2);
+      cp_async_commit();
+      cp_async_wait_group<2>();
+      __syncthreads();
+      int i = (c >> 2) + 4 * (k >> 1), j = (c & 3) + 4 * (k & 1);
+      if (act) {
+        int ks = i * KT + j;
+        const zf *Ah = Ar + ((c % 3) * 4 + k) * 36;
+        float2 vre[9][2], vim[9][2];
+#pragma unroll
+        for (int d = 0; d < 9; ++d) {
+          int ls = (i + d / 3) * KTH + (j + d % 3);
+#pragma unroll
+          for (int sp = 0; sp < 2; ++sp) {
+            float4 v = rs4[(ls * 2 + sp) * RP + p];
+            vre[d][sp] = make_float2(v.x, v.y);
+            vim[d][sp] = make_float2(v.z, v.w);
+          }
+        }
+        float2 svr[2], svi[2];
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+          zf a_[9][2];
+#pragma unroll
+          for (int d = 0; d < 9; ++d) ld2<float>(Ah + d * 4 + t * 2, a_[d][0], a_[d][1]);
+          float2 n0r = bc2(0.f), n0i = bc2(0.f), n1r = bc2(0.f), n1i = bc2(0.f);
+#pragma unroll
+          for (int d = 0; d < 9; ++d) {
+            float2 &nr = (d & 1) ? n1r : n0r, &ni = (d & 1) ? n1i : n0i;
+#pragma unroll
+            for (int sp = 0; sp < 2; ++sp) {
+              float ar = sp ? -a_[d][1].re : a_[d][0].re, ai = sp ? -a_[d][1].im : a_[d][0].im;
+              // cfma(acc, a, b): re += a.re b.re - a.im b.im, im += a.re b.im + a.im b.re
+              nr = __ffma2_rn(bc2(ar), vre[d][sp], nr);
+              nr = __ffma2_rn(bc2(-ai), vim[d][sp], nr);
+              ni = __ffma2_rn(bc2(ar), vim[d][sp], ni);
+              ni = __ffma2_rn(bc2(ai), vre[d][sp], ni);
+            }
+          }
+          float sc = ds[2 * ks + t];
+          if (t) sc = -sc;
+          svr[t] = __fmul2_rn(bc2(sc), __fadd2_rn(n0r, n1r));
+          svi[t] = __fmul2_rn(bc2(sc), __fadd2_rn(n0i, n1i));
+#pragma unroll
+          for (int d = 0; d < 9; ++d)
+#pragma unroll
+            for (int sp = 0; sp < 2; ++sp) {
+              // r_sub: rv.re = fma(-sr, a.re); fma(-si, a.im); rv.im = fma(-si, a.re); fma(sr, a.im)
+              float gg = (sp == t) ? 1.f : -1.f;
+              float2 sr = __fmul2_rn(bc2(gg), svr[t]), si = __fmul2_rn(bc2(gg), svi[t]);
+              float ar = a_[d][sp].re, ai = a_[d][sp].im;
+              vre[d][sp] = __ffma2_rn(neg2(sr), bc2(ar), vre[d][sp]);
+              vre[d][sp] = __ffma2_rn(neg2(si), bc2(ai), vre[d][sp]);
+              vim[d][sp] = __ffma2_rn(neg2(si), bc2(ar), vim[d][sp]);
+              vim[d][sp] = __ffma2_rn(sr, bc2(ai), vim[d][sp]);
+            }
+        }
+        long xo = x_at(c), xn = c + 4 < 16 ? x_at(c + 4) : 0;
+#pragma unroll
+        for (int sp = 0; sp < 2; ++sp) {
+          float4 xv = xp[u][sp];
+          xv.x += svr[sp].x;
+          xv.y += svi[sp].x;
+          xv.z += svr[sp].y;
+          xv.w += svi[sp].y;
+          *(float4 *)(x + xo + sp * nrhs) = xv;
+          if (c + 4 < 16) xp[u][sp] = *(const float4 *)(x + xn + sp * nrhs);
+        }
+#pragma unroll
+        for (int d = 0; d < 9; ++d) {
+          int ls = (i + d / 3) * KTH + (j + d % 3);
+#pragma unroll
+          for (int sp = 0; sp < 2; ++sp)
+            rs4[(ls * 2 + sp) * RP + p] = make_float4(vre[d][sp].x, vre[d][sp].y, vim[d][sp].x, vim[d][sp].y);
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int e = tid; e < KTH * KTH * 2 * RP; e += NT) {
+    int c = e % RP, row = e / RP;
+    if (2 * c >= Rc) continue;
+    long h = hs[row >> 1];
+    float4 v = rs4[e];
+    *(float4 *)(r + (h * 2 + (row & 1)) * nrhs + r0 + 2 * c) = make_float4(v.x, v.z, v.y, v.w);
+  }
+}
+
 // One right-hand side: a warp per site of the colour step, lane = 2 d + s
 // holds one term of the row's inner product; shared memory: A rows, den and
 // r of tile + halo [100][2].
@@ -979,6 +1149,28 @@ static int tile_default_R(int nrhs, int prec) {
   return 32;
 }
 
+// packed-pair kernel (FP32 stencil only); false when it does not apply
+template <typename T, typename S>
+static bool launch_tile_pk(const Level &L, const LevelOps &o, int tc, void *x, void *r, int nrhs, double omega,
+                           cudaStream_t s, int *rc) {
+  if constexpr (std::is_same<T, float>::value && std::is_same<S, zf>::value) {
+    if (nrhs % 2 || (uintptr_t)r % 16 || (uintptr_t)x % 16) return false;
+    constexpr int R = 32;
+    size_t smem = (size_t)KTH * KTH * 2 * R * sizeof(zf) + KT * KT * 2 * sizeof(float) + 3 * 4 * 36 * sizeof(zf) +
+                  KTH * KTH * sizeof(int);
+    static std::atomic<unsigned long long> limit_set{0};
+    *rc = set_smem_limit((const void *)k_kacz_tile_pk<R>, smem, limit_set);
+    if (*rc) return true;
+    dim3 grid((L.N / (2 * KT)) * (L.N / (4 * KT)), (nrhs + R - 1) / R);
+    k_kacz_tile_pk<R><<<grid, 2 * R, smem, s>>>(L.geo, tc, o.A.as<zf>(), o.den.as<float>(), (zf *)x, (zf *)r, nrhs,
+                                                (float)omega);
+    return true;
+  } else {
+    (void)L; (void)o; (void)tc; (void)x; (void)r; (void)nrhs; (void)omega; (void)s; (void)rc;
+    return false;
+  }
+}
+
 template <typename T, typename S>
 static int launch_tile(const Level &L, const LevelOps &o, int tc, void *x, void *r, int nrhs, double omega,
                        cudaStream_t s, int param) {
@@ -989,6 +1181,12 @@ static int launch_tile(const Level &L, const LevelOps &o, int tc, void *x, void 
     return WL_OK;
   }
   int R = param & 255, rpt = std::max(1, param >> 8);
+  if (rpt == 4) {  // packed pairs; where they do not apply, the one-per-thread kernel (same numbers)
+    int rc = WL_OK;
+    if (launch_tile_pk<T, S>(L, o, tc, x, r, nrhs, omega, s, &rc)) return rc;
+    R = 32;
+    rpt = 1;
+  }
   if (R == 8) return launch_tile_r<T, S, 8, 1>(L, o, tc, x, r, nrhs, omega, s);
   if constexpr (sizeof(T) == 8) {  // FP64: chunks up to 16, one right-hand side per thread
     return launch_tile_r<T, S, 16, 1>(L, o, tc, x, r, nrhs, omega, s);
@@ -1116,6 +1314,8 @@ int autotune_sweeps(wl_amg *a, int nrhs, int prec, cudaStream_t s) {
           cand.push_back(KTune{nrhs, prec, 2, tile_param(R, 1), 0.f});
           if (R >= 16 && prec != WL_FP64) cand.push_back(KTune{nrhs, prec, 2, tile_param(R, 2), 0.f});
         }
+      if (prec == WL_FP32 && nrhs >= 16 && nrhs % 2 == 0)  // packed FP32 pairs
+        cand.push_back(KTune{nrhs, prec, 2, tile_param(32, 4), 0.f});
     } else {
       cand.push_back(KTune{nrhs, prec, 0, 0, 0.f});
       if (nrhs > 1)  // block-resident sweeps (thread per item, as forms 0 and 1 at nrhs > 1)
@@ -1348,7 +1548,9 @@ static int kaczmarz_entry(wl_amg *a, int level, void *x, void *r, int nrhs, int 
     const Level &L = a->lev[level];
     bool tile = a->prm.kacz_order == 1 && wl::tile_ok(L.N);
     int R = param & 255, rpt = std::max(1, param >> 8);
-    bool ok = tile ? (form == 2 && (nrhs == 1 || ((R == 8 && rpt == 1) || ((R == 16 || R == 32) && rpt <= 2))) &&
+    bool ok = tile ? (form == 2 &&
+                      (nrhs == 1 || ((R == 8 && rpt == 1) || ((R == 16 || R == 32) && rpt <= 2)) ||
+                       (R == 32 && rpt == 4 && prec == WL_FP32)) &&
                       !(prec == WL_FP64 && (R > 16 || rpt > 1)))
                    : ((form == 0) || (form == 1 && param >= 1) ||
                       (form == 3 && nrhs > 1 && wl::block_fits(L, param, prec)));
