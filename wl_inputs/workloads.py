@@ -82,6 +82,10 @@ for _name, _w in WORKLOADS.items():
 # its description; chosen by measurement (V(4,4), one pass, tile-coloured
 # sweeps, FP32 matvec inside a restart cycle with FP64 true residuals)
 WORKLOADS["C4"].update(nu=4, gs_passes=1, kacz_order=1, arnoldi_matvec=1)
+# the single right-hand-side mixed-precision workload with the same cycle; C3b
+# is its variant with BF16-stored stencils and interpolation weights
+WORKLOADS["C3"].update(nu=4, gs_passes=1, kacz_order=1, arnoldi_matvec=1)
+WORKLOADS["C3b"] = dict(WORKLOADS["C3"], precision="bf16")
 
 
 def _shifts():
@@ -120,7 +124,13 @@ def workload(name: str, with_gauge: bool = True, eta=None):
     w = dict(WORKLOADS[name])
     w["name"] = name
     w["levels"] = len(w["blocks"]) + 1
-    sh = _shifts().get(name)
+    shifts = _shifts()
+    sh = shifts.get(name)
+    if sh is None:  # a workload on the same gauge field and target shares its shift
+        for other, ow in WORKLOADS.items():
+            if other in shifts and all(ow.get(k) == w.get(k) for k in ("N", "beta", "sweeps", "seed", "target")):
+                sh = shifts[other]
+                break
     w["m"] = None if sh is None or sh.get("m") is None else float(sh["m"])
     w["eta0"] = None if sh is None or sh.get("eta0") is None else float(sh["eta0"])
     if eta is not None:   # eta_min(D) = eta: m = eta - min Re lambda(D_0)
