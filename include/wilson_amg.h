@@ -30,9 +30,12 @@
  *   are the layouts of the hierarchy file (see amg_export).
  *
  * Ownership: the caller owns every array it passes; the library copies the
- * gauge in wilson_create and owns its hierarchy and workspace.  All work is
- * enqueued on the stream given to wilson_create; calls that return results
- * to the host (amg_solve's info, amg_fgmres) synchronise that stream.
+ * gauge in wilson_create and owns its hierarchy and workspace.  Streams:
+ * each wl_op runs its kernels on a work stream of its own, which at every
+ * call first waits (an event) for the work already queued on the stream
+ * given to wilson_create, so device arrays produced there are ready.  Calls
+ * that return results to the host (amg_solve, amg_fgmres, amg_rho, the
+ * per-step entry points) synchronise the work stream before returning.
  *
  * Errors: 0 = OK, 1 = WL_NOT_CONVERGED (x holds the best iterate), negative
  * values are errors; wl_last_error() returns a message for the calling

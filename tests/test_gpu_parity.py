@@ -274,6 +274,31 @@ def test_rho_protocol(O, shared, cycle):
         amg.close()
 
 
+def test_rho_divergent_cycle(O, ops, tmp_path):
+    """A cycle whose coarse correction is scaled up diverges: GPU and oracle
+    stop at the last finite error norm with the same ratio (the definition in
+    Sec. 4 presumes convergence); the GPU call reports WL_NOT_CONVERGED."""
+    from oracle.hierfile import write
+    w, op = ops("C1")
+    h = O.Hierarchy.setup(w["N"], w["U"], w["m"], O.setup_params(w["blocks"], k_r=w["k"], k_e=w["k"],
+                                                                  seed=w["seed"]))
+    Pw, As = h.export()
+    As = [a * 1e-6 for a in As]
+    hb = O.Hierarchy.from_arrays(h.N, h.U, h.m, h.Nl, h.Bl[:-1], Pw, As)
+    path = str(tmp_path / "scaled.wlh")
+    write(path, h.U, h.m, h.Nl, h.Bl, Pw, As)
+    amg = W.amg_import(op, path, W.amg_params_default(nu_pre=1, nu_post=1))
+    x0 = cgauss(4, 1, h.n(0))
+    rr, ir, hr, met = hb.rho(x0, tol=1e-8, maxit=100, nu1=1, nu2=1, gamma=1)
+    assert not met and rr > 1e4
+    rc, rho, it, hist = W.amg_rho(amg, T(x0[None]), T(np.zeros((1, h.n(0)))), 1, 1e-8, 100, hist=True)
+    assert rc == W.WL_NOT_CONVERGED
+    assert abs(int(it[0]) - ir) <= 1 and np.isfinite(rho[0])
+    k = min(int(it[0]), ir)
+    assert np.abs(hist[0, :k + 1] / hr[:k + 1] - 1).max() <= 1e-6
+    assert abs(rho[0] - rr) <= 1e-3 * rr
+
+
 @pytest.mark.parametrize("name", ["T64", "C1"])
 def test_transfers_and_coarsest(shared, name):
     w, op, h, amg, _ = shared(name)
