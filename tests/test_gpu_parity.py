@@ -510,3 +510,20 @@ def test_degenerate_inputs(O, shared, ops):
     with pytest.raises(W.WilsonAMGError) as e:
         W.wilson_create(T(w["U"]), N, -2.0)
     assert e.value.code == W.WL_EINVAL
+
+
+def test_batch_above_the_launch_limit(shared):
+    """amg_solve splits a call with more right-hand sides than one batched
+    launch takes (256) into chunks; every right-hand side converges and
+    matches its own single solve."""
+    w, op, h, amg, _ = shared("T32")
+    N, nrhs = w["N"], 300
+    b = rhs_batch(N, nrhs, 41)
+    psi = torch.zeros_like(T(b))
+    rc, info = W.amg_solve(amg, T(b), psi, nrhs, 1e-11)
+    assert rc == W.WL_OK and len(info) == nrhs
+    assert max(i["true_relres"] for i in info) <= 1e-11
+    for q in (0, 255, 256, 299):
+        one = torch.zeros_like(T(b[q:q + 1]))
+        W.amg_solve(amg, T(b[q:q + 1]), one, 1, 1e-11)
+        assert np.linalg.norm(H(one[0]) - H(psi[q])) / np.linalg.norm(H(one[0])) <= 1e-8, q
