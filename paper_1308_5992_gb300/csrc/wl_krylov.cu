@@ -199,12 +199,18 @@ __global__ void __launch_bounds__(256) k_maxpy(const cx<Tv> *__restrict__ V, lon
   w[e] = acc;
 }
 
-__global__ void k_scale_rhs(const zd *__restrict__ in, zd *__restrict__ out, const double *__restrict__ f,
-                            long E, int R) {
+// out = f[rhs] in (the next Arnoldi vector) and its copy in the cycle
+// precision, the next cycle's input (the cast rounds as k_cast does)
+template <typename Tc>
+__global__ void k_scale_rhs_cyc(const zd *__restrict__ in, zd *__restrict__ out, cx<Tc> *__restrict__ cyc,
+                                const double *__restrict__ f, long E, int R) {
   long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= E) return;
-  out[e] = f[e % R] * in[e];
+  zd v = f[e % R] * in[e];
+  out[e] = v;
+  cyc[e] = ccast<Tc>(v);
 }
+
 
 __global__ void k_sub(const zd *__restrict__ a, const zd *__restrict__ b, zd *__restrict__ c, long E) {
   long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -423,19 +429,20 @@ int fg_cycle(wl_amg *a, const zd *bnorm_h, zd *xh, int nrhs, double tol, const i
   (void)bnorm_h;
   WL_CUDA(cudaMemcpyAsync(k.active, active, sizeof(int) * nrhs, cudaMemcpyHostToDevice, s));
   WL_CUDA(cudaMemsetAsync(k.iters, 0, sizeof(int) * nrhs, s));
+  // v_j = f[rhs] w is written together with the cycle-precision copy that
+  // the cycle of step j reads (lev[0].f)
+  auto scale_next = [&](const zd *in, zd *out) {
+    if (prec == WL_FP64) k_scale_rhs_cyc<double><<<gE, 256, 0, s>>>(in, out, a->lev[0].f.as<zd>(), k.inv, E, nrhs);
+    else k_scale_rhs_cyc<float><<<gE, 256, 0, s>>>(in, out, a->lev[0].f.as<zf>(), k.inv, E, nrhs);
+    wl_count_launches(1);
+  };
   k_cycle_start<<<WL_GRID(nrhs, 128), 128, 0, s>>>(k);
-  k_scale_rhs<<<gE, 256, 0, s>>>(rr, V, k.inv, E, nrhs);
-  wl_count_launches(2);
+  wl_count_launches(1);
+  scale_next(rr, V);
   int jdone = 0;
   for (int j = 0; j < m; ++j) {
-    zd *vj = V + j * vs;
     void *zj = Zb + (size_t)j * vs * zb_;
-    // z_j = M(v_j) in the cycle precision
-    if (prec == WL_FP64) WL_CUDA(cudaMemcpyAsync(a->lev[0].f.p, vj, sizeof(zd) * E, cudaMemcpyDeviceToDevice, s));
-    else {
-      k_cast<float, double><<<gE, 256, 0, s>>>(vj, a->lev[0].f.as<zf>(), E);
-      wl_count_launches(1);
-    }
+    // z_j = M(v_j) in the cycle precision (lev[0].f holds v_j)
     WL_TRY(cycle_run(a, nrhs, prec, s));
     WL_CUDA(cudaMemcpyAsync(zj, a->lev[0].x.p, zb_ * E, cudaMemcpyDeviceToDevice, s));
     // w = Dhat z_j (FP64)
@@ -454,10 +461,7 @@ int fg_cycle(wl_amg *a, const zd *bnorm_h, zd *xh, int nrhs, double tol, const i
     WL_CUDA(cudaMemsetAsync(k.running, 0, sizeof(int) * 2, s));
     k_givens<<<WL_GRID(nrhs, 128), 128, 0, s>>>(k, j, tol);
     wl_count_launches(1);
-    if (j + 1 < m) {
-      k_scale_rhs<<<gE, 256, 0, s>>>(w, V + (j + 1) * vs, k.inv, E, nrhs);
-      wl_count_launches(1);
-    }
+    if (j + 1 < m) scale_next(w, V + (j + 1) * vs);
     WL_CUDA(cudaGetLastError());
     int run[2];
     WL_CUDA(cudaMemcpyAsync(h_d + nrhs, k.running, sizeof(int) * 2, cudaMemcpyDeviceToHost, s));
