@@ -873,7 +873,7 @@ int kaczmarz_colour(wl_amg *a, int l, int prec, void *x, void *r, int nrhs, int 
 }
 
 // resident blocks of 128 threads for the cooperative sweep (cached per
-// kernel instance)
+// kernel instance and device)
 template <typename T, typename S>
 static int coop_blocks() {
   static std::atomic<int> cached[WL_MAX_DEVICES];  // per device, 0 = not yet known
