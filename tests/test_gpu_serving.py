@@ -85,3 +85,34 @@ def test_admission_by_memory(resident):
         W.srv_add(srv, a0)
     assert e.value.code == W.WL_OOM
     srv.close()
+
+
+def test_alone_equals_mix_benchmark_cycle():
+    """The serving configuration the benchmark runs (FP32 tile-coloured
+    V(4,4), FP32 Arnoldi matvec, one Gram-Schmidt pass): a right-hand side
+    gives the same solution alone and inside a larger request that overflows
+    the slots, so it is admitted while its batch mates are on the GPU."""
+    w = workload("T64")
+    op = W.wilson_create(_T(w["U"]), w["N"], w["m"])
+    p = W.amg_params_default(k_r=w["k"], k_e=w["k"], seed=w["seed"], precision=W.WL_FP32, nu_pre=4, nu_post=4,
+                             gs_passes=1, kacz_order=1, arnoldi_matvec=1)
+    p.levels = len(w["blocks"]) + 1
+    for l, b in enumerate(w["blocks"]):
+        p.block[l] = b
+    amg = W.amg_setup(op, p)
+    b = _T(rhs_batch(w["N"], 9, 43))
+    srv = W.srv_create(8 << 30, 4)
+    cfg = W.srv_add(srv, amg)
+    W.srv_start(srv)
+    x_alone = torch.zeros_like(b[5:6])
+    rid = W.srv_submit(srv, cfg, b[5:6].contiguous(), x_alone, 1, TOL)
+    W.srv_drain(srv)
+    assert W.srv_poll(srv, rid, 1)[0]
+    x_mix = torch.zeros_like(b)
+    rid = W.srv_submit(srv, cfg, b, x_mix, 9, TOL)
+    W.srv_drain(srv)
+    done, info, lat = W.srv_poll(srv, rid, 9)
+    assert done and all(i["status"] == W.WL_OK and i["true_relres"] <= TOL for i in info)
+    assert float(torch.linalg.norm(x_mix[5] - x_alone[0]) / torch.linalg.norm(x_alone[0])) <= 1e-9
+    assert max(_residual(op, w, b, x_mix)) <= 1e-9
+    srv.close()
