@@ -366,11 +366,14 @@ def test_fgmres_and_solve_match_oracle(shared, name):
 
 
 @pytest.mark.parametrize("prec", [W.WL_FP32, W.WL_FP32_BF16])
-def test_mixed_precision_solve(O, ops, shared, prec):
+@pytest.mark.parametrize("order,matvec", [(0, 0), (1, 1)])
+def test_mixed_precision_solve(O, ops, shared, prec, order, matvec):
     """FP32 (or BF16-stored) cycle inside FP64 FGMRES with iterative
-    refinement reaches the FP64 accuracy."""
+    refinement reaches the FP64 accuracy, with the 16-colour or the
+    tile-coloured ordering and the FP64 or FP32 Arnoldi matvec."""
     w, op, h, _, path = shared("C2")
-    amg = W.amg_import(op, path, W.amg_params_default(zero_guess=1, precision=prec))
+    amg = W.amg_import(op, path, W.amg_params_default(zero_guess=1, precision=prec, kacz_order=order,
+                                                      arnoldi_matvec=matvec))
     b = rhs_batch(w["N"], 1, 12)
     psi = torch.zeros_like(T(b))
     rc, info = W.amg_solve(amg, T(b), psi, 1, 1e-12)
@@ -527,3 +530,42 @@ def test_batch_above_the_launch_limit(shared):
         one = torch.zeros_like(T(b[q:q + 1]))
         W.amg_solve(amg, T(b[q:q + 1]), one, 1, 1e-11)
         assert np.linalg.norm(H(one[0]) - H(psi[q])) / np.linalg.norm(H(one[0])) <= 1e-8, q
+
+
+def _round_bf16(a):
+    """complex128 -> nearest float32 -> nearest bfloat16 (ties to even),
+    returned as complex128: the rounding the library applies to stencils"""
+    def r(x):
+        u = np.ascontiguousarray(x.astype(np.float32)).view(np.uint32).astype(np.uint64)
+        u = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+        return u.astype(np.uint32).view(np.float32).astype(np.float64)
+    return r(a.real) + 1j * r(a.imag)
+
+
+def test_bf16_stencil_sweeps(O, ops, tmp_path):
+    """BF16-stored stencils: on a hierarchy whose coarse stencils are already
+    BF16 numbers (so every stored copy is exact), the BF16 Kaczmarz sweeps of
+    both orderings (the tile kernel on the 64x64 level) match the oracle's
+    FP64 sweeps on the same operator to FP32 rounding."""
+    from oracle.hierfile import write
+    w, op = ops("T128")
+    h = O.Hierarchy.setup(w["N"], w["U"], w["m"], O.setup_params(w["blocks"], k_r=w["k"], k_e=w["k"],
+                                                                  seed=w["seed"]))
+    Pw, As = h.export()
+    As = [_round_bf16(a) for a in As]
+    hb = O.Hierarchy.from_arrays(h.N, h.U, h.m, h.Nl, h.Bl[:-1], Pw, As)
+    path = str(tmp_path / "bf16.wlh")
+    write(path, h.U, h.m, h.Nl, h.Bl, Pw, As)
+    nrhs = 6
+    for order, oorder in ((0, O.ORDER_COLOUR), (1, O.ORDER_TILE)):
+        amg = W.amg_import(op, path, W.amg_params_default(zero_guess=1, kacz_order=order))
+        for l in range(1, h.L - 1):
+            n = h.n(l)
+            x0 = 0.1 * np.stack([cgauss(230 + l, r, n) for r in range(nrhs)])
+            r0 = np.stack([cgauss(240 + l, r, n) for r in range(nrhs)])
+            ref = [hb.kaczmarz(l, x0[r], r0[r], order=oorder, sweeps=2) for r in range(nrhs)]
+            xr, rr = np.stack([a for a, _ in ref]), np.stack([b for _, b in ref])
+            xg, rg = T(x0), T(r0)
+            W.amg_kaczmarz(amg, l, xg, rg, nrhs, 2, W.WL_FP32_BF16)
+            assert rel(H(xg), xr) <= 1e-5 and rel(H(rg), rr) <= 1e-5, (order, l, rel(H(xg), xr))
+        amg.close()

@@ -70,6 +70,9 @@ WORKLOADS["T32"] = dict(N=32, beta=3.0, sweeps=50, target=2e-2, seed=12, blocks=
                         precision="fp64", nrhs=1)
 WORKLOADS["T64"] = dict(N=64, beta=6.0, sweeps=100, target=1e-2, seed=13, blocks=[2, 2], k=8,
                         precision="fp64", nrhs=1)
+# a coarse level of side 64 (the smallest the tile-coloured ordering covers)
+WORKLOADS["T128"] = dict(N=128, beta=6.0, sweeps=100, target=1e-2, seed=14, blocks=[2, 2, 2], k=6,
+                         precision="fp64", nrhs=1)
 
 
 # solve-cycle parameters (defaults: V(2,2), FGMRES(20), two Gram-Schmidt passes)
