@@ -543,20 +543,44 @@ def _round_bf16(a):
 
 
 def test_bf16_stencil_sweeps(O, ops, tmp_path):
-    """BF16-stored stencils: on a hierarchy whose coarse stencils are already
-    BF16 numbers (so every stored copy is exact), the BF16 Kaczmarz sweeps of
-    both orderings (the tile kernel on the 64x64 level) match the oracle's
-    FP64 sweeps on the same operator to FP32 rounding."""
+    """BF16 storage: on a hierarchy whose coarse stencils and interpolation
+    weights are already BF16 numbers (so every stored copy is exact), the
+    BF16 coarse stencil apply, restriction, prolongation and the Kaczmarz
+    sweeps of both orderings (the tile kernel on the 64x64 level) match the
+    oracle's FP64 steps on the same operators to FP32 rounding."""
     from oracle.hierfile import write
     w, op = ops("T128")
     h = O.Hierarchy.setup(w["N"], w["U"], w["m"], O.setup_params(w["blocks"], k_r=w["k"], k_e=w["k"],
                                                                   seed=w["seed"]))
     Pw, As = h.export()
+    Pw = [_round_bf16(p) for p in Pw]
     As = [_round_bf16(a) for a in As]
     hb = O.Hierarchy.from_arrays(h.N, h.U, h.m, h.Nl, h.Bl[:-1], Pw, As)
     path = str(tmp_path / "bf16.wlh")
     write(path, h.U, h.m, h.Nl, h.Bl, Pw, As)
     nrhs = 6
+    # BF16-stored coarse stencil apply and BF16-stored transfers
+    amg = W.amg_import(op, path, W.amg_params_default(zero_guess=1))
+    for l in range(h.L):
+        n = h.n(l)
+        x = np.stack([cgauss(250 + l, r, n) for r in range(nrhs)])
+        if l >= 1:
+            y = torch.zeros_like(T(x))
+            W.amg_level_apply(amg, l, T(x), y, nrhs, W.WL_FP32_BF16)
+            ref = np.stack([hb.apply(l, x[r]) for r in range(nrhs)])
+            assert rel(H(y), ref) <= 1e-6, ("apply", l, rel(H(y), ref))
+        if l + 1 < h.L:
+            nc = h.n(l + 1)
+            fc = torch.zeros((nrhs, nc), dtype=torch.complex128, device=DEV)
+            W.amg_restrict(amg, l, T(x), fc, nrhs, W.WL_FP32_BF16)
+            ref = np.stack([hb.restrict(l, x[r]) for r in range(nrhs)])
+            assert rel(H(fc), ref) <= 1e-6, ("restrict", l, rel(H(fc), ref))
+            e = np.stack([cgauss(260 + l, r, nc) for r in range(nrhs)])
+            xg = torch.zeros_like(T(x))
+            W.amg_prolong(amg, l, T(e), xg, nrhs, W.WL_FP32_BF16)
+            ref = np.stack([hb.prolong(l, e[r], np.zeros(n)) for r in range(nrhs)])
+            assert rel(H(xg), ref) <= 1e-6, ("prolong", l, rel(H(xg), ref))
+    amg.close()
     for order, oorder in ((0, O.ORDER_COLOUR), (1, O.ORDER_TILE)):
         amg = W.amg_import(op, path, W.amg_params_default(zero_guess=1, kacz_order=order))
         for l in range(1, h.L - 1):
