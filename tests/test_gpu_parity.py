@@ -349,6 +349,24 @@ def test_w_cycle(O, shared, name):
     assert rel(H(xg), ref) <= 1e-12, rel(H(xg), ref)
 
 
+@pytest.mark.parametrize("cycle,nrhs", [(W.WL_CYCLE_V, 3), (W.WL_CYCLE_W, 3), (W.WL_CYCLE_V, 24)])
+def test_tile_ordered_cycle(O, shared, cycle, nrhs):
+    """Whole cycles with the tile-coloured ordering (tile kernel on the 128x128
+    grid, 16 colours below) against the oracle's tile-ordered cycle: FP64
+    1e-12, FP32 1e-5; 24 right-hand sides take the tiled stencil and the
+    autotuned launch forms."""
+    w, op, h, _, path = shared("C2")
+    amg = W.amg_import(op, path, W.amg_params_default(zero_guess=1, cycle=cycle, nu_pre=4, nu_post=4,
+                                                      kacz_order=1))
+    n = h.n(0)
+    f = np.stack([cgauss(331, q, n) for q in range(nrhs)])
+    ref = np.stack([h.cycle(f[q], nu1=4, nu2=4, gamma=cycle + 1, order=O.ORDER_TILE) for q in range(nrhs)])
+    for prec, tol in ((W.WL_FP64, 1e-12), (W.WL_FP32, 1e-5)):
+        xg = torch.zeros_like(T(f))
+        W.amg_cycle(amg, T(f), xg, nrhs, prec)
+        assert rel(H(xg), ref) <= tol, (prec, rel(H(xg), ref))
+
+
 # ---------------------------------------------------------- full solves
 @pytest.mark.parametrize("name", ["T64", "C1", "C2"])
 def test_fgmres_and_solve_match_oracle(shared, name):
