@@ -479,3 +479,19 @@ def test_rho_divergent_cycle_stops_at_overflow(O, h32):
     assert not met and 2 <= nu < 100
     assert np.all(np.isfinite(hist)) and hist[-1] > 1e100
     assert rho > 1e4 and rho == hist[-1] / hist[-2]
+
+
+def test_hierarchy_complexities(O, h64):
+    """Sec. 4's structure: with 2x2 cells down to the N = 16 coarsest grid,
+    N = 128 gives 4 grids and N = 256 gives 5 (the Sec. 4 workloads), and the
+    grid and operator complexities stay below the stated 1.4."""
+    from wl_inputs.workloads import WORKLOADS
+    gold = json.load(open(os.path.join(GOLDEN, "paper_structure.json")))
+    assert len(WORKLOADS["P128_b6_c0"]["blocks"]) + 1 == gold["grids_N128"]
+    assert len(WORKLOADS["P256_b6_c0"]["blocks"]) + 1 == gold["grids_N256"]
+    h, _ = h64
+    rows = [h.dense(l).shape[0] for l in range(h.L)]
+    nnz = [int((np.abs(h.dense(l)) > 0).sum()) for l in range(h.L)]
+    assert h.Nl[-1] == gold["coarsest_N"]
+    assert sum(rows) / rows[0] <= gold["max_complexity"]
+    assert sum(nnz) / nnz[0] <= gold["max_complexity"]
