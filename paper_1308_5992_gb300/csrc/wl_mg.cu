@@ -413,7 +413,16 @@ __global__ void __launch_bounds__(4 * R / RPT) k_kacz_tile(Geo g, int tc, const 
         xp[u][m][1] = x[xo + m * RQ + nrhs];
       }
   }
+  // Steps 4 i' .. 4 i' + 3 walk row i' of every quadrant.  Along a row the
+  // 3x3 window of r around the site (rows da, columns db) slides by one
+  // column: the columns that stay are kept in registers, one new column is
+  // read and the column that leaves is written back (the whole window at
+  // the row's end).  No other thread touches a kept cell meanwhile: at every
+  // step the four quadrants' windows are disjoint, and the kept cells lie in
+  // this thread's windows of both steps.  Two thirds of the shared-memory
+  // traffic of r go away; the arithmetic and its order are unchanged.
   for (int c0 = 0; c0 < 16; c0 += 4) {
+    cx<T> rv[RPT][9][2];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const int c = c0 + u;
@@ -426,14 +435,18 @@ __global__ void __launch_bounds__(4 * R / RPT) k_kacz_tile(Geo g, int tc, const 
       if (act[0]) {
         int ks = i * KT + j;
         const S *Ah = Ar + ((c % 3) * 4 + k) * 36;
-        cx<T> rv[RPT][9][2];
 #pragma unroll
         for (int d = 0; d < 9; ++d) {
           int ls = (i + d / 3) * KTH + (j + d % 3);  // (i + da + 1, j + db + 1)
 #pragma unroll
           for (int m = 0; m < RPT; ++m) {
-            rv[m][d][0] = rs[(ls * 2) * R + q0 + m * RQ];
-            rv[m][d][1] = rs[(ls * 2 + 1) * R + q0 + m * RQ];
+            if (u > 0 && d % 3 < 2) {  // column db + 1 of the previous step
+              rv[m][d][0] = rv[m][d + 1][0];
+              rv[m][d][1] = rv[m][d + 1][1];
+            } else {
+              rv[m][d][0] = rs[(ls * 2) * R + q0 + m * RQ];
+              rv[m][d][1] = rs[(ls * 2 + 1) * R + q0 + m * RQ];
+            }
           }
         }
         cx<T> sv[RPT][2];
@@ -473,6 +486,7 @@ __global__ void __launch_bounds__(4 * R / RPT) k_kacz_tile(Geo g, int tc, const 
         }
 #pragma unroll
         for (int d = 0; d < 9; ++d) {
+          if (u < 3 && d % 3) continue;  // kept for the next step
           int ls = (i + d / 3) * KTH + (j + d % 3);
 #pragma unroll
           for (int m = 0; m < RPT; ++m)
