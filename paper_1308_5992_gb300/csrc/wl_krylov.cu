@@ -680,7 +680,10 @@ extern "C" int wl_time_kernel(wl_amg *a, int kind, int level, int nrhs, int prec
     switch (kind) {
       case WL_K_DHAT: return wl::dhat_apply_dev(a->op, a->Z.p, prec != WL_FP64, a->w.as<zd>(), nrhs, s);
       case WL_K_KACZ: return wl::kaczmarz_colour(a, level, prec, L.x.p, L.r.p, nrhs, rep & 15, s);
-      case WL_K_KACZ_TILE: return wl::kaczmarz_tile(a, level, prec, L.x.p, L.r.p, nrhs, rep & 3, s);
+      case WL_K_KACZ_TILE: {  // the autotuned form where the level has one, else the default chunk
+        KTune t = wl::sweep_form_of(a, level, prec, nrhs);
+        return wl::kaczmarz_tile(a, level, prec, L.x.p, L.r.p, nrhs, rep & 3, s, t.form == 2 ? t.param : 0);
+      }
       case WL_K_STENCIL: return wl::stencil_apply(a, level, prec, L.x.p, L.r.p, L.f.p, nrhs, s);
       case WL_K_RESTRICT: return wl::restrict_op(a, level, prec, L.r.p, a->lev[level + 1].f.p, nrhs, s);
       case WL_K_PROLONG: return wl::prolong_op(a, level, prec, a->lev[level + 1].x.p, L.x.p, nrhs, s);

@@ -321,6 +321,58 @@ __device__ __forceinline__ void tile_stage_rows(const Geo &g, int A0, int B0, co
   }
 }
 
+// Row inner product of a Kaczmarz step, num = sum_d a_0 r_0 - a_1 r_1
+// (complex, a_s = A[h][d][t][s], r_s of neighbour d), as eight independent
+// chains: per spin s, P_s = sum_d Re(a_s) (Re r_s, Im r_s) and
+// Q_s = sum_d Im(a_s) (Re r_s, Im r_s), then a_s r_s summed is
+// (P.re - Q.im, P.im + Q.re).  PAIRED (FP32 only) runs each (re, im) pair of
+// chains as one paired FMA (__ffma2_rn), lane for lane the same operation,
+// so both forms give the same bits.
+template <typename T, bool PAIRED>
+__device__ __forceinline__ cx<T> row_dot(const cx<T> (&a)[9][2], const cx<T> (&rv)[9][2]) {
+  cx<T> P[2], Q[2];
+  if constexpr (PAIRED) {
+    static_assert(std::is_same<T, float>::value, "paired FMAs are FP32");
+    float2 p2[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)}, q2[2] = {p2[0], p2[0]};
+#pragma unroll
+    for (int d = 0; d < 9; ++d)
+#pragma unroll
+      for (int sp = 0; sp < 2; ++sp) {
+        float2 v = make_float2(rv[d][sp].re, rv[d][sp].im);
+        p2[sp] = __ffma2_rn(make_float2(a[d][sp].re, a[d][sp].re), v, p2[sp]);
+        q2[sp] = __ffma2_rn(make_float2(a[d][sp].im, a[d][sp].im), v, q2[sp]);
+      }
+#pragma unroll
+    for (int sp = 0; sp < 2; ++sp) {
+      P[sp] = mk(p2[sp].x, p2[sp].y);
+      Q[sp] = mk(q2[sp].x, q2[sp].y);
+    }
+  } else {
+#pragma unroll
+    for (int sp = 0; sp < 2; ++sp) P[sp] = Q[sp] = mk<T>(0, 0);
+#pragma unroll
+    for (int d = 0; d < 9; ++d)
+#pragma unroll
+      for (int sp = 0; sp < 2; ++sp) {
+        cx<T> v = rv[d][sp], c = a[d][sp];
+        P[sp].re = fma(c.re, v.re, P[sp].re);
+        P[sp].im = fma(c.re, v.im, P[sp].im);
+        Q[sp].re = fma(c.im, v.re, Q[sp].re);
+        Q[sp].im = fma(c.im, v.im, Q[sp].im);
+      }
+  }
+  return mk((P[0].re - Q[0].im) - (P[1].re - Q[1].im), (P[0].im + Q[0].re) - (P[1].im + Q[1].re));
+}
+
+// r_sub as two paired FMAs: (re, im) += (-sr, -si) Re a, then += (-si, sr) Im a
+// (the same four roundings in the same order per component)
+__device__ __forceinline__ void r_sub_paired(cx<float> &rv, float2 m1, float2 m2, cx<float> a) {
+  float2 v = make_float2(rv.re, rv.im);
+  v = __ffma2_rn(m1, make_float2(a.re, a.re), v);
+  v = __ffma2_rn(m2, make_float2(a.im, a.im), v);
+  rv = mk(v.x, v.y);
+}
+
 // Several right-hand sides: a block of 4 R / RPT threads, thread (k, q) owns
 // site k of the current colour step and right-hand sides r0 + q + j R / RPT
 // (j < RPT), which share the stencil coefficients and the index arithmetic.
@@ -331,7 +383,7 @@ __device__ __forceinline__ void tile_stage_rows(const Geo &g, int A0, int B0, co
 // start on 16-byte boundaries (16-byte copies), else one complex per copy.
 // Every right-hand side sees the same operations in the same order for any
 // RPT, so the variants agree bit for bit.
-template <typename T, typename S, int R, int RPT>
+template <typename T, typename S, int R, int RPT, bool PAIRED>
 __global__ void __launch_bounds__(4 * R / RPT) k_kacz_tile(Geo g, int tc, const S *__restrict__ A,
                                                            const T *__restrict__ den, cx<T> *__restrict__ x,
                                                            cx<T> *__restrict__ r, int nrhs, int vec, T omega) {
@@ -459,18 +511,22 @@ __global__ void __launch_bounds__(4 * R / RPT) k_kacz_tile(Geo g, int tc, const 
           if (t) sc = -sc;
 #pragma unroll
           for (int m = 0; m < RPT; ++m) {
-            cx<T> n0 = mk<T>(0, 0), n1 = mk<T>(0, 0);  // two chains: independent FMAs in flight
+            sv[m][t] = sc * row_dot<T, PAIRED>(a_, rv[m]);
+            if constexpr (PAIRED) {
+              float sr = sv[m][t].re, si = sv[m][t].im;  // g_s g_t = +1 (s = t), -1 (s != t)
+              float2 m1p = make_float2(-sr, -si), m2p = make_float2(-si, sr);
+              float2 m1n = make_float2(sr, si), m2n = make_float2(si, -sr);
 #pragma unroll
-            for (int d = 0; d < 9; ++d) {
-              cx<T> &nn = (d & 1) ? n1 : n0;
-              cfma(nn, a_[d][0], rv[m][d][0]);
-              cfma(nn, mk<T>(-a_[d][1].re, -a_[d][1].im), rv[m][d][1]);
+              for (int d = 0; d < 9; ++d)
+#pragma unroll
+                for (int sp = 0; sp < 2; ++sp)
+                  r_sub_paired(rv[m][d][sp], sp == t ? m1p : m1n, sp == t ? m2p : m2n, a_[d][sp]);
+            } else {
+#pragma unroll
+              for (int d = 0; d < 9; ++d)
+#pragma unroll
+                for (int sp = 0; sp < 2; ++sp) r_sub(rv[m][d][sp], (sp == t) ? (T)1 : (T)-1, sv[m][t], a_[d][sp]);
             }
-            sv[m][t] = sc * (n0 + n1);
-#pragma unroll
-            for (int d = 0; d < 9; ++d)
-#pragma unroll
-              for (int sp = 0; sp < 2; ++sp) r_sub(rv[m][d][sp], (sp == t) ? (T)1 : (T)-1, sv[m][t], a_[d][sp]);
           }
         }
         long xo = x_at(c), xn = c + 4 < 16 ? x_at(c + 4) : 0;
@@ -514,175 +570,6 @@ __global__ void __launch_bounds__(4 * R / RPT) k_kacz_tile(Geo g, int tc, const 
       long h = hs[row >> 1];
       r[(h * 2 + (row & 1)) * nrhs + r0 + q2] = rs[e];
     }
-  }
-}
-
-// FP32, complex-float stencil, two adjacent right-hand sides per thread in
-// packed pairs: every FMA of the RPT = 1 kernel is done for both right-hand
-// sides by one paired FMA (__ffma2_rn, sm_100 and later) in the same order,
-// so the result is bit-identical.  In shared memory each 16-byte piece of a
-// row of r holds (re_q, re_q+1, im_q, im_q+1) instead of the global order
-// (re_q, im_q, re_q+1, im_q+1).  Needs 16-byte aligned rows (vec).
-__device__ __forceinline__ float2 bc2(float v) { return make_float2(v, v); }
-__device__ __forceinline__ float2 neg2(float2 v) { return make_float2(-v.x, -v.y); }
-
-template <int R>
-__global__ void __launch_bounds__(2 * R) k_kacz_tile_pk(Geo g, int tc, const zf *__restrict__ A,
-                                                        const float *__restrict__ den, zf *__restrict__ x,
-                                                        zf *__restrict__ r, int nrhs, float omega) {
-  extern __shared__ __align__(16) unsigned char sm_raw[];
-  float4 *rs4 = (float4 *)sm_raw;                       // [100][2][R / 2] pieces
-  float *ds = (float *)(rs4 + KTH * KTH * 2 * (R / 2));
-  zf *Ar = (zf *)(ds + KT * KT * 2);
-  int *hs = (int *)(Ar + 3 * 4 * 36);
-  constexpr int NT = 2 * R;
-  constexpr int RP = R / 2;                             // right-hand-side pairs (threads per site)
-  constexpr int ROWC = 36 * (int)sizeof(zf) / 16;
-  int A0, B0;
-  tile_origin(g, tc, A0, B0);
-  int r0 = blockIdx.y * R;
-  int Rc = min(R, nrhs - r0);  // even (nrhs even, R even)
-  int tid = threadIdx.x;
-  for (int ls = tid; ls < KTH * KTH; ls += NT) {
-    int a = A0 + ls / KTH - 1, b = B0 + ls % KTH - 1;
-    hs[ls] = g.idx(a + b, a - b);
-  }
-  __syncthreads();
-  for (int e = tid; e < KTH * KTH * 2 * RP; e += NT) {
-    int c = e % RP, row = e / RP;
-    if (2 * c >= Rc) continue;
-    long h = hs[row >> 1];
-    cp_async(rs4 + e, r + (h * 2 + (row & 1)) * nrhs + r0 + 2 * c, 16);
-  }
-  for (int e = tid; e < KT * KT * 2; e += NT) {
-    int ks = e >> 1;
-    long h = hs[(ks / KT + 1) * KTH + ks % KT + 1];
-    ds[e] = omega / den[2 * h + (e & 1)];
-  }
-  cp_async_commit();
-  auto issue_rows = [&](int c) {
-    zf *dst = Ar + (c % 3) * 4 * 36;
-    for (int e = tid; e < 4 * ROWC; e += NT) {
-      int kk = e / ROWC, c16 = e - kk * ROWC;
-      int i = (c >> 2) + 4 * (kk >> 1), j = (c & 3) + 4 * (kk & 1);
-      long h = hs[(i + 1) * KTH + j + 1];
-      cp_async((char *)(dst + kk * 36) + 16 * c16, (const char *)(A + h * 36) + 16 * c16, 16);
-    }
-  };
-  issue_rows(0);
-  cp_async_commit();
-  issue_rows(1);
-  cp_async_commit();
-  // r has landed (all but the two newest groups): regroup each piece into pairs
-  cp_async_wait_group<2>();
-  __syncthreads();
-  for (int e = tid; e < KTH * KTH * 2 * RP; e += NT) {
-    float4 v = rs4[e];
-    rs4[e] = make_float4(v.x, v.z, v.y, v.w);
-  }
-  const int k = tid / RP, p = tid % RP;
-  const bool act = 2 * p < Rc;
-  auto x_at = [&](int c) -> long {
-    int i = (c >> 2) + 4 * (k >> 1), j = (c & 3) + 4 * (k & 1);
-    return (long)hs[(i + 1) * KTH + j + 1] * 2 * nrhs + r0 + 2 * p;
-  };
-  float4 xp[4][2];  // x of (q, q+1) in the global order, spin 0 and 1
-#pragma unroll
-  for (int u = 0; u < 4; ++u)
-    if (act) {
-      long xo = x_at(u);
-      xp[u][0] = *(const float4 *)(x + xo);
-      xp[u][1] = *(const float4 *)(x + xo + nrhs);
-    }
-  for (int c0 = 0; c0 < 16; c0 += 4) {
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int c = c0 + u;
-      if (c + 2 < 16) issue_rows(c + 2);
-      cp_async_commit();
-      cp_async_wait_group<2>();
-      __syncthreads();
-      int i = (c >> 2) + 4 * (k >> 1), j = (c & 3) + 4 * (k & 1);
-      if (act) {
-        int ks = i * KT + j;
-        const zf *Ah = Ar + ((c % 3) * 4 + k) * 36;
-        float2 vre[9][2], vim[9][2];
-#pragma unroll
-        for (int d = 0; d < 9; ++d) {
-          int ls = (i + d / 3) * KTH + (j + d % 3);
-#pragma unroll
-          for (int sp = 0; sp < 2; ++sp) {
-            float4 v = rs4[(ls * 2 + sp) * RP + p];
-            vre[d][sp] = make_float2(v.x, v.y);
-            vim[d][sp] = make_float2(v.z, v.w);
-          }
-        }
-        float2 svr[2], svi[2];
-#pragma unroll
-        for (int t = 0; t < 2; ++t) {
-          zf a_[9][2];
-#pragma unroll
-          for (int d = 0; d < 9; ++d) ld2<float>(Ah + d * 4 + t * 2, a_[d][0], a_[d][1]);
-          float2 n0r = bc2(0.f), n0i = bc2(0.f), n1r = bc2(0.f), n1i = bc2(0.f);
-#pragma unroll
-          for (int d = 0; d < 9; ++d) {
-            float2 &nr = (d & 1) ? n1r : n0r, &ni = (d & 1) ? n1i : n0i;
-#pragma unroll
-            for (int sp = 0; sp < 2; ++sp) {
-              float ar = sp ? -a_[d][1].re : a_[d][0].re, ai = sp ? -a_[d][1].im : a_[d][0].im;
-              // cfma(acc, a, b): re += a.re b.re - a.im b.im, im += a.re b.im + a.im b.re
-              nr = __ffma2_rn(bc2(ar), vre[d][sp], nr);
-              nr = __ffma2_rn(bc2(-ai), vim[d][sp], nr);
-              ni = __ffma2_rn(bc2(ar), vim[d][sp], ni);
-              ni = __ffma2_rn(bc2(ai), vre[d][sp], ni);
-            }
-          }
-          float sc = ds[2 * ks + t];
-          if (t) sc = -sc;
-          svr[t] = __fmul2_rn(bc2(sc), __fadd2_rn(n0r, n1r));
-          svi[t] = __fmul2_rn(bc2(sc), __fadd2_rn(n0i, n1i));
-#pragma unroll
-          for (int d = 0; d < 9; ++d)
-#pragma unroll
-            for (int sp = 0; sp < 2; ++sp) {
-              // r_sub: rv.re = fma(-sr, a.re); fma(-si, a.im); rv.im = fma(-si, a.re); fma(sr, a.im)
-              float gg = (sp == t) ? 1.f : -1.f;
-              float2 sr = __fmul2_rn(bc2(gg), svr[t]), si = __fmul2_rn(bc2(gg), svi[t]);
-              float ar = a_[d][sp].re, ai = a_[d][sp].im;
-              vre[d][sp] = __ffma2_rn(neg2(sr), bc2(ar), vre[d][sp]);
-              vre[d][sp] = __ffma2_rn(neg2(si), bc2(ai), vre[d][sp]);
-              vim[d][sp] = __ffma2_rn(neg2(si), bc2(ar), vim[d][sp]);
-              vim[d][sp] = __ffma2_rn(sr, bc2(ai), vim[d][sp]);
-            }
-        }
-        long xo = x_at(c), xn = c + 4 < 16 ? x_at(c + 4) : 0;
-#pragma unroll
-        for (int sp = 0; sp < 2; ++sp) {
-          float4 xv = xp[u][sp];
-          xv.x += svr[sp].x;
-          xv.y += svi[sp].x;
-          xv.z += svr[sp].y;
-          xv.w += svi[sp].y;
-          *(float4 *)(x + xo + sp * nrhs) = xv;
-          if (c + 4 < 16) xp[u][sp] = *(const float4 *)(x + xn + sp * nrhs);
-        }
-#pragma unroll
-        for (int d = 0; d < 9; ++d) {
-          int ls = (i + d / 3) * KTH + (j + d % 3);
-#pragma unroll
-          for (int sp = 0; sp < 2; ++sp)
-            rs4[(ls * 2 + sp) * RP + p] = make_float4(vre[d][sp].x, vre[d][sp].y, vim[d][sp].x, vim[d][sp].y);
-        }
-      }
-      __syncthreads();
-    }
-  }
-  for (int e = tid; e < KTH * KTH * 2 * RP; e += NT) {
-    int c = e % RP, row = e / RP;
-    if (2 * c >= Rc) continue;
-    long h = hs[row >> 1];
-    float4 v = rs4[e];
-    *(float4 *)(r + (h * 2 + (row & 1)) * nrhs + r0 + 2 * c) = make_float4(v.x, v.z, v.y, v.w);
   }
 }
 
@@ -1137,15 +1024,15 @@ static size_t tile_smem(int R) {
   return rows + index + (size_t)KT * KT * 2 * sizeof(T) + (size_t)KTH * KTH * 2 * R * sizeof(cx<T>);
 }
 
-template <typename T, typename S, int R, int RPT>
+template <typename T, typename S, int R, int RPT, bool PAIRED = false>
 static int launch_tile_r(const Level &L, const LevelOps &o, int tc, void *x, void *r, int nrhs, double omega,
                          cudaStream_t s) {
   size_t smem = tile_smem<T, S>(R);
   static std::atomic<unsigned long long> limit_set{0};  // devices whose limit is raised
-  WL_TRY(set_smem_limit((const void *)k_kacz_tile<T, S, R, RPT>, smem, limit_set));
+  WL_TRY(set_smem_limit((const void *)k_kacz_tile<T, S, R, RPT, PAIRED>, smem, limit_set));
   int vec = ((uintptr_t)r % 16 == 0) && (sizeof(T) == 8 || nrhs % 2 == 0);
   dim3 grid((L.N / (2 * KT)) * (L.N / (4 * KT)), (nrhs + R - 1) / R);
-  k_kacz_tile<T, S, R, RPT><<<grid, 4 * R / RPT, smem, s>>>(L.geo, tc, o.A.as<S>(), o.den.as<T>(), (cx<T> *)x,
+  k_kacz_tile<T, S, R, RPT, PAIRED><<<grid, 4 * R / RPT, smem, s>>>(L.geo, tc, o.A.as<S>(), o.den.as<T>(), (cx<T> *)x,
                                                             (cx<T> *)r, nrhs, vec, (T)omega);
   return WL_OK;
 }
@@ -1163,28 +1050,6 @@ static int tile_default_R(int nrhs, int prec) {
   return 32;
 }
 
-// packed-pair kernel (FP32 stencil only); false when it does not apply
-template <typename T, typename S>
-static bool launch_tile_pk(const Level &L, const LevelOps &o, int tc, void *x, void *r, int nrhs, double omega,
-                           cudaStream_t s, int *rc) {
-  if constexpr (std::is_same<T, float>::value && std::is_same<S, zf>::value) {
-    if (nrhs % 2 || (uintptr_t)r % 16 || (uintptr_t)x % 16) return false;
-    constexpr int R = 32;
-    size_t smem = (size_t)KTH * KTH * 2 * R * sizeof(zf) + KT * KT * 2 * sizeof(float) + 3 * 4 * 36 * sizeof(zf) +
-                  KTH * KTH * sizeof(int);
-    static std::atomic<unsigned long long> limit_set{0};
-    *rc = set_smem_limit((const void *)k_kacz_tile_pk<R>, smem, limit_set);
-    if (*rc) return true;
-    dim3 grid((L.N / (2 * KT)) * (L.N / (4 * KT)), (nrhs + R - 1) / R);
-    k_kacz_tile_pk<R><<<grid, 2 * R, smem, s>>>(L.geo, tc, o.A.as<zf>(), o.den.as<float>(), (zf *)x, (zf *)r, nrhs,
-                                                (float)omega);
-    return true;
-  } else {
-    (void)L; (void)o; (void)tc; (void)x; (void)r; (void)nrhs; (void)omega; (void)s; (void)rc;
-    return false;
-  }
-}
-
 template <typename T, typename S>
 static int launch_tile(const Level &L, const LevelOps &o, int tc, void *x, void *r, int nrhs, double omega,
                        cudaStream_t s, int param) {
@@ -1195,22 +1060,22 @@ static int launch_tile(const Level &L, const LevelOps &o, int tc, void *x, void 
     return WL_OK;
   }
   int R = param & 255, rpt = std::max(1, param >> 8);
-  if (rpt == 4) {  // packed pairs; where they do not apply, the one-per-thread kernel (same numbers)
-    int rc = WL_OK;
-    if (launch_tile_pk<T, S>(L, o, tc, x, r, nrhs, omega, s, &rc)) return rc;
-    R = 32;
-    rpt = 1;
-  }
-  if (R == 8) return launch_tile_r<T, S, 8, 1>(L, o, tc, x, r, nrhs, omega, s);
   if constexpr (sizeof(T) == 8) {  // FP64: chunks up to 16, one right-hand side per thread
+    if (R == 8) return launch_tile_r<T, S, 8, 1>(L, o, tc, x, r, nrhs, omega, s);
     return launch_tile_r<T, S, 16, 1>(L, o, tc, x, r, nrhs, omega, s);
-  } else {
+  } else {  // rpt 8: one right-hand side per thread with paired FMAs
+    bool pr = rpt == 8;
+    if (R == 8)
+      return pr ? launch_tile_r<T, S, 8, 1, true>(L, o, tc, x, r, nrhs, omega, s)
+                : launch_tile_r<T, S, 8, 1>(L, o, tc, x, r, nrhs, omega, s);
     if (R == 16) {
       if (rpt == 2) return launch_tile_r<T, S, 16, 2>(L, o, tc, x, r, nrhs, omega, s);
-      return launch_tile_r<T, S, 16, 1>(L, o, tc, x, r, nrhs, omega, s);
+      return pr ? launch_tile_r<T, S, 16, 1, true>(L, o, tc, x, r, nrhs, omega, s)
+                : launch_tile_r<T, S, 16, 1>(L, o, tc, x, r, nrhs, omega, s);
     }
     if (rpt == 2) return launch_tile_r<T, S, 32, 2>(L, o, tc, x, r, nrhs, omega, s);
-    return launch_tile_r<T, S, 32, 1>(L, o, tc, x, r, nrhs, omega, s);
+    return pr ? launch_tile_r<T, S, 32, 1, true>(L, o, tc, x, r, nrhs, omega, s)
+              : launch_tile_r<T, S, 32, 1>(L, o, tc, x, r, nrhs, omega, s);
   }
 }
 
@@ -1326,10 +1191,9 @@ int autotune_sweeps(wl_amg *a, int nrhs, int prec, cudaStream_t s) {
           if (prec == WL_FP64 && R > 16) continue;
           if (R / 2 >= nrhs && R > 8) continue;  // mostly idle lanes
           cand.push_back(KTune{nrhs, prec, 2, tile_param(R, 1), 0.f});
+          if (prec != WL_FP64) cand.push_back(KTune{nrhs, prec, 2, tile_param(R, 8), 0.f});  // paired FMAs
           if (R >= 16 && prec != WL_FP64) cand.push_back(KTune{nrhs, prec, 2, tile_param(R, 2), 0.f});
         }
-      if (prec == WL_FP32 && nrhs >= 16 && nrhs % 2 == 0)  // packed FP32 pairs
-        cand.push_back(KTune{nrhs, prec, 2, tile_param(32, 4), 0.f});
     } else {
       cand.push_back(KTune{nrhs, prec, 0, 0, 0.f});
       if (nrhs > 1)  // block-resident sweeps (thread per item, as forms 0 and 1 at nrhs > 1)
@@ -1563,8 +1427,8 @@ static int kaczmarz_entry(wl_amg *a, int level, void *x, void *r, int nrhs, int 
     bool tile = a->prm.kacz_order == 1 && wl::tile_ok(L.N);
     int R = param & 255, rpt = std::max(1, param >> 8);
     bool ok = tile ? (form == 2 &&
-                      (nrhs == 1 || ((R == 8 && rpt == 1) || ((R == 16 || R == 32) && rpt <= 2)) ||
-                       (R == 32 && rpt == 4 && prec == WL_FP32)) &&
+                      (nrhs == 1 || (R == 8 && (rpt == 1 || rpt == 8)) ||
+                       ((R == 16 || R == 32) && (rpt <= 2 || rpt == 8))) &&
                       !(prec == WL_FP64 && (R > 16 || rpt > 1)))
                    : ((form == 0) || (form == 1 && param >= 1) ||
                       (form == 3 && nrhs > 1 && wl::block_fits(L, param, prec)));
