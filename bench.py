@@ -33,7 +33,7 @@ METRIC = "Wilson-AMG solves/s at 1e-10 rel err (mixed+batched vs plain FP64); p9
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the kernels the
 # roofline reports, from ncu captures of the C4 workload at 64 right-hand sides
 # (profiles/traffic_c4_512x512_64rhs.md); None until captured for the current kernel
-TRAFFIC = {"k_mdot": 3228150000, "k_kacz_tile": 127790000}
+TRAFFIC = {"k_mdot": 3228150000, "k_kacz_tile": 127775488}
 TOL = 1e-10
 
 
@@ -58,6 +58,10 @@ def parse():
     ap.add_argument("--kernel-only", default="", choices=["", "dot", "axpy", "kacz", "tile", "dhat"],
                     help="set up the workload, then time one kernel family (wl_time_kernel) inside an NVTX "
                          "range 'cap' for profilers; prints one JSON line")
+    ap.add_argument("--sweep-forms", default="",
+                    help="pin the Kaczmarz launch form per level for the benchmark's batch width, "
+                         "'form,param;form,param;...' from level 0 (as the JSON line's sweep_forms "
+                         "reports them), so that a profiled run uses the plain run's forms")
     ap.add_argument("--study-sizes", default="128,256")
     ap.add_argument("--study-configs", type=int, default=3)
     ap.add_argument("--study-setup", default="W", choices=["W", "superV"],
@@ -238,6 +242,7 @@ def run_gb300(args, rank, world, local_rank):
             raise RuntimeError("solve did not converge: %s" % info)
         return info
 
+    pin_sweep_forms(W, amg, args.sweep_forms, nrhs, prec)
     for _ in range(args.warmup):
         step(amg, b, x, nrhs)
 
@@ -380,6 +385,7 @@ def run_gb300(args, rank, world, local_rank):
         "plain_fp64_single_rhs": {"value": round(1e3 / (sorted(p64)[1]), 3), "unit": "solves/s",
                                   "ms": sorted(p64)[1], "iters": inf64[0]["iters"]},
         "e2e": e2e, "gpu_launches": int(launches), "roofline": roof, "roofline_more": roof_more, "clocks": clk,
+        "sweep_forms": [list(W.amg_sweep_form(amg, l, nrhs, prec)) for l in range(len(w["blocks"]))],
     }
     if not args.no_serving:
         out["serving"] = run_serving(args, rank, dev, W, torch)
@@ -522,6 +528,13 @@ def run_reference(args, rank, world):
                     "d2h_bytes_per_step": 0}}
 
 
+def pin_sweep_forms(W, amg, spec, nrhs, prec):
+    """Apply --sweep-forms ('form,param;...' from level 0) before the first cycle."""
+    for level, item in enumerate(v for v in spec.split(";") if v):
+        form, param = (int(t) for t in item.split(","))
+        W.amg_pin_sweep_form(amg, level, nrhs, prec, form, param)
+
+
 def run_kernel_only(args):
     """Set up the workload's hierarchy, run one cycle of the batch width (so
     the autotuner has chosen its launch forms) and time one kernel family on
@@ -544,6 +557,7 @@ def run_kernel_only(args):
     for l, b in enumerate(w["blocks"]):
         p.block[l] = b
     amg = W.amg_setup(op, p)
+    pin_sweep_forms(W, amg, args.sweep_forms, nrhs, prec)
     f = torch.ones((nrhs, N * N), dtype=torch.complex128, device=dev)
     W.amg_cycle(amg, f, torch.zeros_like(f), nrhs, prec)  # runs the autotuner for this width
     W.wl_time_kernel(amg, kind, 0, nrhs, prec, 3)
@@ -553,7 +567,7 @@ def run_kernel_only(args):
     torch.cuda.synchronize()
     torch.cuda.nvtx.range_pop()
     print(json.dumps({"kernel_only": args.kernel_only, "workload": args.workload, "nrhs": nrhs,
-                      "avg_launch_ms": ms}))
+                      "avg_launch_ms": ms, "level0_sweep_form": list(W.amg_sweep_form(amg, 0, nrhs, prec))}))
 
 
 def run_study_rho(args):

@@ -279,11 +279,20 @@ int wl_time_kernel(wl_amg *amg, int kind, int level, int nrhs, int prec, int rep
  * right-hand sides in precision `prec`: form 0 = one launch per colour,
  * 1 = cooperative launch with *param blocks, 2 = tile-coloured kernel with
  * right-hand-side chunk (*param & 255) and right-hand sides per thread
- * (*param >> 8), 3 = one launch for all colours with a block per *param
+ * (*param >> 8: 1 or 2; 8 = one per thread with paired FP32 FMAs), 3 = one launch for all colours with a block per *param
  * right-hand sides (small levels, x and r in shared memory); *us = the autotuner's measured time of one
  * sweep in microseconds, 0 when the form was not measured (explicit
  * sweep_kernel, or no cycle of that width yet).  Errors: WL_EINVAL. */
 int amg_sweep_form(wl_amg *amg, int level, int nrhs, int prec, int *form, int *param, float *us);
+/* Pin the Kaczmarz launch form of `level` (not the coarsest) for `nrhs`
+ * right-hand sides in precision `prec` (form and param as in
+ * amg_sweep_form; the form must belong to the hierarchy's ordering on that
+ * level).  The autotuner then keeps it, so a cycle of that width captured
+ * afterwards uses it; graphs captured earlier are not changed.  For
+ * reproducible measurements (a profiler slows every launch, so the tuner's
+ * timings under it do not hold).  Ignored while sweep_kernel != 0.  Not
+ * thread-safe against solves on the same hierarchy.  Errors: WL_EINVAL. */
+int amg_pin_sweep_form(wl_amg *amg, int level, int nrhs, int prec, int form, int param);
 /* amg_kaczmarz with an explicit launch form (form and param as reported by
  * amg_sweep_form; the form must belong to the hierarchy's ordering on that
  * level), for tests and measurements: every form of one ordering computes

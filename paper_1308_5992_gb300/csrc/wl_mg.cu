@@ -1414,6 +1414,20 @@ extern "C" int amg_level_apply(wl_amg *a, int level, const void *x, void *y, int
   return WL_OK;
 }
 
+// does launch form (form, param) exist for a sweep of `level` (not the
+// coarsest) with nrhs right-hand sides in precision prec?
+static bool form_exists(const wl_amg *a, int level, int nrhs, int prec, int form, int param) {
+  const Level &L = a->lev[level];
+  bool tile = a->prm.kacz_order == 1 && wl::tile_ok(L.N);
+  int R = param & 255, rpt = std::max(1, param >> 8);
+  return tile ? (form == 2 &&
+                 (nrhs == 1 || (R == 8 && (rpt == 1 || rpt == 8)) ||
+                  ((R == 16 || R == 32) && (rpt <= 2 || rpt == 8))) &&
+                 !(prec == WL_FP64 && (R > 16 || rpt > 1)))
+              : ((form == 0) || (form == 1 && param >= 1) ||
+                 (form == 3 && nrhs > 1 && wl::block_fits(L, param, prec)));
+}
+
 // form < 0: the solver's own choice; else an explicit launch form (KTune)
 static int kaczmarz_entry(wl_amg *a, int level, void *x, void *r, int nrhs, int sweeps, int prec, int form,
                           int param, const char *who) {
@@ -1422,20 +1436,9 @@ static int kaczmarz_entry(wl_amg *a, int level, void *x, void *r, int nrhs, int 
     wl_set_error("%s: invalid argument (the coarsest level is not relaxed)", who);
     return WL_EINVAL;
   }
-  if (form >= 0) {
-    const Level &L = a->lev[level];
-    bool tile = a->prm.kacz_order == 1 && wl::tile_ok(L.N);
-    int R = param & 255, rpt = std::max(1, param >> 8);
-    bool ok = tile ? (form == 2 &&
-                      (nrhs == 1 || (R == 8 && (rpt == 1 || rpt == 8)) ||
-                       ((R == 16 || R == 32) && (rpt <= 2 || rpt == 8))) &&
-                      !(prec == WL_FP64 && (R > 16 || rpt > 1)))
-                   : ((form == 0) || (form == 1 && param >= 1) ||
-                      (form == 3 && nrhs > 1 && wl::block_fits(L, param, prec)));
-    if (!ok) {
-      wl_set_error("%s: launch form %d / %d does not exist for this level and ordering", who, form, param);
-      return WL_EINVAL;
-    }
+  if (form >= 0 && !form_exists(a, level, nrhs, prec, form, param)) {
+    wl_set_error("%s: launch form %d / %d does not exist for this level and ordering", who, form, param);
+    return WL_EINVAL;
   }
   cudaStream_t s = a->op->stream;
   int n2 = a->lev[level].n * 2;
@@ -1531,6 +1534,22 @@ extern "C" int amg_cycle(wl_amg *a, const void *f, void *x, int nrhs, int prec) 
   WL_TRY(wl::cycle_run(a, nrhs, prec, s));
   WL_TRY(wl::from_internal(a->lev[0].x.p, (zd *)x, n2, nrhs, pin, s));
   WL_CUDA(cudaStreamSynchronize(s));
+  return WL_OK;
+}
+
+extern "C" int amg_pin_sweep_form(wl_amg *a, int level, int nrhs, int prec, int form, int param) {
+  WL_TRY(check_amg(a, level, nrhs, prec, "amg_pin_sweep_form"));
+  if (level == a->L - 1 || !form_exists(a, level, nrhs, prec, form, param)) {
+    wl_set_error("amg_pin_sweep_form: launch form %d / %d does not exist for this level and ordering", form, param);
+    return WL_EINVAL;
+  }
+  std::vector<KTune> &tv = a->lev[level].tune;
+  for (KTune &k : tv)
+    if (k.nrhs == nrhs && k.prec == prec) {
+      k = KTune{nrhs, prec, form, param, 0.f};
+      return WL_OK;
+    }
+  tv.push_back(KTune{nrhs, prec, form, param, 0.f});
   return WL_OK;
 }
 

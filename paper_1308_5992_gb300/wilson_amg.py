@@ -84,6 +84,7 @@ def lib():
             "amg_fgmres": (i, [P, P, P, i, d, C.POINTER(wl_info)]),
             "amg_rho": (i, [P, P, P, i, d, i, P, P, P]),
             "amg_sweep_form": (i, [P, i, i, i, P, P, P]),
+            "amg_pin_sweep_form": (i, [P, i, i, i, i, i]),
             "amg_kaczmarz_form": (i, [P, i, P, P, i, i, i, i, i]),
             "wl_last_error": (C.c_char_p, []),
             "wl_time_kernel": (i, [P, i, i, i, i, i, C.POINTER(d)]),
@@ -290,9 +291,16 @@ def amg_rho(amg, x0, x, nrhs, tol=1e-8, maxit=100, hist=False):
     return rc, rho, it, h
 
 
+def amg_pin_sweep_form(amg, level, nrhs, prec, form, param):
+    """Pin the Kaczmarz launch form of `level` for (nrhs, prec); cycles of
+    that width captured afterwards use it (see amg_sweep_form for the codes)."""
+    return _chk(lib().amg_pin_sweep_form(amg.handle, level, nrhs, prec, form, param), "amg_pin_sweep_form")
+
+
 def amg_sweep_form(amg, level, nrhs, prec):
     """(form, param, us) of the Kaczmarz sweep on `level`: form 0 per-colour
-    launches, 1 cooperative (param blocks), 2 tile kernel (param = RHS chunk | RHS per thread << 8);
+    launches, 1 cooperative (param blocks), 2 tile kernel (param = RHS chunk | RHS per thread << 8,
+    8 meaning one RHS per thread with paired FP32 FMAs), 3 block-resident (param RHS per block);
     us = measured time of one sweep (0 if not measured)."""
     f, p, u = C.c_int(), C.c_int(), C.c_float()
     _chk(lib().amg_sweep_form(amg.handle, level, nrhs, prec, C.byref(f), C.byref(p), C.byref(u)),

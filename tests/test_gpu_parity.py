@@ -197,6 +197,24 @@ def test_sweep_forms_agree_and_autotuner(O, shared, order):
             assert np.array_equal(xa, xb) and np.array_equal(ra, rb), (sk, l)
 
 
+def test_pin_sweep_form(shared):
+    """A pinned launch form survives the autotuner (the other levels are
+    still tuned); forms of the other ordering and the coarsest level are
+    refused."""
+    w, op, h, _, path = shared("C2")
+    nrhs, prec = 4, W.WL_FP32
+    amg = W.amg_import(op, path, W.amg_params_default(zero_guess=1, kacz_order=1, precision=prec))
+    W.amg_pin_sweep_form(amg, 0, nrhs, prec, 2, 16 | 8 << 8)
+    f = T(np.stack([cgauss(185, r, h.n(0)) for r in range(nrhs)]))
+    W.amg_cycle(amg, f, torch.zeros_like(f), nrhs, prec)
+    assert W.amg_sweep_form(amg, 0, nrhs, prec)[:2] == (2, 16 | 8 << 8)
+    assert W.amg_sweep_form(amg, 1, nrhs, prec)[2] > 0
+    for level, form, param in ((0, 0, 0), (1, 2, 32), (h.L - 1, 0, 0)):
+        with pytest.raises(W.WilsonAMGError):
+            W.amg_pin_sweep_form(amg, level, nrhs, prec, form, param)
+    amg.close()
+
+
 @pytest.mark.parametrize("order,nrhs", [(0, 5), (1, 5), (1, 40)])
 def test_every_launch_form_agrees_bitwise(shared, order, nrhs):
     """Each launch form of the sweep (per-colour, cooperative with several
