@@ -382,7 +382,8 @@ __device__ __forceinline__ void r_sub_paired(cx<float> &rv, float2 m1, float2 m2
 // R = 32, so four blocks fit an SM).  vec: r rows
 // start on 16-byte boundaries (16-byte copies), else one complex per copy.
 // Every right-hand side sees the same operations in the same order for any
-// RPT, so the variants agree bit for bit.
+// R, RPT and PAIRED (paired FP32 FMAs in row_dot and r_sub_paired), so the
+// variants agree bit for bit.
 template <typename T, typename S, int R, int RPT, bool PAIRED>
 __global__ void __launch_bounds__(4 * R / RPT) k_kacz_tile(Geo g, int tc, const S *__restrict__ A,
                                                            const T *__restrict__ den, cx<T> *__restrict__ x,
