@@ -52,3 +52,21 @@ def test_reference_arm_under_torchrun_prints_once():
     assert len(lines) == 1
     _check(lines[0])
     assert lines[0]["n_gpus"] == 2
+
+
+def test_sweep_forms_option_pins_each_level():
+    """--sweep-forms 'form,param;...' pins level 0, 1, ... in order."""
+    sys.path.insert(0, ROOT)
+    import bench
+    calls = []
+
+    class FakeW:
+        @staticmethod
+        def amg_pin_sweep_form(amg, level, nrhs, prec, form, param):
+            calls.append((amg, level, nrhs, prec, form, param))
+
+    bench.pin_sweep_forms(FakeW, "h", "2,2080;2,2064;3,2", 64, 1)
+    assert calls == [("h", 0, 64, 1, 2, 2080), ("h", 1, 64, 1, 2, 2064), ("h", 2, 64, 1, 3, 2)]
+    calls.clear()
+    bench.pin_sweep_forms(FakeW, "h", "", 64, 1)
+    assert calls == []
