@@ -520,7 +520,13 @@ def run_reference(args, rank, world):
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(1e3 * sum(ts) / len(ts), 2), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "L": w["N"], "nrhs_per_step": 1},
+            "config": {"workload": "%s: %dx%d lattice, beta=%g, %d Metropolis sweeps, m=%.6f (smallest |eig| %g), "
+                                   "%d grids, blocks %s, k=%d, 1 RHS per solve (the first right-hand sides of the "
+                                   "GPU arm's batch), FP64 CPU oracle: V(2,2) 16-colour Kaczmarz cycle, FGMRES(20) "
+                                   "with classical Gram-Schmidt and one reorthogonalisation, tol %g"
+                                   % (args.workload, w["N"], w["N"], w["beta"], w["sweeps"], w["m"], w["target"],
+                                      len(w["blocks"]) + 1, w["blocks"], w["k"], TOL),
+                       "name": args.workload, "L": w["N"], "nrhs_per_step": 1},
             "cpu_baseline": {"value": round(value, 4), "unit": "solves/s", "cores": 1, "kind": "oracle",
                              "sample": "one single-RHS solve per step (oracle setup untimed: %.1f s)"
                                        % res["setup_s"]},

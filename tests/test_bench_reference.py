@@ -31,7 +31,7 @@ def _check(line):
     e2e = line["e2e"]
     assert e2e["value"] == line["value"] and e2e["unit"] == line["unit"]
     assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
-    assert line["config"]["workload"] == "C1"
+    assert line["config"]["name"] == "C1" and line["config"]["workload"].startswith("C1: 32x32 lattice")
 
 
 def test_reference_arm_single_process():
