@@ -64,7 +64,7 @@ enum {
 };
 
 enum { WL_FP64 = 0, WL_FP32 = 1, WL_FP32_BF16 = 2 }; /* cycle precision */
-enum { WL_OP_D = 0, WL_OP_DHAT = 1 };                 /* wl_apply        */
+enum { WL_OP_D = 0, WL_OP_DHAT = 1, WL_OP_Z = 2 };    /* wl_apply        */
 enum { WL_CYCLE_V = 0, WL_CYCLE_W = 1 };
 
 typedef struct {
@@ -125,7 +125,9 @@ void amg_params_default(amg_params *p);
 int wilson_create(const void *gauge, int L, double m, void *cuda_stream, wl_op **out);
 void wl_destroy(wl_op *op);
 
-/* y = D x (which = WL_OP_D; x, y full fields [nrhs][L][L][2]) or
+/* y = D x (which = WL_OP_D; x, y full fields [nrhs][L][L][2]), y = Z x
+ * with Z = Gamma5 D (which = WL_OP_Z, Thm. 3.1; Gamma5 = +1 on spin 0, -1 on
+ * spin 1, so Z is Hermitian; same layout) or
  * y = Dhat x (which = WL_OP_DHAT, Eq. 3.2 with the 1/c scaling of Sec. 3.2;
  * x, y level-0 vectors [nrhs][L^2/2][2]), computed matrix-free from the
  * links in precision prec (WL_FP64 or WL_FP32; FP32 rounds x and the links

@@ -118,6 +118,14 @@ def wilson_apply(N, U, m, psi):
     return out
 
 
+def z_apply(N, U, m, psi):
+    """Z psi = Gamma5 D psi (Thm. 3.1), Gamma5 = diag(1, -1) on each site's
+    two spins; psi and the result in the full-field layout [N][N][2]."""
+    out = wilson_apply(N, U, m, psi).reshape(N, N, 2)
+    out[..., 1] *= -1
+    return out.reshape(np.shape(psi))
+
+
 def dhat_csr(N, U, m):
     import scipy.sparse as sp
     U = _c(U)

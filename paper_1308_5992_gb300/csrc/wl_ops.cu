@@ -112,10 +112,12 @@ __global__ void k_hop(Geo g, const cx<Tc> *__restrict__ V, int par_out,
   out[o + nrhs] = ccast<Tout>(o1);
 }
 
-// D psi on the full lattice, ABI layout [nrhs][N][N][2]: D = c (I - K)
+// D psi on the full lattice, ABI layout [nrhs][N][N][2]: D = c (I - K);
+// g5 = 1 gives Z psi = Gamma5 D psi (Thm. 3.1: the spin-1 row negated, an
+// exact sign flip of the D result)
 template <typename Tc>
 __global__ void k_wilson_full(int N, double c, const cx<Tc> *__restrict__ V,
-                              const zd *__restrict__ in, zd *__restrict__ out, int nrhs) {
+                              const zd *__restrict__ in, zd *__restrict__ out, int nrhs, int g5) {
   long tid = (long)blockIdx.x * blockDim.x + threadIdx.x;
   long nz = (long)N * N;
   if (tid >= nz * nrhs) return;
@@ -137,7 +139,7 @@ __global__ void k_wilson_full(int N, double c, const cx<Tc> *__restrict__ V,
   cx<Tc> p0 = ccast<Tc>(in[o]), p1 = ccast<Tc>(in[o + 1]);
   Tc cc = (Tc)c;
   out[o] = ccast<double>(cc * (p0 - o0));
-  out[o + 1] = ccast<double>(cc * (p1 - o1));
+  out[o + 1] = ccast<double>((g5 ? -cc : cc) * (p1 - o1));
 }
 
 // bhat_e = b_e/c + K_eo (b_o/c); b in ABI layout [nrhs][N][N][2], bhat
@@ -531,7 +533,7 @@ int enter(wl_op *op) {
 
 extern "C" int wl_apply(wl_op *op, int which, const void *x, void *y, int nrhs, int prec) {
   if (!op || !x || !y || nrhs < 1 || (prec != WL_FP64 && prec != WL_FP32) ||
-      (which != WL_OP_D && which != WL_OP_DHAT)) {
+      (which != WL_OP_D && which != WL_OP_DHAT && which != WL_OP_Z)) {
     wl_set_error("wl_apply: invalid argument");
     return WL_EINVAL;
   }
@@ -539,12 +541,15 @@ extern "C" int wl_apply(wl_op *op, int which, const void *x, void *y, int nrhs, 
   cudaStream_t s = op->stream;
   Geo g = op->geo;
   int N = op->N;
-  if (which == WL_OP_D) {
+  if (which == WL_OP_D || which == WL_OP_Z) {
     long tot = (long)N * N * nrhs;
+    int g5 = which == WL_OP_Z;
     if (prec == WL_FP64)
-      k_wilson_full<double><<<WL_GRID(tot, 256), 256, 0, s>>>(N, op->c, op->Uf64.as<zd>(), (const zd *)x, (zd *)y, nrhs);
+      k_wilson_full<double><<<WL_GRID(tot, 256), 256, 0, s>>>(N, op->c, op->Uf64.as<zd>(), (const zd *)x, (zd *)y,
+                                                              nrhs, g5);
     else
-      k_wilson_full<float><<<WL_GRID(tot, 256), 256, 0, s>>>(N, op->c, op->Uf32.as<zf>(), (const zd *)x, (zd *)y, nrhs);
+      k_wilson_full<float><<<WL_GRID(tot, 256), 256, 0, s>>>(N, op->c, op->Uf32.as<zf>(), (const zd *)x, (zd *)y,
+                                                             nrhs, g5);
     WL_CUDA(cudaGetLastError());
     return WL_OK;
   }

@@ -15,7 +15,7 @@ from . import _build
 WL_OK, WL_NOT_CONVERGED = 0, 1
 WL_EINVAL, WL_OOM, WL_ECUDA, WL_TIMEOUT, WL_NAN, WL_BAD_HIERARCHY = -1, -2, -3, -4, -5, -6
 WL_FP64, WL_FP32, WL_FP32_BF16 = 0, 1, 2
-WL_OP_D, WL_OP_DHAT = 0, 1
+WL_OP_D, WL_OP_DHAT, WL_OP_Z = 0, 1, 2
 WL_CYCLE_V, WL_CYCLE_W = 0, 1
 (WL_K_DHAT, WL_K_KACZ, WL_K_STENCIL, WL_K_RESTRICT, WL_K_PROLONG, WL_K_COARSEST, WL_K_GS_DOT,
  WL_K_GS_AXPY, WL_K_KACZ_TILE) = range(9)

@@ -60,3 +60,18 @@ def test_float_widening_formula():
             d = ((u.astype(np.uint64) & np.uint64(0x80000000)) << np.uint64(32)) | \
                 (np.uint64(e + 896) << np.uint64(52)) | ((u.astype(np.uint64) & np.uint64(0x7FFFFF)) << np.uint64(29))
             assert np.array_equal(d.view(np.float64), f.astype(np.float64))
+
+
+def test_binding_constants_match_header_enums():
+    """Every enumerator of include/wilson_amg.h has the same value in the binding."""
+    from paper_1308_5992_gb300 import wilson_amg as W
+    txt = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "wilson_amg.h")).read(), flags=re.S)
+    pairs = []
+    for body in re.findall(r"enum\s*\{([^}]*)\}", txt):
+        for item in body.split(","):
+            m = re.match(r"\s*(WL_\w+)\s*=\s*(-?\d+)\s*$", item)
+            if m:
+                pairs.append((m.group(1), int(m.group(2))))
+    assert len(pairs) >= 15
+    for name, value in pairs:
+        assert getattr(W, name) == value, name

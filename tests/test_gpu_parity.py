@@ -76,10 +76,17 @@ def test_dhat_and_d_apply(O, ops, name, nrhs):
         assert rel(H(y), ref) <= tol, (prec, rel(H(y), ref))
     psi = np.stack([cgauss(20 + r, 1, 2 * N * N).reshape(N, N, 2) for r in range(nrhs)])
     refD = np.stack([O.wilson_apply(N, U, m, psi[r].reshape(-1)).reshape(N, N, 2) for r in range(nrhs)])
+    refZ = np.stack([O.z_apply(N, U, m, psi[r]) for r in range(nrhs)])
     for prec, tol in ((W.WL_FP64, 1e-14), (W.WL_FP32, 1e-6)):
         y = torch.zeros_like(T(psi))
         W.wl_apply(op, W.WL_OP_D, T(psi), y, nrhs, prec)
         assert rel(H(y), refD) <= tol
+        z = torch.zeros_like(T(psi))
+        W.wl_apply(op, W.WL_OP_Z, T(psi), z, nrhs, prec)  # Z = Gamma5 D (Thm. 3.1)
+        assert rel(H(z), refZ) <= tol
+        g5y = H(y)
+        g5y[..., 1] *= -1
+        assert np.array_equal(H(z), g5y)  # an exact sign flip of the D result
 
 
 @pytest.mark.parametrize("name,nrhs", [("T32", 1), ("T64", 3)])

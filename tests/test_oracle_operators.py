@@ -35,6 +35,23 @@ def test_gamma5_hermiticity(O, N, kind):
     assert np.abs(Ge @ Dh - Dh.conj().T @ Ge).max() <= 1e-14 * np.abs(Dh).max()
 
 
+@pytest.mark.parametrize("N,kind", [(4, "rand"), (8, "metro")])
+def test_z_is_hermitian(O, N, kind):
+    """Thm. 3.1: Z = Gamma5 D is Hermitian (a consequence of the
+    gamma5-hermiticity of D).  Z is assembled column by column from z_apply,
+    so a wrong spin sign or layout in z_apply breaks the symmetry."""
+    U = _rand_gauge(N, 2) if kind == "rand" else metropolis_u1(N, 3.0, 30, 5)
+    m = 0.11
+    n = 2 * N * N
+    Z = np.empty((n, n), complex)
+    for j in range(n):
+        e = np.zeros(n, complex)
+        e[j] = 1.0
+        Z[:, j] = O.z_apply(N, U, m, e.reshape(N, N, 2)).reshape(-1)
+    assert np.abs(Z - Z.conj().T).max() <= 1e-14 * np.abs(Z).max()
+    assert np.abs(np.diag(Z)[1::2] + (m + 2)).max() <= 1e-14  # Gamma5 flips the spin-1 diagonal
+
+
 def test_block_form(O):
     """Eq. 2.2: in spin-permuted order D = 1/2 [[A, B], [-B^H, A]] with the
     gauge Laplacian A and the gauge gradient B of Sec. 2.  Readings: the
