@@ -75,3 +75,17 @@ def test_binding_constants_match_header_enums():
     assert len(pairs) >= 15
     for name, value in pairs:
         assert getattr(W, name) == value, name
+
+
+def test_no_host_fallback_without_a_device():
+    """Without a CUDA device the library reports WL_ECUDA instead of
+    computing anything on the host (there is no CPU path)."""
+    torch = __import__("pytest").importorskip("torch")
+    if torch.cuda.is_available():
+        __import__("pytest").skip("a device is present")
+    import numpy as np
+    from paper_1308_5992_gb300 import wilson_amg as W
+    U = np.ones((2, 32, 32), np.complex128)
+    out = ctypes.c_void_p()
+    rc = W.lib().wilson_create(ctypes.c_void_p(U.ctypes.data), 32, 0.1, None, ctypes.byref(out))
+    assert rc == W.WL_ECUDA and not out.value
