@@ -31,10 +31,10 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Wilson-AMG solves/s at 1e-10 rel err (mixed+batched vs plain FP64); p99 ms"
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the kernels the
-# roofline reports, from ncu captures of the C4 workload at 64 right-hand sides
-# (profiles/traffic_c4_512x512_64rhs.md); None until captured for the current kernel
+# roofline reports, from one ncu capture of the C4 workload at 64 right-hand sides
+# (ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum on bench.py --kernel-only);
+# None until captured for the current kernel
 TRAFFIC = {"k_mdot": 3228150000, "k_kacz_tile": 127775488}
-TOL = 1e-10
 
 
 def parse():
@@ -47,9 +47,13 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=8.0)
-    ap.add_argument("--serve-configs", type=int, default=4,
+    ap.add_argument("--serve-configs", type=int, default=16,
                     help="resident configurations S00.. of the serving mix (16 = all five lattice sizes)")
-    ap.add_argument("--serve-hbm-gb", type=float, default=64.0, help="device-memory budget of the server")
+    ap.add_argument("--serve-hbm-gb", type=float, default=160.0, help="device-memory budget of the server")
+    ap.add_argument("--tol", type=float, default=1e-10,
+                    help="relative residual at which a right-hand side counts as solved")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0,
+                    help="timed CPU work per oracle variant (at least one solve each)")
     ap.add_argument("--nrhs", type=int, default=0, help="override the workload's RHS per step")
     ap.add_argument("--kacz-order", type=int, default=-1, help="override the Kaczmarz ordering (0 or 1)")
     ap.add_argument("--study", default="", choices=["", "rho"],
@@ -70,38 +74,89 @@ def parse():
 
 
 # ----------------------------------------------------------- oracle (CPU)
-def _oracle_solves(name, nsolves, out_q):
-    """Runs in a spawned process: the oracle's own setup (untimed), then
-    `nsolves` timed single-RHS solves of the workload."""
+def _host_info():
+    info = {"nproc": os.cpu_count()}
     try:
-        import numpy as np
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            k, _, v = ln.partition(":")
+            if k.strip() in ("Model name", "Architecture", "Socket(s)", "Core(s) per socket"):
+                info[k.strip()] = v.strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return info
+
+
+def _oracle_leg(variant, name, hier, cyc, tol, seconds, nmax, ref_rhs, out_q):
+    """Runs in a spawned process.  The oracle build `variant` ("plain": one
+    thread; "omp": every host core) loads the GPU's exported hierarchy (so
+    both arms solve on the same operators) and times single right-hand-side
+    solves of the workload's first right-hand sides with the cycle `cyc`
+    until `seconds` of solve time are spent (at least one, at most nmax).
+    With ref_rhs it then solves that right-hand side to 1e-13 (untimed) as
+    the reference solution the GPU's error is measured against."""
+    try:
         from oracle import oracle as O
+        from oracle.hierfile import read, gauge_hash
         from wl_inputs import workload, rhs_batch
+        O.use_variant(variant)
         w = workload(name)
-        p = O.setup_params(w["blocks"], k_r=w["k"], k_e=w["k"], seed=w["seed"])
+        d = read(hier)
+        if d["gauge_hash"] != gauge_hash(w["U"]):
+            raise ValueError("hierarchy file belongs to another gauge field")
         t0 = time.time()
-        h = O.Hierarchy.setup(w["N"], w["U"], w["m"], p)
-        setup_s = time.time() - t0
-        times, iters, sols = [], [], []
-        for i in range(nsolves):
+        h = O.Hierarchy.from_arrays(w["N"], w["U"], d["m"], d["Nl"], d["Bl"], d["Pw"], d["As"])
+        load_s = time.time() - t0
+        times, iters = [], []
+        for i in range(nmax):
             b = rhs_batch(w["N"], 1, 100, first=i)[0]
             t0 = time.perf_counter()
-            psi, info = h.solve(b, tol=TOL)
+            _, info = h.solve(b, tol=tol, **cyc)
             times.append(time.perf_counter() - t0)
             iters.append(info["iters"])
-            if i == 0:
-                sols.append(psi)
-        out_q.put(dict(ok=True, setup_s=setup_s, times=times, iters=iters, psi0=sols[0]))
+            if info["status"] != 0:
+                raise RuntimeError("oracle solve did not converge: %s" % info)
+            if sum(times) >= seconds:
+                break
+        res = dict(ok=True, variant=variant, threads=O.threads(), load_s=load_s, times=times, iters=iters)
+        if ref_rhs is not None:
+            b = rhs_batch(w["N"], 1, 100, first=ref_rhs)[0]
+            ref, info = h.solve(b, tol=1e-13, **cyc)
+            res.update(ref=ref, ref_relres=info["relres"])
+        out_q.put(res)
     except Exception as e:  # reported, never silently replaced
-        out_q.put(dict(ok=False, error=repr(e)))
+        out_q.put(dict(ok=False, variant=variant, error=repr(e)))
 
 
-def start_oracle(name, nsolves):
+def _child_result(target, args, timeout):
+    """Run target(*args, queue) in a spawned process and return what it put
+    on the queue; a child that dies without a result is reported, not waited
+    for."""
+    import queue as _queue
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
-    p = ctx.Process(target=_oracle_solves, args=(name, nsolves, q), daemon=True)
+    p = ctx.Process(target=target, args=args + (q,), daemon=True)
     p.start()
-    return p, q
+    t_end = time.time() + timeout
+    res = None
+    while res is None and time.time() < t_end:
+        try:
+            res = q.get(timeout=2)
+        except _queue.Empty:
+            if not p.is_alive():
+                try:
+                    res = q.get(timeout=1)
+                except _queue.Empty:
+                    res = dict(ok=False, error="oracle process exited with code %s" % p.exitcode)
+    if res is None:
+        p.terminate()
+        res = dict(ok=False, error="oracle process timed out after %g s" % timeout)
+    p.join(timeout=60)
+    return res
+
+
+def run_oracle_leg(*args, timeout=1800):
+    return _child_result(_oracle_leg, args, timeout)
 
 
 # ------------------------------------------------------------- clocks
@@ -201,11 +256,7 @@ def run_gb300(args, rank, world, local_rank):
     N, nrhs = w["N"], max(1, args.nrhs or w["nrhs"])
     prec = {"fp64": W.WL_FP64, "fp32": W.WL_FP32, "bf16": W.WL_FP32_BF16}[w["precision"]]
 
-    # CPU baseline leg: the oracle, started before the first GPU call
-    oracle_proc = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        oracle_proc = start_oracle(args.workload, 3)
-
+    TOL = args.tol
     op = W.wilson_create(torch.from_numpy(w["U"]).to(dev), N, w["m"])
 
     def params(precision, plain=False):
@@ -229,7 +280,6 @@ def run_gb300(args, rank, world, local_rank):
     hier = os.path.join("/tmp", "wl_bench_%d_%d.wlh" % (os.getpid(), rank))
     W.amg_export(amg, hier)
     amg64 = W.amg_import(op, hier, params(W.WL_FP64, plain=True))  # same hierarchy, plain FP64 method
-    os.remove(hier)
 
     b_host = torch.from_numpy(rhs_batch(N, nrhs, 100 + 1000 * rank)).pin_memory()
     b = b_host.to(dev)
@@ -308,10 +358,10 @@ def run_gb300(args, rank, world, local_rank):
         torch.cuda.synchronize()
         p64.append(e0.elapsed_time(e1))
 
-    # Roofline.  The launch list of this workload (profiles/launches_c4_512x512_64rhs.md)
-    # ranks the tile-coloured Kaczmarz kernel first (44% of kernel time over levels 0 and
-    # 1), then the FP64 Gram-Schmidt update k_maxpy and the multi-dots k_mdot; with the
-    # 16-colour ordering k_mdot and the colour passes lead.
+    # Roofline.  The ncu launch list of this workload ranks the tile-coloured Kaczmarz
+    # kernel first (28 % of kernel time on level 0, 37 % over levels 0 and 1), then the
+    # FP64 Gram-Schmidt update k_maxpy and the multi-dots k_mdot; with the 16-colour
+    # ordering k_mdot and the colour passes lead.
     n0 = N * N // 2
     E = 2 * n0 * nrhs
     hbm, src = peaks()
@@ -387,27 +437,53 @@ def run_gb300(args, rank, world, local_rank):
         "e2e": e2e, "gpu_launches": int(launches), "roofline": roof, "roofline_more": roof_more, "clocks": clk,
         "sweep_forms": [list(W.amg_sweep_form(amg, l, nrhs, prec)) for l in range(len(w["blocks"]))],
     }
+    # CPU baseline: the oracle on the host cores, after the GPU's timed region (nothing else
+    # runs meanwhile), on the GPU's exported hierarchy; two builds: one thread with the
+    # lexicographic Kaczmarz ordering, and every core with the 16-colour ordering.  The
+    # all-cores run also solves the batch's first right-hand side to 1e-13, the reference
+    # the GPU solution's error is measured against.
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        from oracle import oracle as O
+        cyc = dict(m=w["fgmres_m"], nu1=w["nu"], nu2=w["nu"], gamma=2 if w["cycle"] == "W" else 1,
+                   gs_passes=w["gs_passes"])
+        legs = [run_oracle_leg("plain", args.workload, hier, dict(cyc, order=O.ORDER_LEX), TOL, args.cpu_seconds,
+                               3, None),
+                run_oracle_leg("omp", args.workload, hier, dict(cyc, order=O.ORDER_COLOUR), TOL, args.cpu_seconds,
+                               8, 0)]
+        variants = []
+        for res in legs:
+            if not res.get("ok"):
+                variants.append({"variant": res.get("variant"), "error": res.get("error")})
+                continue
+            ts = res["times"]
+            variants.append({"variant": res["variant"], "value": round(len(ts) / sum(ts), 4), "unit": "solves/s",
+                             "cores": res["threads"],
+                             "order": "lexicographic" if res["variant"] == "plain" else "16-colour",
+                             "solves": len(ts), "seconds": round(sum(ts), 2), "iters": res["iters"]})
+        best = max((v for v in variants if "value" in v), key=lambda v: v["value"], default=None)
+        out["cpu_baseline"] = {
+            "value": best["value"] if best else None, "unit": "solves/s", "cores": best["cores"] if best else None,
+            "kind": "oracle",
+            "sample": "single-RHS solves of the workload's first right-hand sides on the GPU's exported "
+                      "hierarchy, %s(%d,%d) cycle, FGMRES(%d) with %d Gram-Schmidt pass(es), tol %g, about %g s "
+                      "of solve time per build, run after the GPU's timed region"
+                      % (w["cycle"], w["nu"], w["nu"], w["fgmres_m"], w["gs_passes"], TOL, args.cpu_seconds),
+            "variants": variants, "host": _host_info()}
+        omp = legs[1]
+        if omp.get("ok"):
+            one = torch.zeros_like(b[:1])
+            step(amg, b[:1].contiguous(), one, 1)
+            got = one[0].cpu().numpy()
+            ref = omp["ref"]
+            err = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+            out["rel_err_vs_exact"] = {
+                "value": err, "max_elementwise": float(np.abs(got - ref).max() / np.abs(ref).max()),
+                "tol": TOL, "reference": "oracle FP64 solve of the batch's first right-hand side to a relative "
+                                         "residual of %.1e on the same hierarchy" % omp["ref_relres"],
+                "meets_1e-10": err <= 1e-10}
+    os.remove(hier)
     if not args.no_serving:
         out["serving"] = run_serving(args, rank, dev, W, torch)
-    if oracle_proc is not None:
-        proc, q = oracle_proc
-        res = q.get(timeout=1800)
-        proc.join(timeout=60)
-        if res.get("ok"):
-            ts = res["times"]
-            out["cpu_baseline"] = {"value": round(len(ts) / sum(ts), 4), "unit": "solves/s", "cores": 1,
-                                   "kind": "oracle",
-                                   "sample": "%d single-RHS solves of the same workload (the oracle's own setup, "
-                                             "untimed: %.1f s); iterations %s" % (len(ts), res["setup_s"],
-                                                                                 res["iters"])}
-            ref = res["psi0"]
-            one = torch.zeros_like(b[:1])
-            bref = torch.from_numpy(rhs_batch(N, 1, 100)).to(dev)
-            step(amg, bref, one, 1)
-            got = one[0].cpu().numpy()
-            out["rel_err_vs_oracle"] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
-        else:
-            out["cpu_baseline"] = {"value": None, "error": res.get("error")}
     return out
 
 
@@ -462,7 +538,7 @@ def run_serving(args, rank, dev, W, torch):
         b = pools[c][:nr].contiguous()
         x = torch.zeros_like(b)
         torch.cuda.synchronize()
-        return W.srv_submit(srv, cid, b, x, nr, TOL), nr, x
+        return W.srv_submit(srv, cid, b, x, nr, args.tol), nr, x
 
     # capacity: a closed-loop burst
     burst = requests(16, 1)
@@ -503,33 +579,60 @@ def run_serving(args, rank, dev, W, torch):
             "hbm_budget_gb": args.serve_hbm_gb, "hbm_reserved_gb": round(reserved / (1 << 30), 2)}
 
 
+def _reference_leg(name, nsolves, tol, out_q):
+    """Runs in a spawned process: the all-cores oracle build, its own setup of
+    the workload (untimed), then `nsolves` timed single right-hand-side
+    solves with the GPU arm's cycle (V(nu,nu), FGMRES(m), Gram-Schmidt passes)
+    and the 16-colour Kaczmarz ordering."""
+    try:
+        from oracle import oracle as O
+        from wl_inputs import workload, rhs_batch
+        O.use_variant("omp")
+        w = workload(name)
+        p = O.setup_params(w["blocks"], k_r=w["k"], k_e=w["k"], seed=w["seed"])
+        t0 = time.time()
+        h = O.Hierarchy.setup(w["N"], w["U"], w["m"], p)
+        setup_s = time.time() - t0
+        times, iters = [], []
+        for i in range(nsolves):
+            b = rhs_batch(w["N"], 1, 100, first=i)[0]
+            t0 = time.perf_counter()
+            _, info = h.solve(b, tol=tol, m=w["fgmres_m"], nu1=w["nu"], nu2=w["nu"],
+                              gamma=2 if w["cycle"] == "W" else 1, order=O.ORDER_COLOUR, gs_passes=w["gs_passes"])
+            times.append(time.perf_counter() - t0)
+            iters.append(info["iters"])
+        out_q.put(dict(ok=True, setup_s=setup_s, times=times, iters=iters, threads=O.threads()))
+    except Exception as e:  # reported, never silently replaced
+        out_q.put(dict(ok=False, error=repr(e)))
+
+
 def run_reference(args, rank, world):
     """The oracle as it stands, on the host cores, same metric and workload."""
     if rank != 0:
         return None
     from wl_inputs import workload
     w = workload(args.workload, with_gauge=False)
-    proc, q = start_oracle(args.workload, args.warmup + args.steps)
-    res = q.get(timeout=3600)
-    proc.join(timeout=60)
+    res = _child_result(_reference_leg, (args.workload, args.warmup + args.steps, args.tol), 3600)
     if not res.get("ok"):
         return {"impl": "reference", "unavailable": "oracle failed: %s" % res.get("error")}
     ts = res["times"][args.warmup:]
     value = len(ts) / sum(ts)
+    sample = ("one single-RHS solve per step, %d threads (oracle setup untimed: %.1f s); iterations %s"
+              % (res["threads"], res["setup_s"], res["iters"][args.warmup:]))
     return {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "solves/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(1e3 * sum(ts) / len(ts), 2), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "%s: %dx%d lattice, beta=%g, %d Metropolis sweeps, m=%.6f (smallest |eig| %g), "
                                    "%d grids, blocks %s, k=%d, 1 RHS per solve (the first right-hand sides of the "
-                                   "GPU arm's batch), FP64 CPU oracle: V(2,2) 16-colour Kaczmarz cycle, FGMRES(20) "
-                                   "with classical Gram-Schmidt and one reorthogonalisation, tol %g"
+                                   "GPU arm's batch), FP64 CPU oracle on every host core: %s(%d,%d) 16-colour "
+                                   "Kaczmarz cycle, FGMRES(%d) with %d Gram-Schmidt pass(es), tol %g"
                                    % (args.workload, w["N"], w["N"], w["beta"], w["sweeps"], w["m"], w["target"],
-                                      len(w["blocks"]) + 1, w["blocks"], w["k"], TOL),
+                                      len(w["blocks"]) + 1, w["blocks"], w["k"], w["cycle"], w["nu"], w["nu"],
+                                      w["fgmres_m"], w["gs_passes"], args.tol),
                        "name": args.workload, "L": w["N"], "nrhs_per_step": 1},
-            "cpu_baseline": {"value": round(value, 4), "unit": "solves/s", "cores": 1, "kind": "oracle",
-                             "sample": "one single-RHS solve per step (oracle setup untimed: %.1f s)"
-                                       % res["setup_s"]},
+            "cpu_baseline": {"value": round(value, 4), "unit": "solves/s", "cores": res["threads"], "kind": "oracle",
+                             "sample": sample},
             "e2e": {"value": round(value, 4), "unit": "solves/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
 

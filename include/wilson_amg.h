@@ -58,7 +58,9 @@ enum {
   WL_EINVAL = -1,
   WL_OOM = -2,
   WL_ECUDA = -3,
-  WL_TIMEOUT = -4,
+  WL_TIMEOUT = -4,       /* reserved: no kernel of this library waits on a flag (the one
+                            grid-wide barrier is a cooperative launch's), so no call
+                            returns it */
   WL_NAN = -5,
   WL_BAD_HIERARCHY = -6
 };
@@ -107,7 +109,7 @@ typedef struct {
 } amg_params;
 
 typedef struct {
-  int status;             /* WL_OK or WL_NOT_CONVERGED for this right-hand side     */
+  int status;             /* WL_OK, WL_NOT_CONVERGED or WL_NAN for this right-hand side */
   int restarts;           /* FGMRES cycles run                                       */
   int iters;              /* FGMRES iterations (preconditioner applications)         */
   double true_relres;     /* ||bhat - Dhat x|| / ||bhat|| recomputed in FP64         */
@@ -150,9 +152,15 @@ int amg_setup(wl_op *op, const amg_params *params, wl_amg **out);
 /* Solve D psi = b for nrhs right-hand sides (b, x full fields
  * [nrhs][L][L][2], device).  x is the initial guess unless
  * params.zero_guess.  Stops each right-hand side when its FP64 relative
- * residual of the reduced system is <= tol.  info: host array [nrhs].
- * Returns WL_OK if every right-hand side converged, WL_NOT_CONVERGED
- * otherwise, or an error (WL_NAN if a residual became non-finite). */
+ * residual of the reduced system is <= tol, or after max_restarts FGMRES
+ * cycles (x then holds the last iterate, whose true residual info reports).
+ * info: host array [nrhs].  A right-hand side whose residual becomes
+ * non-finite (a NaN or Inf in its b or initial guess, say) is retired with
+ * info[r].status = WL_NAN and its x is not meaningful; the other right-hand
+ * sides of the batch are solved as usual (no kernel mixes right-hand sides).
+ * Returns WL_NAN if some right-hand side was retired that way, else
+ * WL_NOT_CONVERGED if some missed tol, else WL_OK; other negative values
+ * are errors of the whole call. */
 int amg_solve(wl_amg *amg, const void *b, void *x, int nrhs, double tol, wl_info *info);
 
 /* Hierarchy file: header "WLAMGH01", version, levels, N_l, B_l, m, gauge
@@ -186,7 +194,8 @@ int amg_coarsest(wl_amg *amg, const void *f, void *x, int nrhs);
  * configured V or W cycle, nu_pre / nu_post sweeps). */
 int amg_cycle(wl_amg *amg, const void *f, void *x, int nrhs, int prec);
 /* FGMRES on Dhat x = bhat (level-0 vectors, x = initial guess); info host
- * array [nrhs]. */
+ * array [nrhs].  Return values and per-right-hand-side status as for
+ * amg_solve. */
 int amg_fgmres(wl_amg *amg, const void *bhat, void *x, int nrhs, double tol, wl_info *info);
 /* Sec. 4's convergence estimate of the stand-alone solver: the configured
  * cycle (V or W, nu_pre / nu_post, precision) used as the stationary
@@ -217,11 +226,15 @@ int amg_rho(wl_amg *amg, const void *x0, void *x, int nrhs, double tol, int maxi
  * Limit: L^2 * nrhs <= 2^20 (for example L = 512 with nrhs <= 4, L = 1024
  * with nrhs = 1); larger sizes return WL_EINVAL with a message naming the
  * limit.  The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) and caches it; make that first call before any
- * stream capture.  All calls share the array, which keeps the last call's
- * contents (every element read is first overwritten, so nothing needs
- * clearing); calls whose work overlaps on the GPU race on it.  Synchronous:
- * returns after y is written. */
+ * (cudaGetSymbolAddress) and caches it for the life of the process, so the
+ * library must not be used across a cudaDeviceReset (or any teardown of the
+ * device's primary context): the cached address would then be stale.  All
+ * calls share the array, which keeps the last call's contents (every
+ * element read is first overwritten, so nothing needs clearing); calls whose
+ * work overlaps on the GPU race on it.  Synchronous: the call waits for its
+ * kernels (a stream synchronisation) and returns after y is written, so it
+ * must not be called while the caller's stream, or the operator's, is being
+ * captured into a CUDA graph. */
 int wl_dhat_apply_noalloc(wl_op *op, const void *x, void *y, int nrhs);
 
 /* ---- serving: continuous batching over resident hierarchies ----
@@ -254,6 +267,10 @@ int srv_add(wl_server *srv, wl_amg *amg, int *cfg_id);
 int srv_info(wl_server *srv, int cfg, int *slots, unsigned long long *bytes);
 int srv_start(wl_server *srv);
 int srv_submit(wl_server *srv, int cfg, const void *b, void *x, int nrhs, double tol, long long *req_id);
+/* *done = 1 once every right-hand side of the request is retired; returns
+ * the request's status (WL_OK, WL_NOT_CONVERGED, or WL_NAN when one of its
+ * right-hand sides had a non-finite residual: that one alone is retired,
+ * other requests and the server go on). */
 int srv_poll(wl_server *srv, long long req_id, int *done, wl_info *info /* host [nrhs] */, double *latency_ms);
 int srv_drain(wl_server *srv);
 void srv_destroy(wl_server *srv);

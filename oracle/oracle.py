@@ -18,29 +18,52 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "wilson_oracle.c")
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
+# the same source built with -fopenmp: timed as the all-cores CPU baseline only
+_LIB_OMP_PATH = os.path.join(_HERE, "liboracle_omp.so")
 _lib = None
+_variant = "plain"
 
 ORDER_LEX = 0
 ORDER_COLOUR = 1
 ORDER_TILE = 2
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (plain C11, no architecture flags)."""
-    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < max(
+def build(force: bool = False, omp: bool = False) -> str:
+    """Compile the oracle with gcc (plain C11, no architecture flags); with
+    omp, the all-cores variant of the same source (-fopenmp)."""
+    path = _LIB_OMP_PATH if omp else _LIB_PATH
+    if force or not os.path.exists(path) or os.path.getmtime(path) < max(
             os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "wilson_oracle.h"))):
-        tmp = _LIB_PATH + ".%d.tmp" % os.getpid()
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-fPIC", "-shared",
+        tmp = path + ".%d.tmp" % os.getpid()
+        flags = ["-fopenmp"] if omp else []
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-fPIC", "-shared", *flags,
                                "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _LIB_PATH)
-    return _LIB_PATH
+        os.replace(tmp, path)
+    return path
+
+
+def use_variant(name: str) -> None:
+    """Select, before the first call, which build this process loads:
+    "plain" (the oracle the tests check against) or "omp" (the same source
+    built with OpenMP, for the timed all-cores CPU baseline)."""
+    global _variant
+    if _lib is not None and name != _variant:
+        raise RuntimeError("oracle library already loaded as %s" % _variant)
+    if name not in ("plain", "omp"):
+        raise ValueError(name)
+    _variant = name
+
+
+def threads() -> int:
+    """Host threads the loaded build runs its loops on."""
+    return lib().or_threads()
 
 
 def lib():
     global _lib
     if _lib is None:
-        build()
-        L = C.CDLL(_LIB_PATH)
+        path = build(omp=_variant == "omp")
+        L = C.CDLL(path)
         P = C.c_void_p
         i, d = C.c_int, C.c_double
         sig = {
@@ -65,8 +88,9 @@ def lib():
             "or_prolong": (i, [P, i, P, P]),
             "or_coarsest_solve": (i, [P, P, P]),
             "or_cycle": (i, [P, i, P, P, i, i, i, i]),
-            "or_fgmres": (i, [P, P, P, d, i, i, i, i, i, i, P, P, P]),
-            "or_solve": (i, [i, P, d, P, P, P, d, i, i, i, i, i, i, P, P]),
+            "or_fgmres": (i, [P, P, P, d, i, i, i, i, i, i, i, P, P, P]),
+            "or_solve": (i, [i, P, d, P, P, P, d, i, i, i, i, i, i, i, P, P]),
+            "or_threads": (i, []),
             "or_rho": (i, [P, P, d, i, i, i, i, i, P, P, P]),
             "or_tile_size": (i, [i]),
             "or_ls_fit": (i, [i, i, i, P, P, P]),
@@ -319,12 +343,15 @@ class Hierarchy:
         return x
 
     def fgmres(self, b, x0=None, tol=1e-10, m=20, max_restarts=50, nu1=2, nu2=2, gamma=1,
-               precond=1):
+               precond=1, gs_passes=2):
+        """precond: 0 none, 1 / 2 / 3 the cycle with the 16-colour / tile /
+        lexicographic Kaczmarz ordering; gs_passes: 1 = classical
+        Gram-Schmidt, 2 = with one reorthogonalisation."""
         b = _c(b)
         x = np.zeros_like(b) if x0 is None else _c(x0).copy()
         it, rs, rr = C.c_int(), C.c_int(), C.c_double()
         st = _chk(lib().or_fgmres(self._h, _p(b), _p(x), tol, m, max_restarts, nu1, nu2, gamma,
-                                  precond, C.byref(it), C.byref(rs), C.byref(rr)), "fgmres")
+                                  precond, gs_passes, C.byref(it), C.byref(rs), C.byref(rr)), "fgmres")
         return x, dict(status=st, iters=it.value, restarts=rs.value, relres=rr.value)
 
     def rho(self, x0, tol=1e-8, maxit=100, nu1=4, nu2=4, gamma=2, order=ORDER_COLOUR):
@@ -338,10 +365,12 @@ class Hierarchy:
                                C.byref(it), _p(hist)), "rho")
         return r.value, it.value, hist[:it.value + 1], st == 0
 
-    def solve(self, b, tol=1e-10, m=20, max_restarts=50, nu1=2, nu2=2, gamma=1, order=ORDER_COLOUR):
+    def solve(self, b, tol=1e-10, m=20, max_restarts=50, nu1=2, nu2=2, gamma=1, order=ORDER_COLOUR,
+              gs_passes=2):
         b = _c(b)
         psi = np.zeros_like(b)
         it, rr = C.c_int(), C.c_double()
         st = _chk(lib().or_solve(self.N, _p(self.U), self.m, self._h, _p(b), _p(psi), tol, m,
-                                 max_restarts, nu1, nu2, gamma, order, C.byref(it), C.byref(rr)), "solve")
+                                 max_restarts, nu1, nu2, gamma, order, gs_passes, C.byref(it), C.byref(rr)),
+                  "solve")
         return psi, dict(status=st, iters=it.value, relres=rr.value)

@@ -6,8 +6,19 @@
  * CUDA library is checked against this file; the two share no code.
  *
  * Readings of passages that the paper leaves open are marked "Reading:".
+ *
+ * The file builds two ways.  The plain build (gcc, no OpenMP) is the oracle
+ * that the tests check against.  The all-cores build (-fopenmp) is timed as
+ * the CPU baseline only: its "#pragma omp" lines split loops whose
+ * iterations are independent (matrix rows, the sites of one Kaczmarz colour,
+ * the tiles of one tile colour, vector updates) over the host cores; the
+ * plain build ignores them, so its arithmetic is the serial one.
  */
 #include "wilson_oracle.h"
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #include <math.h>
 #include <stdlib.h>
@@ -153,6 +164,7 @@ static int csr_from_triplets(int nrow, int ncol, const triplets *t, or_csr *A) {
 }
 
 static void csr_matvec(const or_csr *A, const cplx *x, cplx *y) {
+#pragma omp parallel for schedule(static)
   for (int i = 0; i < A->nrow; ++i) {
     cplx s = 0;
     for (int p = A->rowptr[i]; p < A->rowptr[i + 1]; ++p) s += A->val[p] * x[A->col[p]];
@@ -772,6 +784,7 @@ int or_tile_size(int N) { return (N >= 64 && N % 32 == 0) ? 8 : 0; }
 static void tile_sweep(const or_csr *AT, int N, cplx *x, cplx *r, double omega) {
   int T = or_tile_size(N);
   for (int tc = 0; tc < 4; ++tc)
+#pragma omp parallel for collapse(2) schedule(static)
     for (int ta = 0; ta < N / T; ++ta)
       for (int tb = 0; tb < N / (2 * T); ++tb) {
         if ((ta & 1) + 2 * (tb & 1) != tc) continue;
@@ -801,6 +814,7 @@ int or_kaczmarz(const or_hier *h, int l, cplx *x, cplx *r, int order, int sweeps
       for (int i = 0; i < 2 * n; ++i) kaczmarz_update(AT, i, x, r, omega);
     } else {
       for (int k = 0; k < 16; ++k)
+#pragma omp parallel for schedule(static)
         for (int q = 0; q < n; ++q) {
           int site = perm ? perm[q] : q;
           if (or_colour(N, site) != k) continue;
@@ -873,25 +887,35 @@ int or_cycle(const or_hier *h, int l, const cplx *f, cplx *x, int nu1, int nu2,
 
 static double vnorm(int n, const cplx *v) {
   double s = 0;
+#pragma omp parallel for reduction(+ : s) schedule(static)
   for (int i = 0; i < n; ++i) s += creal(v[i]) * creal(v[i]) + cimag(v[i]) * cimag(v[i]);
   return sqrt(s);
 }
 
 static cplx vdot(int n, const cplx *a, const cplx *b) { /* a^H b */
-  cplx s = 0;
-  for (int i = 0; i < n; ++i) s += conj(a[i]) * b[i];
-  return s;
+  double sr = 0, si = 0;
+#pragma omp parallel for reduction(+ : sr, si) schedule(static)
+  for (int i = 0; i < n; ++i) {
+    cplx t = conj(a[i]) * b[i];
+    sr += creal(t);
+    si += cimag(t);
+  }
+  return CMPLX(sr, si);
 }
 
 /* Flexible GMRES(m) (Saad 1993) with right preconditioning z_j = M(v_j),
- * classical Gram-Schmidt with one reorthogonalisation and Givens rotations.
- * Sec. 4 uses GMRES(32) preconditioned by a W(4,4) cycle; any cycle is
- * allowed here.  At each restart the true residual is recomputed.
- * precond = 0: identity (plain GMRES). Returns 0 converged, 1 not. */
+ * classical Gram-Schmidt (gs_passes = 1) or classical Gram-Schmidt with one
+ * reorthogonalisation (gs_passes = 2), and Givens rotations.  Sec. 4 uses
+ * GMRES(32) preconditioned by a W(4,4) cycle; any cycle is allowed here.
+ * At each restart the true residual is recomputed.  precond = 0: identity
+ * (plain GMRES); 1, 2, 3: the cycle with the 16-colour, tile-coloured or
+ * lexicographic Kaczmarz ordering.  Returns 0 converged, 1 not. */
 int or_fgmres(const or_hier *h, const cplx *b, cplx *x, double tol, int mrestart,
-              int max_restarts, int nu1, int nu2, int gamma, int precond,
+              int max_restarts, int nu1, int nu2, int gamma, int precond, int gs_passes,
               int *iters_out, int *restarts_out, double *relres_out) {
   int n = h->A[0].nrow, m = mrestart;
+  if (gs_passes < 1 || gs_passes > 2 || precond < 0 || precond > 3 || m < 1 || m > 64) return OR_EINVAL;
+  const int cyc_order[4] = {0, OR_ORDER_COLOUR, OR_ORDER_TILE, OR_ORDER_LEX};
   cplx *V = malloc(sizeof(cplx) * (size_t)n * (m + 1));
   cplx *Z = malloc(sizeof(cplx) * (size_t)n * m);
   cplx *w = malloc(sizeof(cplx) * n), *r = malloc(sizeof(cplx) * n);
@@ -920,16 +944,17 @@ int or_fgmres(const or_hier *h, const cplx *b, cplx *x, double tol, int mrestart
     int jend = 0;
     for (int j = 0; j < m; ++j) {
       cplx *vj = V + (size_t)j * n, *zj = Z + (size_t)j * n;
-      if (precond) rc = or_cycle(h, 0, vj, zj, nu1, nu2, gamma, precond == 2 ? OR_ORDER_TILE : OR_ORDER_COLOUR);
+      if (precond) rc = or_cycle(h, 0, vj, zj, nu1, nu2, gamma, cyc_order[precond]);
       else memcpy(zj, vj, sizeof(cplx) * n);
       if (rc) break;
       csr_matvec(&h->A[0], zj, w);
       for (int k = 0; k <= j; ++k) hcol[k] = 0;
-      for (int pass = 0; pass < 2; ++pass) {
+      for (int pass = 0; pass < gs_passes; ++pass) {
         cplx hp[64];
         for (int k = 0; k <= j; ++k) hp[k] = vdot(n, V + (size_t)k * n, w);
         for (int k = 0; k <= j; ++k) {
           const cplx *vk = V + (size_t)k * n;
+#pragma omp parallel for schedule(static)
           for (int i = 0; i < n; ++i) w[i] -= hp[k] * vk[i];
           hcol[k] += hp[k];
         }
@@ -969,6 +994,7 @@ int or_fgmres(const or_hier *h, const cplx *b, cplx *x, double tol, int mrestart
       y[i] = s / H[(size_t)i * m + i];
     }
     for (int k = 0; k < jend; ++k)
+#pragma omp parallel for schedule(static)
       for (int i = 0; i < n; ++i) x[i] += y[k] * Z[(size_t)k * n + i];
     restarts++;
   }
@@ -1021,14 +1047,15 @@ int or_rho(const or_hier *h, const cplx *x0, double tol, int maxit, int nu1, int
 /* Sec. 4: D psi = b through the reduced system Dhat psi_e = bhat. */
 int or_solve(int N, const cplx *U, double m, const or_hier *h, const cplx *b,
              cplx *psi, double tol, int mrestart, int max_restarts, int nu1,
-             int nu2, int gamma, int order, int *iters_out, double *relres_out) {
+             int nu2, int gamma, int order, int gs_passes, int *iters_out, double *relres_out) {
   int n = n_sites(N) * 2;
   cplx *bh = malloc(sizeof(cplx) * n), *xe = calloc(n, sizeof(cplx));
   if (!bh || !xe) { free(bh); free(xe); return OR_ENOMEM; }
   int rc = or_eo_reduce(N, U, m, b, bh);
   int st = 1;
+  int precond = order == OR_ORDER_TILE ? 2 : order == OR_ORDER_LEX ? 3 : 1;
   if (!rc) st = or_fgmres(h, bh, xe, tol, mrestart, max_restarts, nu1, nu2, gamma,
-                          order == OR_ORDER_TILE ? 2 : 1, iters_out, NULL, relres_out);
+                          precond, gs_passes, iters_out, NULL, relres_out);
   if (!rc && st >= 0) rc = or_eo_reconstruct(N, U, m, b, xe, psi);
   free(bh); free(xe);
   return rc ? rc : st;
@@ -1588,4 +1615,13 @@ or_hier *or_setup(int N, const cplx *U, double m, const or_setup_params *p,
   for (int l = 0; l < L; ++l) { free(S.Vr[l]); free(S.Ve[l]); free(S.lr[l]); free(S.le[l]); }
   if (rc) { or_hier_free(h); return NULL; }
   return h;
+}
+
+/* Host threads the loops above run on: 1 in the plain build. */
+int or_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
 }

@@ -104,19 +104,22 @@ int or_coarsest_solve(const or_hier *h, const cplx *f, cplx *x);
 int or_cycle(const or_hier *h, int l, const cplx *f, cplx *x, int nu1, int nu2,
              int gamma, int order);
 int or_fgmres(const or_hier *h, const cplx *b, cplx *x, double tol, int mrestart,
-              int max_restarts, int nu1, int nu2, int gamma, int precond,
+              int max_restarts, int nu1, int nu2, int gamma, int precond, int gs_passes,
               int *iters_out, int *restarts_out, double *relres_out);
 int or_rho(const or_hier *h, const cplx *x0, double tol, int maxit, int nu1, int nu2,
            int gamma, int order, double *rho_out, int *iters_out, double *hist);
 int or_solve(int N, const cplx *U, double m, const or_hier *h, const cplx *b,
              cplx *psi, double tol, int mrestart, int max_restarts, int nu1,
-             int nu2, int gamma, int order, int *iters_out, double *relres_out);
+             int nu2, int gamma, int order, int gs_passes, int *iters_out, double *relres_out);
 
 /* ---- setup building blocks (Secs. 3.3-3.5) ---- */
 int or_ls_fit(int Nf, int B, int k, const cplx *V, const double *w, cplx *Pw);
 int or_galerkin(const or_hier *h, int l, cplx *Ac_stencil);
 int or_gen_eig(int n, const cplx *Z, const cplx *T, double *lam, cplx *V);
 int or_dense_lu_solve(int n, const cplx *A, const cplx *b, cplx *x);
+
+/* host threads of this build (1 unless built with OpenMP) */
+int or_threads(void);
 
 /* ---- helpers for tests ---- */
 int or_csr_dense(const or_csr *A, cplx *dense);

@@ -34,6 +34,7 @@ struct KS {
   zd *yT;      // [m][nrhs] the same, rhs innermost
   double *bnorm, *beta, *nrm2, *inv;  // [nrhs]
   int *active, *stop, *jend, *iters;  // [nrhs]
+  int *nanf;                          // [nrhs] non-finite value seen (Arnoldi residual, or masked input)
   int *running;                       // [1]
 };
 
@@ -63,6 +64,7 @@ static KS ks_layout(void *base, int m, int nrhs) {
   k.stop = (int *)take(sizeof(int) * nrhs);
   k.jend = (int *)take(sizeof(int) * nrhs);
   k.iters = (int *)take(sizeof(int) * nrhs);
+  k.nanf = (int *)take(sizeof(int) * nrhs);
   k.running = (int *)take(sizeof(int) * 4);
   return k;
 }
@@ -268,8 +270,12 @@ __global__ void k_givens(KS k, int j, double tol) {
   k.iters[r] += 1;
   k.jend[r] = j + 1;
   double res = sqrt(cnorm2(g[j + 1]));
-  bool done = !(res > tol * k.bnorm[r]) || hn == 0.0 || !isfinite(res);
-  if (!isfinite(res)) k.running[1] = 1;  // NaN / Inf seen
+  bool bad = !isfinite(res);
+  bool done = !(res > tol * k.bnorm[r]) || hn == 0.0 || bad;
+  if (bad) {  // NaN / Inf seen: this right-hand side stops; the others go on
+    k.running[1] = 1;
+    k.nanf[r] = 1;
+  }
   k.inv[r] = (done || hn == 0.0) ? 0.0 : 1.0 / hn;
   if (done) k.stop[r] = 1;
   else atomicAdd(k.running, 1);
@@ -317,6 +323,14 @@ __global__ void k_zero_hcol(KS k) {
   int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= k.nrhs) return;
   for (int i = 0; i <= k.m; ++i) k.hcol[(long)r * (k.m + 1) + i] = mk(0.0, 0.0);
+}
+
+// zero the entries (and squared norm) of the right-hand sides flagged in mask
+__global__ void k_zero_masked(zd *__restrict__ v, long E, int R, const int *__restrict__ mask,
+                              double *__restrict__ nrm2) {
+  long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < E && mask[e % R]) v[e] = mk(0.0, 0.0);
+  if (e < R && mask[e]) nrm2[e] = 0.0;
 }
 
 __global__ void k_re_of(const zd *a, double *b, int n) {
@@ -385,7 +399,10 @@ int fg_norms(wl_amg *a, const zd *v, int nrhs, double *out) {
 }
 
 // true FP64 residual a->rr = bh - Dhat x and its norms (host output); the
-// squared norms stay in the Krylov scalars for the next fg_cycle
+// squared norms stay in the Krylov scalars for the next fg_cycle.  A
+// right-hand side whose residual norm is not finite gets rnorm = NaN and its
+// residual (and squared norm) zeroed, so no later kernel of the batch reads a
+// non-finite value of it; the caller retires it with WL_NAN.
 int fg_residual(wl_amg *a, const zd *bh, const zd *xh, int nrhs, double *rnorm) {
   wl_op *op = a->op;
   cudaStream_t s = op->stream;
@@ -400,12 +417,22 @@ int fg_residual(wl_amg *a, const zd *bh, const zd *xh, int nrhs, double *rnorm) 
   double *h_d = (double *)a->h_small;
   WL_CUDA(cudaMemcpyAsync(h_d, k.nrm2, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s));
   WL_CUDA(cudaStreamSynchronize(s));
+  std::vector<int> bad(nrhs, 0);
+  int nbad = 0;
   for (int r = 0; r < nrhs; ++r) {
     rnorm[r] = sqrt(h_d[r]);
     if (!std::isfinite(rnorm[r])) {
-      wl_set_error("non-finite residual for right-hand side %d", r);
-      return WL_NAN;
+      rnorm[r] = NAN;
+      bad[r] = 1;
+      ++nbad;
     }
+  }
+  if (nbad) {
+    WL_CUDA(cudaMemcpyAsync(k.nanf, bad.data(), sizeof(int) * nrhs, cudaMemcpyHostToDevice, s));
+    k_zero_masked<<<WL_GRID(E, 256), 256, 0, s>>>(rr, E, nrhs, k.nanf, k.nrm2);
+    wl_count_launches(1);
+    WL_CUDA(cudaGetLastError());
+    WL_CUDA(cudaStreamSynchronize(s));
   }
   return WL_OK;
 }
@@ -413,8 +440,11 @@ int fg_residual(wl_amg *a, const zd *bh, const zd *xh, int nrhs, double *rnorm) 
 // One restart cycle of FGMRES(m) from the residual left by fg_residual, for
 // the right-hand sides with active[r] != 0 (the others are untouched):
 // Arnoldi with z_j = M(v_j), Gram-Schmidt, Givens; then x += Z y.
-// iters_out[r]: iterations this cycle ran for r (host).
-int fg_cycle(wl_amg *a, const zd *bnorm_h, zd *xh, int nrhs, double tol, const int *active, int *iters_out) {
+// iters_out[r]: iterations this cycle ran for r (host); nan_out[r] (host, or
+// NULL): 1 if r's Arnoldi residual became non-finite (r stopped there; its x
+// is not to be trusted and the next true residual retires it).
+int fg_cycle(wl_amg *a, const zd *bnorm_h, zd *xh, int nrhs, double tol, const int *active, int *iters_out,
+             int *nan_out) {
   wl_op *op = a->op;
   cudaStream_t s = op->stream;
   int prec = a->prm.precision, m = a->prm.fgmres_m;
@@ -429,6 +459,7 @@ int fg_cycle(wl_amg *a, const zd *bnorm_h, zd *xh, int nrhs, double tol, const i
   (void)bnorm_h;
   WL_CUDA(cudaMemcpyAsync(k.active, active, sizeof(int) * nrhs, cudaMemcpyHostToDevice, s));
   WL_CUDA(cudaMemsetAsync(k.iters, 0, sizeof(int) * nrhs, s));
+  WL_CUDA(cudaMemsetAsync(k.nanf, 0, sizeof(int) * nrhs, s));
   // v_j = f[rhs] w is written together with the cycle-precision copy that
   // the cycle of step j reads (lev[0].f)
   auto scale_next = [&](const zd *in, zd *out) {
@@ -468,10 +499,6 @@ int fg_cycle(wl_amg *a, const zd *bnorm_h, zd *xh, int nrhs, double tol, const i
     WL_CUDA(cudaStreamSynchronize(s));
     memcpy(run, h_d + nrhs, sizeof(int) * 2);
     jdone = j + 1;
-    if (run[1]) {
-      wl_set_error("non-finite Arnoldi residual");
-      return WL_NAN;
-    }
     if (run[0] == 0) break;
   }
   k_trisolve<<<WL_GRID(nrhs, 128), 128, 0, s>>>(k);
@@ -480,6 +507,7 @@ int fg_cycle(wl_amg *a, const zd *bnorm_h, zd *xh, int nrhs, double tol, const i
   wl_count_launches(2);
   WL_CUDA(cudaGetLastError());
   WL_CUDA(cudaMemcpyAsync(iters_out, k.iters, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, s));
+  if (nan_out) WL_CUDA(cudaMemcpyAsync(nan_out, k.nanf, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, s));
   WL_CUDA(cudaStreamSynchronize(s));
   return WL_OK;
 }
@@ -493,9 +521,13 @@ int fg_upload_bnorm(wl_amg *a, const double *bn, int nrhs) {
 }
 
 // restarted FGMRES on a fixed batch: every right-hand side runs until its
-// true residual is <= tol * ||bhat|| or max_restarts cycles are spent
+// true residual is <= tol * ||bhat|| or max_restarts cycles are spent; one
+// whose residual becomes non-finite is retired with WL_NAN while the others
+// go on.  Returns WL_NAN if any right-hand side was retired that way, else
+// WL_NOT_CONVERGED if any missed tol, else WL_OK.
 int fgmres_run(wl_amg *a, const zd *bh, zd *xh, int nrhs, double tol, wl_info *info) {
-  std::vector<int> active(nrhs, 1), iters(nrhs, 0), restarts(nrhs, 0), it(nrhs, 0);
+  std::vector<int> active(nrhs, 1), iters(nrhs, 0), restarts(nrhs, 0), it(nrhs, 0), nanr(nrhs, 0),
+      nanc(nrhs, 0);
   std::vector<double> relres(nrhs, 0.0), bnorm(nrhs, 0.0), rn(nrhs, 0.0);
   WL_TRY(fg_norms(a, bh, nrhs, bnorm.data()));
   for (int r = 0; r < nrhs; ++r)
@@ -506,26 +538,38 @@ int fgmres_run(wl_amg *a, const zd *bh, zd *xh, int nrhs, double tol, wl_info *i
     WL_TRY(fg_residual(a, bh, xh, nrhs, rn.data()));
     int any = 0;
     for (int r = 0; r < nrhs; ++r) {
+      if (!std::isfinite(rn[r])) nanr[r] = 1;
+      if (nanr[r]) {
+        relres[r] = NAN;
+        active[r] = 0;
+        continue;
+      }
       relres[r] = rn[r] / bnorm[r];
       active[r] = active[r] && relres[r] > tol && cyc < a->prm.max_restarts;
       any |= active[r];
     }
     if (!any) break;
-    WL_TRY(fg_cycle(a, nullptr, xh, nrhs, tol, active.data(), it.data()));
+    WL_TRY(fg_cycle(a, nullptr, xh, nrhs, tol, active.data(), it.data(), nanc.data()));
     for (int r = 0; r < nrhs; ++r) {
       iters[r] += it[r];
       if (active[r]) restarts[r]++;
     }
   }
+  int nnan = 0;
   for (int r = 0; r < nrhs; ++r) {
-    bool ok = relres[r] <= tol;
-    if (!ok) status = WL_NOT_CONVERGED;
+    bool ok = !nanr[r] && relres[r] <= tol;
+    if (nanr[r]) ++nnan;
+    else if (!ok) status = WL_NOT_CONVERGED;
     if (info) {
-      info[r].status = ok ? WL_OK : WL_NOT_CONVERGED;
+      info[r].status = nanr[r] ? WL_NAN : ok ? WL_OK : WL_NOT_CONVERGED;
       info[r].restarts = restarts[r];
       info[r].iters = iters[r];
       info[r].true_relres = relres[r];
     }
+  }
+  if (nnan) {
+    wl_set_error("non-finite residual for %d of %d right-hand sides", nnan, nrhs);
+    return WL_NAN;
   }
   return status;
 }
@@ -546,7 +590,7 @@ extern "C" int amg_fgmres(wl_amg *a, const void *bhat, void *x, int nrhs, double
   WL_TRY(wl::to_internal((const zd *)bhat, a->bh.p, n2, nrhs, WL_FP64, s));
   WL_TRY(wl::to_internal((const zd *)x, a->xh.p, n2, nrhs, WL_FP64, s));
   int rc = wl::fgmres_run(a, a->bh.as<zd>(), a->xh.as<zd>(), nrhs, tol, info);
-  if (rc < 0) return rc;
+  if (rc < 0 && rc != WL_NAN) return rc;
   WL_TRY(wl::from_internal(a->xh.p, (zd *)x, n2, nrhs, WL_FP64, s));
   WL_CUDA(cudaStreamSynchronize(s));
   return rc;
@@ -650,8 +694,9 @@ extern "C" int amg_solve(wl_amg *a, const void *b, void *x, int nrhs, double tol
     else
       WL_TRY(wl::take_even_internal(op, xx, a->xh.as<zd>(), nb, s));
     int rc = wl::fgmres_run(a, a->bh.as<zd>(), a->xh.as<zd>(), nb, tol, info ? info + r0 : nullptr);
-    if (rc < 0) return rc;
-    if (rc) status = rc;
+    if (rc < 0 && rc != WL_NAN) return rc;
+    if (rc == WL_NAN || status == WL_NAN) status = WL_NAN;
+    else if (rc) status = rc;
     WL_TRY(wl::eo_reconstruct_internal(op, bb, a->xh.as<zd>(), xx, nb, s));
   }
   WL_CUDA(cudaStreamSynchronize(s));

@@ -12,7 +12,10 @@
 //
 // The array's name in host code is only a host-side stand-in: its device
 // address is fetched with cudaGetSymbolAddress once per device (with that
-// device current) by the first call on that device and cached.  Every call
+// device current) by the first call on that device and cached for the life
+// of the process, so the library must not be used across a cudaDeviceReset
+// (the cached address would be stale).  The call synchronises its stream
+// before returning, so it must not be issued during a stream capture.  Every call
 // shares the array: the first kernel overwrites every element it later reads,
 // so nothing needs clearing, but two calls whose work overlaps on the GPU
 // (on different streams or operators) race on it.

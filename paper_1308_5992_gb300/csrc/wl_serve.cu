@@ -32,7 +32,8 @@
 namespace wl {
 int fg_norms(wl_amg *a, const zd *v, int nrhs, double *out);
 int fg_residual(wl_amg *a, const zd *bh, const zd *xh, int nrhs, double *rnorm);
-int fg_cycle(wl_amg *a, const zd *bnorm_h, zd *xh, int nrhs, double tol, const int *active, int *iters_out);
+int fg_cycle(wl_amg *a, const zd *bnorm_h, zd *xh, int nrhs, double tol, const int *active, int *iters_out,
+             int *nan_out);
 int fg_upload_bnorm(wl_amg *a, const double *bn, int nrhs);
 }
 
@@ -409,8 +410,9 @@ static int worker_step(wl_server *S, Worker *W) {
   for (int q = 0; q < nq; ++q) {
     Slot &sl = W->slots[cols[q]];
     double rel = rn[q] / sl.bnorm;
-    bool conv = rel <= sl.req->tol;
-    bool give_up = sl.restarts >= a->prm.max_restarts;
+    bool bad = !std::isfinite(rel);  // retired alone; the other slots go on
+    bool conv = !bad && rel <= sl.req->tol;
+    bool give_up = bad || sl.restarts >= a->prm.max_restarts;
     if (conv || give_up) {
       Req *R = sl.req;
       const zd *bj = R->b + (size_t)sl.j * op->N * op->N * 2;
@@ -421,11 +423,12 @@ static int worker_step(wl_server *S, Worker *W) {
       WL_CUDA(cudaStreamSynchronize(s));
       std::lock_guard<std::mutex> lk(S->mu);
       wl_info &inf = R->info[sl.j];
-      inf.status = conv ? WL_OK : WL_NOT_CONVERGED;
+      inf.status = bad ? WL_NAN : conv ? WL_OK : WL_NOT_CONVERGED;
       inf.iters = sl.iters;
       inf.restarts = sl.restarts;
       inf.true_relres = rel;
-      if (!conv) R->status = WL_NOT_CONVERGED;
+      if (bad) R->status = WL_NAN;
+      else if (!conv && R->status != WL_NAN) R->status = WL_NOT_CONVERGED;
       if (--R->remaining == 0) {
         R->t_done = clk::now();
         R->done = true;
@@ -447,7 +450,7 @@ static int worker_step(wl_server *S, Worker *W) {
   double tol = 1.0;
   for (int q = 0; q < nq; ++q)
     if (active[q]) tol = std::min(tol, W->slots[cols[q]].req->tol);
-  WL_TRY(wl::fg_cycle(a, nullptr, W->PX.as<zd>(), nq, tol, active.data(), it.data()));
+  WL_TRY(wl::fg_cycle(a, nullptr, W->PX.as<zd>(), nq, tol, active.data(), it.data(), nullptr));
   for (int q = 0; q < nq; ++q)
     if (active[q]) {
       W->slots[cols[q]].iters += it[q];

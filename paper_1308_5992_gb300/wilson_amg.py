@@ -2,8 +2,13 @@
 
 Argument marshalling only: every step runs in the CUDA library.  Arrays are
 torch tensors on the GPU (complex128, contiguous); the binding passes their
-device pointers and the current torch stream.  Importing this module fails
-loudly if the library cannot be loaded: there is no CPU path.
+device pointers and the current torch stream.  The C ABI receives bare
+pointers and cannot see how large a buffer is, so before every call the
+binding checks that each tensor lives on the operator's device and holds at
+least the complex values the call reads or writes (ValueError otherwise):
+a short buffer would make a kernel read or write past its end.  Importing
+this module fails loudly if the library cannot be loaded: there is no CPU
+path.
 """
 import atexit
 import ctypes as C
@@ -120,6 +125,25 @@ def _ptr(t):
     return C.c_void_p(t.data_ptr())
 
 
+def _nrhs(nrhs):
+    """nrhs as a count of buffer rows; the library itself rejects nrhs < 1
+    and counts above its limits (WL_EINVAL)"""
+    if not isinstance(nrhs, int):
+        raise TypeError("nrhs must be an int, got %r" % (nrhs,))
+    return max(nrhs, 0)
+
+
+def _buf(t, need, device, what):
+    """Device pointer of t after checking that t is a contiguous complex128
+    CUDA tensor on `device` with at least `need` elements."""
+    p = _ptr(t)
+    if device is not None and t.device != device:
+        raise ValueError("%s is on %s, the operator on %s" % (what, t.device, device))
+    if t.numel() < need:
+        raise ValueError("%s holds %d complex values, the call needs %d" % (what, t.numel(), need))
+    return p
+
+
 def _stream():
     import torch
     return C.c_void_p(torch.cuda.current_stream().cuda_stream)
@@ -171,9 +195,10 @@ atexit.register(_close_all)
 class wl_op:
     """Owns a wl_op* (Wilson operator for one gauge field)."""
 
-    def __init__(self, ptr, L, m):
+    def __init__(self, ptr, L, m, device=None):
         self._p = ptr
         self.L, self.m = L, m
+        self.device = device
         self._amgs = weakref.WeakSet()
         _live_op.add(self)
 
@@ -203,6 +228,15 @@ class wl_amg:
         self.op = op
         op._amgs.add(self)
         _live_amg.add(self)
+        buf = (C.c_int * 8)()
+        nl = lib().amg_levels(ptr, C.cast(buf, C.c_void_p))
+        self.Nl = [buf[i] for i in range(nl)]  # lattice side of every level
+
+    def n(self, level):
+        """complex values of one level vector (N_l^2 / 2 sites, 2 spins)"""
+        if not 0 <= level < len(self.Nl):
+            raise ValueError("level %d outside 0..%d" % (level, len(self.Nl) - 1))
+        return self.Nl[level] ** 2
 
     @property
     def handle(self):
@@ -222,21 +256,35 @@ class wl_amg:
 
 # ---------------------------------------------------------- C ABI mirrors
 def wilson_create(gauge, L, m):
+    g = _buf(gauge, 2 * max(int(L), 0) ** 2, None, "gauge")   # the library checks L itself
     out = C.c_void_p()
-    _chk(lib().wilson_create(_ptr(gauge), L, m, _stream(), C.byref(out)), "wilson_create")
-    return wl_op(out, L, m)
+    _chk(lib().wilson_create(g, L, m, _stream(), C.byref(out)), "wilson_create")
+    return wl_op(out, L, m, gauge.device)
+
+
+def _full(op, nrhs):   # full fields [nrhs][L][L][2]
+    return _nrhs(nrhs) * op.L * op.L * 2
+
+
+def _even(op, nrhs):   # level-0 vectors [nrhs][L^2/2][2]
+    return _nrhs(nrhs) * op.L * op.L
 
 
 def wl_apply(op, which, x, y, nrhs, prec=WL_FP64):
-    return _chk(lib().wl_apply(op.handle, which, _ptr(x), _ptr(y), nrhs, prec), "wl_apply")
+    need = _even(op, nrhs) if which == WL_OP_DHAT else _full(op, nrhs)
+    return _chk(lib().wl_apply(op.handle, which, _buf(x, need, op.device, "x"), _buf(y, need, op.device, "y"),
+                               nrhs, prec), "wl_apply")
 
 
 def wl_eo_reduce(op, b, bhat, nrhs):
-    return _chk(lib().wl_eo_reduce(op.handle, _ptr(b), _ptr(bhat), nrhs), "wl_eo_reduce")
+    return _chk(lib().wl_eo_reduce(op.handle, _buf(b, _full(op, nrhs), op.device, "b"),
+                                   _buf(bhat, _even(op, nrhs), op.device, "bhat"), nrhs), "wl_eo_reduce")
 
 
 def wl_eo_reconstruct(op, b, xe, psi, nrhs):
-    return _chk(lib().wl_eo_reconstruct(op.handle, _ptr(b), _ptr(xe), _ptr(psi), nrhs),
+    return _chk(lib().wl_eo_reconstruct(op.handle, _buf(b, _full(op, nrhs), op.device, "b"),
+                                        _buf(xe, _even(op, nrhs), op.device, "xe"),
+                                        _buf(psi, _full(op, nrhs), op.device, "psi"), nrhs),
                 "wl_eo_reconstruct")
 
 
@@ -265,16 +313,23 @@ def amg_levels(amg):
 
 
 def amg_solve(amg, b, x, nrhs, tol):
+    """(rc, info per right-hand side); rc is WL_OK, WL_NOT_CONVERGED or WL_NAN
+    (some right-hand side had a non-finite residual and was retired; info
+    says which), other codes raise."""
+    op = amg.op
+    need = _full(op, nrhs)
     info = (wl_info * nrhs)()
-    rc = _chk(lib().amg_solve(amg.handle, _ptr(b), _ptr(x), nrhs, tol, info), "amg_solve",
-              ok=(WL_OK, WL_NOT_CONVERGED))
+    rc = _chk(lib().amg_solve(amg.handle, _buf(b, need, op.device, "b"), _buf(x, need, op.device, "x"), nrhs,
+                              tol, info), "amg_solve", ok=(WL_OK, WL_NOT_CONVERGED, WL_NAN))
     return rc, [i.as_dict() for i in info]
 
 
 def amg_fgmres(amg, bhat, x, nrhs, tol):
+    op = amg.op
+    need = _even(op, nrhs)
     info = (wl_info * nrhs)()
-    rc = _chk(lib().amg_fgmres(amg.handle, _ptr(bhat), _ptr(x), nrhs, tol, info), "amg_fgmres",
-              ok=(WL_OK, WL_NOT_CONVERGED))
+    rc = _chk(lib().amg_fgmres(amg.handle, _buf(bhat, need, op.device, "bhat"), _buf(x, need, op.device, "x"),
+                               nrhs, tol, info), "amg_fgmres", ok=(WL_OK, WL_NOT_CONVERGED, WL_NAN))
     return rc, [i.as_dict() for i in info]
 
 
@@ -282,10 +337,13 @@ def amg_rho(amg, x0, x, nrhs, tol=1e-8, maxit=100, hist=False):
     """Sec. 4's rho of the stand-alone cycle on Dhat x = 0 from x0; returns
     (rc, rho[nrhs], iters[nrhs], hist [nrhs][maxit + 1] or None)."""
     import numpy as np
+    need = _even(amg.op, nrhs)
+    dev = amg.op.device
+    x0p, xp = _buf(x0, need, dev, "x0"), _buf(x, need, dev, "x")
     rho = np.zeros(nrhs)
     it = np.zeros(nrhs, dtype=np.int32)
     h = np.zeros((nrhs, maxit + 1)) if hist else None
-    rc = _chk(lib().amg_rho(amg.handle, _ptr(x0), _ptr(x), nrhs, tol, maxit, rho.ctypes.data_as(C.c_void_p),
+    rc = _chk(lib().amg_rho(amg.handle, x0p, xp, nrhs, tol, maxit, rho.ctypes.data_as(C.c_void_p),
                             it.ctypes.data_as(C.c_void_p), h.ctypes.data_as(C.c_void_p) if hist else None),
               "amg_rho", ok=(WL_OK, WL_NOT_CONVERGED))
     return rc, rho, it, h
@@ -308,35 +366,48 @@ def amg_sweep_form(amg, level, nrhs, prec):
     return f.value, p.value, u.value
 
 
+def _lev(amg, level, nrhs, *named):
+    """device pointers of level-`level` vectors [nrhs][N_l^2/2][2]"""
+    need = _nrhs(nrhs) * amg.n(level)
+    return [_buf(t, need, amg.op.device, what) for what, t in named]
+
+
 def amg_level_apply(amg, level, x, y, nrhs, prec=WL_FP64):
-    return _chk(lib().amg_level_apply(amg.handle, level, _ptr(x), _ptr(y), nrhs, prec),
-                "amg_level_apply")
+    xp, yp = _lev(amg, level, nrhs, ("x", x), ("y", y))
+    return _chk(lib().amg_level_apply(amg.handle, level, xp, yp, nrhs, prec), "amg_level_apply")
 
 
 def amg_kaczmarz(amg, level, x, r, nrhs, sweeps=1, prec=WL_FP64):
-    return _chk(lib().amg_kaczmarz(amg.handle, level, _ptr(x), _ptr(r), nrhs, sweeps, prec),
-                "amg_kaczmarz")
+    xp, rp = _lev(amg, level, nrhs, ("x", x), ("r", r))
+    return _chk(lib().amg_kaczmarz(amg.handle, level, xp, rp, nrhs, sweeps, prec), "amg_kaczmarz")
 
 
 def amg_kaczmarz_form(amg, level, x, r, nrhs, sweeps, prec, form, param):
-    return _chk(lib().amg_kaczmarz_form(amg.handle, level, _ptr(x), _ptr(r), nrhs, sweeps, prec, form, param),
+    xp, rp = _lev(amg, level, nrhs, ("x", x), ("r", r))
+    return _chk(lib().amg_kaczmarz_form(amg.handle, level, xp, rp, nrhs, sweeps, prec, form, param),
                 "amg_kaczmarz_form")
 
 
 def amg_restrict(amg, level, r, fc, nrhs, prec=WL_FP64):
-    return _chk(lib().amg_restrict(amg.handle, level, _ptr(r), _ptr(fc), nrhs, prec), "amg_restrict")
+    (rp,) = _lev(amg, level, nrhs, ("r", r))
+    (fp,) = _lev(amg, level + 1, nrhs, ("fc", fc))
+    return _chk(lib().amg_restrict(amg.handle, level, rp, fp, nrhs, prec), "amg_restrict")
 
 
 def amg_prolong(amg, level, e, x, nrhs, prec=WL_FP64):
-    return _chk(lib().amg_prolong(amg.handle, level, _ptr(e), _ptr(x), nrhs, prec), "amg_prolong")
+    (ep,) = _lev(amg, level + 1, nrhs, ("e", e))
+    (xp,) = _lev(amg, level, nrhs, ("x", x))
+    return _chk(lib().amg_prolong(amg.handle, level, ep, xp, nrhs, prec), "amg_prolong")
 
 
 def amg_coarsest(amg, f, x, nrhs):
-    return _chk(lib().amg_coarsest(amg.handle, _ptr(f), _ptr(x), nrhs), "amg_coarsest")
+    fp, xp = _lev(amg, len(amg.Nl) - 1, nrhs, ("f", f), ("x", x))
+    return _chk(lib().amg_coarsest(amg.handle, fp, xp, nrhs), "amg_coarsest")
 
 
 def amg_cycle(amg, f, x, nrhs, prec=WL_FP64):
-    return _chk(lib().amg_cycle(amg.handle, _ptr(f), _ptr(x), nrhs, prec), "amg_cycle")
+    fp, xp = _lev(amg, 0, nrhs, ("f", f), ("x", x))
+    return _chk(lib().amg_cycle(amg.handle, fp, xp, nrhs, prec), "amg_cycle")
 
 
 def wl_last_error():
@@ -368,6 +439,7 @@ class wl_server:
     def __init__(self, ptr):
         self._p = ptr
         self.amgs = []
+        self.by_cfg = {}
         _live_srv.add(self)
 
     @property
@@ -396,6 +468,7 @@ def srv_add(srv, amg):
     cid = C.c_int()
     _chk(lib().srv_add(srv.handle, amg.handle, C.byref(cid)), "srv_add")
     srv.amgs.append(amg)
+    srv.by_cfg[cid.value] = amg
     return cid.value
 
 
@@ -411,8 +484,13 @@ def srv_start(srv):
 
 
 def srv_submit(srv, cfg, b, x, nrhs, tol):
+    if cfg not in srv.by_cfg:
+        raise ValueError("no configuration %r on this server" % (cfg,))
+    op = srv.by_cfg[cfg].op
+    need = _full(op, nrhs)
     rid = C.c_longlong()
-    _chk(lib().srv_submit(srv.handle, cfg, _ptr(b), _ptr(x), nrhs, tol, C.byref(rid)), "srv_submit")
+    _chk(lib().srv_submit(srv.handle, cfg, _buf(b, need, op.device, "b"), _buf(x, need, op.device, "x"), nrhs,
+                          tol, C.byref(rid)), "srv_submit")
     return rid.value
 
 
@@ -420,7 +498,7 @@ def srv_poll(srv, req_id, nrhs):
     done, lat = C.c_int(), C.c_double()
     info = (wl_info * nrhs)()
     rc = lib().srv_poll(srv.handle, req_id, C.byref(done), info, C.byref(lat))
-    _chk(rc, "srv_poll", ok=(WL_OK, WL_NOT_CONVERGED))
+    _chk(rc, "srv_poll", ok=(WL_OK, WL_NOT_CONVERGED, WL_NAN))
     return bool(done.value), [i.as_dict() for i in info], lat.value
 
 
@@ -434,4 +512,6 @@ def srv_destroy(srv):
 
 def wl_dhat_apply_noalloc(op, x, y, nrhs):
     """y = Dhat x through the allocation-free entry point (see the C header)."""
-    return _chk(lib().wl_dhat_apply_noalloc(op.handle, _ptr(x), _ptr(y), nrhs), "wl_dhat_apply_noalloc")
+    need = _even(op, nrhs)
+    return _chk(lib().wl_dhat_apply_noalloc(op.handle, _buf(x, need, op.device, "x"),
+                                            _buf(y, need, op.device, "y"), nrhs), "wl_dhat_apply_noalloc")

@@ -116,3 +116,41 @@ def test_alone_equals_mix_benchmark_cycle():
     assert float(torch.linalg.norm(x_mix[5] - x_alone[0]) / torch.linalg.norm(x_alone[0])) <= 1e-9
     assert max(_residual(op, w, b, x_mix)) <= 1e-9
     srv.close()
+
+
+def test_serving_matches_oracle(O, tmp_path):
+    """Requests of two lattice sizes (32x32 and 128x128) served together with
+    the benchmark's serving cycle, on hierarchies exported by the oracle: a
+    sampled right-hand side of each request, solved in the mix, matches the
+    oracle's own solve on the same hierarchy to 1e-10 relative error."""
+    from oracle.hierfile import write_hierarchy
+    p = W.amg_params_default(precision=W.WL_FP32, nu_pre=4, nu_post=4, gs_passes=1, kacz_order=1,
+                             arnoldi_matvec=1)
+    srv = W.srv_create(8 << 30, 4)
+    cfgs = []
+    for name in ("T32", "T128"):
+        w = workload(name)
+        h = O.Hierarchy.setup(w["N"], w["U"], w["m"], O.setup_params(w["blocks"], k_r=w["k"], k_e=w["k"],
+                                                                      seed=w["seed"]))
+        path = str(tmp_path / ("%s.wlh" % name))
+        write_hierarchy(path, h)
+        op = W.wilson_create(_T(w["U"]), w["N"], w["m"])
+        cfgs.append((w, h, W.srv_add(srv, W.amg_import(op, path, p))))
+    W.srv_start(srv)
+    live = []
+    for k, (w, h, cfg) in enumerate(cfgs * 2):   # two requests per lattice, interleaved
+        b = rhs_batch(w["N"], 3 + k, 44 + k)
+        x = torch.zeros((3 + k, w["N"], w["N"], 2), dtype=torch.complex128, device=DEV)
+        bd = _T(b)
+        torch.cuda.synchronize()
+        live.append((w, h, b, x, bd, W.srv_submit(srv, cfg, bd, x, 3 + k, 1e-13)))
+    W.srv_drain(srv)
+    for k, (w, h, b, x, bd, rid) in enumerate(live):
+        done, info, _ = W.srv_poll(srv, rid, 3 + k)
+        assert done and all(i["status"] == W.WL_OK and i["true_relres"] <= 1e-13 for i in info)
+        q = k % (3 + k)
+        ref, _ = h.solve(b[q], tol=1e-13)
+        got = x[q].cpu().numpy()
+        assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= 1e-10, (w["name"], k)
+    srv.close()
+

@@ -260,14 +260,17 @@ def test_cycle_linear(O, h64):
         assert np.abs(lhs - rhs).max() <= 1e-12 * np.abs(lhs).max()
 
 
-def test_gmres_minimal_residual(O, h32):
+@pytest.mark.parametrize("gs_passes", [1, 2])
+def test_gmres_minimal_residual(O, h32, gs_passes):
     """Unpreconditioned GMRES after k steps minimises ||b - A x|| over the
-    Krylov space span{b, Ab, ..., A^{k-1} b} (dense least squares)."""
+    Krylov space span{b, Ab, ..., A^{k-1} b} (dense least squares), with
+    classical Gram-Schmidt (one pass) and with one reorthogonalisation (two
+    passes): in exact arithmetic both give the same Arnoldi basis."""
     A = h32.dense(0)
     n = A.shape[0]
     b = cgauss(4, 4, n)
     k = 6
-    x, info = h32.fgmres(b, tol=0.0, m=k, max_restarts=1, precond=0)
+    x, info = h32.fgmres(b, tol=0.0, m=k, max_restarts=1, precond=0, gs_passes=gs_passes)
     K = np.empty((n, k), complex)
     v = b.copy()
     for j in range(k):
@@ -278,6 +281,22 @@ def test_gmres_minimal_residual(O, h32):
     ref = Q @ y
     assert info["iters"] == k
     assert np.abs(x - ref).max() <= 1e-9 * np.abs(ref).max()
+
+
+def test_fgmres_one_pass_cycle_solve(O, h64):
+    """The benchmark's Krylov variant (one Gram-Schmidt pass, tile-coloured
+    V(4,4) cycle) converges to the same solution as the default (two passes,
+    16-colour V(2,2)), and to the sparse-direct solution; the lexicographic
+    cycle too."""
+    h, w = h64
+    N = w["N"]
+    b = rhs_batch(N, 1, 5)[0]
+    D = O.wilson_csr(N, w["U"], w["m"]).tocsc()
+    ref = spla.spsolve(D, b.reshape(-1)).reshape(N, N, 2)
+    for kw in (dict(gs_passes=1, nu1=4, nu2=4, order=O.ORDER_TILE), dict(gs_passes=2, order=O.ORDER_LEX)):
+        psi, info = h.solve(b, tol=1e-13, **kw)
+        assert info["status"] == 0, kw
+        assert np.linalg.norm(psi - ref) <= 1e-10 * np.linalg.norm(ref), kw
 
 
 def test_solve_dense_8x8(O):

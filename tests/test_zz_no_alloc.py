@@ -37,6 +37,26 @@ def test_noalloc_matches_wl_apply_twice():
         assert err <= 1e-14, (call, err)
 
 
+def test_noalloc_allocates_no_device_memory():
+    """After the first call (which only looks up the array's address), a call
+    changes neither the device's free memory nor torch's allocator."""
+    w = workload("T64")
+    N = w["N"]
+    op = W.wilson_create(_dev(w["U"]), N, w["m"])
+    x = _dev(np.stack([cgauss(600 + r, 1, N * N) for r in range(2)]))
+    y = torch.zeros_like(x)
+    W.wl_dhat_apply_noalloc(op, x, y, 2)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    alloc0 = torch.cuda.memory_allocated()
+    for _ in range(3):
+        W.wl_dhat_apply_noalloc(op, x, y, 2)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    assert torch.cuda.memory_allocated() == alloc0
+
+
 def test_noalloc_rejects_oversize():
     w = workload("T64")
     op = W.wilson_create(_dev(w["U"]), w["N"], w["m"])
