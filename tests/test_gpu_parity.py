@@ -521,8 +521,9 @@ def test_hierarchy_roundtrip_and_errors(shared, ops, tmp_path):
     with pytest.raises(W.WilsonAMGError) as e:
         W.amg_import(op2, out)  # another operator
     assert e.value.code == W.WL_BAD_HIERARCHY
+    nc = h.n(len(h.Nl) - 1)   # the coarsest level has no Kaczmarz sweep: the library refuses it
     with pytest.raises(W.WilsonAMGError) as e:
-        W.amg_kaczmarz(amg, len(h.Nl) - 1, T(np.zeros(1)), T(np.zeros(1)), 1)
+        W.amg_kaczmarz(amg, len(h.Nl) - 1, T(np.zeros(nc)), T(np.zeros(nc)), 1)
     assert e.value.code == W.WL_EINVAL
 
 
