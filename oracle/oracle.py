@@ -91,6 +91,11 @@ def lib():
             "or_fgmres": (i, [P, P, P, d, i, i, i, i, i, i, i, P, P, P]),
             "or_solve": (i, [i, P, d, P, P, P, d, i, i, i, i, i, i, i, P, P]),
             "or_threads": (i, []),
+            "or_agg_interp": (i, [i, i, i, P, P]),
+            "or_agg_galerkin": (i, [P, i, i, i, P, P]),
+            "or_agg_apply": (i, [i, i, P, P, P]),
+            "or_agg_restrict": (i, [i, i, i, P, P, P]),
+            "or_agg_prolong": (i, [i, i, i, P, P, P]),
             "or_rho": (i, [P, P, d, i, i, i, i, i, P, P, P]),
             "or_tile_size": (i, [i]),
             "or_ls_fit": (i, [i, i, i, P, P, P]),
@@ -224,6 +229,37 @@ def dense_lu_solve(A, b):
     return x
 
 
+# ------------------------------------------------- aggregation coarse space
+def agg_interp(N, B, k, V):
+    """Q [nc][2][B*B][k]: per aggregate (B x B cell) and spin, the k test
+    vectors V [k][N*N] restricted there, orthonormalised in order."""
+    V = _c(V)
+    nc = (N // B) ** 2 // 2
+    Q = np.zeros((nc, 2, B * B, k), np.complex128)
+    _chk(lib().or_agg_interp(N, B, k, _p(V), _p(Q)), "agg_interp")
+    return Q
+
+
+def agg_apply(Nc, k, Ac, x):
+    Ac, x = _c(Ac), _c(x)
+    y = np.zeros_like(x)
+    _chk(lib().or_agg_apply(Nc, k, _p(Ac), _p(x), _p(y)), "agg_apply")
+    return y
+
+
+def agg_restrict(N, B, k, Q, r):
+    Q, r = _c(Q), _c(r)
+    fc = np.zeros((N // B) ** 2 // 2 * 2 * k, np.complex128)
+    _chk(lib().or_agg_restrict(N, B, k, _p(Q), _p(r), _p(fc)), "agg_restrict")
+    return fc
+
+
+def agg_prolong(N, B, k, Q, e, x):
+    Q, e, x = _c(Q), _c(e), _c(x).copy()
+    _chk(lib().or_agg_prolong(N, B, k, _p(Q), _p(e), _p(x)), "agg_prolong")
+    return x
+
+
 class SetupParams(C.Structure):
     _fields_ = [("levels", C.c_int), ("block", C.c_int * 8), ("k_r", C.c_int), ("k_e", C.c_int),
                 ("mu1", C.c_int), ("mu2", C.c_int), ("nu_pre", C.c_int), ("nu_post", C.c_int),
@@ -305,6 +341,15 @@ class Hierarchy:
         out = np.zeros((rows, cols), np.complex128)
         _chk(lib().or_hier_level_dense(self._h, l, which, _p(out)), "level_dense")
         return out
+
+    def agg_galerkin(self, l, B, k, Q):
+        """Ac [nc][9][2k][2k]: P^H A_l P for the aggregation P of Q, as a
+        9-point stencil of dense 2k x 2k blocks on the N_l / B lattice."""
+        Q = _c(Q)
+        nc = (self.Nl[l] // B) ** 2 // 2
+        Ac = np.zeros((nc, 9, 2 * k, 2 * k), np.complex128)
+        _chk(lib().or_agg_galerkin(self._h, l, B, k, _p(Q), _p(Ac)), "agg_galerkin")
+        return Ac
 
     def apply(self, l, x):
         x = _c(x)

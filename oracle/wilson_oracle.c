@@ -1617,6 +1617,160 @@ or_hier *or_setup(int N, const cplx *U, double m, const or_setup_params *p,
   return h;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Aggregation coarse space.  Sec. 4 closes by naming the alternative to its */
+/* W-cycles that it did not explore: more interpolation variables per coarse */
+/* point.  Reading used here (the aggregation-based solvers the paper cites   */
+/* as related work): the aggregates are the B x B cells of the full          */
+/* coarsening (Sec. 3.2 reading: the cell with corner (a0, b0) = (B floor(a/B),*/
+/* B floor(b/B)) holds the fine sites (a0 + ia, b0 + ib), 0 <= ia, ib < B,    */
+/* member index ia B + ib); for every aggregate and spin s the k test vectors */
+/* restricted to (aggregate, spin s) are orthonormalised by modified         */
+/* Gram-Schmidt in their given order, and those k columns are the columns of  */
+/* P for that (aggregate, spin).  Coarse variable 2k hc + k s + kappa of the  */
+/* coarse site hc (the cell's corner on the N/B lattice).  P is block        */
+/* diagonal in spin, so Gamma5 P = P Gamma5c with Gamma5c = +1 on the first k */
+/* variables of a coarse site and -1 on the last k, and the Galerkin operator */
+/* P^H A P (Sec. 3.5) is Gamma5c-Hermitian.  A fine site couples (3 x 3 box  */
+/* in (a, b)) only to sites of its own or an adjacent cell, so P^H A P is a   */
+/* 9-point stencil of dense 2k x 2k blocks on the coarse lattice.            */
+/* ------------------------------------------------------------------------ */
+static void agg_member(int N, int B, int h, int *hc, int *m) {
+  int x, y;
+  site_xy(N, h, &x, &y);
+  int a = (x + y) / 2, b = (x - y) / 2;
+  int a0 = B * floordiv(a, B), b0 = B * floordiv(b, B);
+  int xc = wrap(a0 + b0, N), yc = wrap(a0 - b0, N);
+  *hc = site_of(N / B, xc / B, yc / B);
+  *m = (a - a0) * B + (b - b0);
+}
+
+/* Q[hc][s][m][kappa] from the k test vectors V[kappa][2 nf] of a level-N
+ * lattice (unknown 2 h + s).  OR_ESTRUCT if some (aggregate, spin) block of
+ * the test vectors has rank < k (modified Gram-Schmidt leaves a column of
+ * norm <= 1e-12 times the column it started from). */
+int or_agg_interp(int N, int B, int k, const cplx *V, cplx *Q) {
+  if (B < 2 || N % B || (N / 2) % B || k < 1 || k > B * B) return OR_EINVAL;
+  int nf = n_sites(N), nc = n_sites(N / B), M = B * B;
+  for (int h = 0; h < nf; ++h) {
+    int hc, m;
+    agg_member(N, B, h, &hc, &m);
+    for (int s = 0; s < 2; ++s)
+      for (int kap = 0; kap < k; ++kap)
+        Q[(((size_t)hc * 2 + s) * M + m) * k + kap] = V[(size_t)kap * 2 * nf + 2 * h + s];
+  }
+  for (int hc = 0; hc < nc; ++hc)
+    for (int s = 0; s < 2; ++s) {
+      cplx *q = Q + ((size_t)hc * 2 + s) * M * k; /* q[m * k + kappa] */
+      for (int kap = 0; kap < k; ++kap) {
+        double n0 = 0;
+        for (int m = 0; m < M; ++m) n0 += creal(q[m * k + kap] * conj(q[m * k + kap]));
+        for (int lam = 0; lam < kap; ++lam) {
+          cplx d = 0; /* q_lambda^H q_kappa */
+          for (int m = 0; m < M; ++m) d += conj(q[m * k + lam]) * q[m * k + kap];
+          for (int m = 0; m < M; ++m) q[m * k + kap] -= d * q[m * k + lam];
+        }
+        double nn = 0;
+        for (int m = 0; m < M; ++m) nn += creal(q[m * k + kap] * conj(q[m * k + kap]));
+        if (!(sqrt(nn) > 1e-12 * sqrt(n0))) return OR_ESTRUCT;
+        for (int m = 0; m < M; ++m) q[m * k + kap] /= sqrt(nn);
+      }
+    }
+  return OR_OK;
+}
+
+static int agg_P_csr(int N, int B, int k, const cplx *Q, or_csr *P) {
+  int nf = n_sites(N), nc = n_sites(N / B), M = B * B;
+  triplets t = {0};
+  int rc = OR_OK;
+  for (int h = 0; h < nf && !rc; ++h) {
+    int hc, m;
+    agg_member(N, B, h, &hc, &m);
+    for (int s = 0; s < 2 && !rc; ++s)
+      for (int kap = 0; kap < k && !rc; ++kap)
+        rc = trip_push(&t, 2 * h + s, 2 * k * hc + k * s + kap, Q[(((size_t)hc * 2 + s) * M + m) * k + kap]);
+  }
+  if (!rc) rc = csr_from_triplets(2 * nf, 2 * k * nc, &t, P);
+  trip_free(&t);
+  return rc;
+}
+
+/* Galerkin operator of level l of h with the aggregation P of Q:
+ * Ac[hc][d][r][c] (2k x 2k blocks, offset d as for the stencils above) =
+ * (P^H A_l P) restricted to the coarse sites hc and neighbour(hc, d). */
+int or_agg_galerkin(const or_hier *h, int l, int B, int k, const cplx *Q, cplx *Ac) {
+  if (l < 0 || l >= h->L) return OR_EINVAL;
+  int N = h->N[l], Nc = N / B, nc = n_sites(Nc), K2 = 2 * k;
+  if (B < 2 || N % B || (N / 2) % B || Nc < 8) return OR_EINVAL;
+  or_csr P = {0}, PH = {0}, AP = {0}, C = {0};
+  int rc = agg_P_csr(N, B, k, Q, &P);
+  if (!rc) rc = csr_transpose(&P, 1, &PH);
+  if (!rc) rc = csr_mul(&h->A[l], &P, &AP);
+  if (!rc) rc = csr_mul(&PH, &AP, &C);
+  if (!rc) {
+    memset(Ac, 0, sizeof(cplx) * (size_t)nc * 9 * K2 * K2);
+    for (int row = 0; row < C.nrow && !rc; ++row) {
+      int hr = row / K2, r = row % K2;
+      for (int p = C.rowptr[row]; p < C.rowptr[row + 1]; ++p) {
+        int hcol = C.col[p] / K2, c = C.col[p] % K2, found = 0;
+        for (int d = 0; d < 9; ++d)
+          if (or_stencil_neighbour(Nc, hr, d) == hcol) {
+            Ac[(((size_t)hr * 9 + d) * K2 + r) * K2 + c] += C.val[p];
+            found = 1;
+            break;
+          }
+        if (!found && C.val[p] != 0) rc = OR_ESTRUCT;
+      }
+    }
+  }
+  csr_free(&P); csr_free(&PH); csr_free(&AP); csr_free(&C);
+  return rc;
+}
+
+/* y = Ac x on the coarse lattice Nc (x, y [nc][2k]): y_h = sum_d Ac[h][d] x_{neighbour(h, d)}. */
+int or_agg_apply(int Nc, int k, const cplx *Ac, const cplx *x, cplx *y) {
+  int nc = n_sites(Nc), K2 = 2 * k;
+  for (int h = 0; h < nc; ++h)
+    for (int r = 0; r < K2; ++r) {
+      cplx s = 0;
+      for (int d = 0; d < 9; ++d) {
+        int j = or_stencil_neighbour(Nc, h, d);
+        for (int c = 0; c < K2; ++c) s += Ac[(((size_t)h * 9 + d) * K2 + r) * K2 + c] * x[(size_t)j * K2 + c];
+      }
+      y[(size_t)h * K2 + r] = s;
+    }
+  return OR_OK;
+}
+
+/* fc = P^H r (r a level-N vector [2 nf], fc [nc][2k]) and x += P e. */
+int or_agg_restrict(int N, int B, int k, const cplx *Q, const cplx *r, cplx *fc) {
+  int nf = n_sites(N), nc = n_sites(N / B), M = B * B;
+  memset(fc, 0, sizeof(cplx) * (size_t)nc * 2 * k);
+  for (int h = 0; h < nf; ++h) {
+    int hc, m;
+    agg_member(N, B, h, &hc, &m);
+    for (int s = 0; s < 2; ++s)
+      for (int kap = 0; kap < k; ++kap)
+        fc[(size_t)hc * 2 * k + k * s + kap] += conj(Q[(((size_t)hc * 2 + s) * M + m) * k + kap]) * r[2 * h + s];
+  }
+  return OR_OK;
+}
+
+int or_agg_prolong(int N, int B, int k, const cplx *Q, const cplx *e, cplx *x) {
+  int nf = n_sites(N), M = B * B;
+  for (int h = 0; h < nf; ++h) {
+    int hc, m;
+    agg_member(N, B, h, &hc, &m);
+    for (int s = 0; s < 2; ++s) {
+      cplx t = 0;
+      for (int kap = 0; kap < k; ++kap)
+        t += Q[(((size_t)hc * 2 + s) * M + m) * k + kap] * e[(size_t)hc * 2 * k + k * s + kap];
+      x[2 * h + s] += t;
+    }
+  }
+  return OR_OK;
+}
+
 /* Host threads the loops above run on: 1 in the plain build. */
 int or_threads(void) {
 #ifdef _OPENMP

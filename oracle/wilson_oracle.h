@@ -118,6 +118,15 @@ int or_galerkin(const or_hier *h, int l, cplx *Ac_stencil);
 int or_gen_eig(int n, const cplx *Z, const cplx *T, double *lam, cplx *V);
 int or_dense_lu_solve(int n, const cplx *A, const cplx *b, cplx *x);
 
+/* ---- aggregation coarse space (Sec. 4's "more interpolation variables") ----
+ * Q [nc][2][B*B][k]: orthonormal columns per (aggregate, spin); Ac
+ * [nc][9][2k][2k]: Galerkin block stencil; coarse vectors [nc][2k]. */
+int or_agg_interp(int N, int B, int k, const cplx *V, cplx *Q);
+int or_agg_galerkin(const or_hier *h, int l, int B, int k, const cplx *Q, cplx *Ac);
+int or_agg_apply(int Nc, int k, const cplx *Ac, const cplx *x, cplx *y);
+int or_agg_restrict(int N, int B, int k, const cplx *Q, const cplx *r, cplx *fc);
+int or_agg_prolong(int N, int B, int k, const cplx *Q, const cplx *e, cplx *x);
+
 /* host threads of this build (1 unless built with OpenMP) */
 int or_threads(void);
 
