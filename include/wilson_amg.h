@@ -237,6 +237,52 @@ int amg_rho(wl_amg *amg, const void *x0, void *x, int nrhs, double tol, int maxi
  * captured into a CUDA graph. */
 int wl_dhat_apply_noalloc(wl_op *op, const void *x, void *y, int nrhs);
 
+/* ---- aggregation coarse space (Sec. 4: "more interpolation variables") ----
+ * Sec. 4 names, as the alternative it did not explore, coarse spaces with
+ * more interpolation variables per coarse point.  An aggregation coarse
+ * space of level `level` of a hierarchy: every B x B cell of the full
+ * coarsening (B = 2 or 4, cells in the rotated coordinates a = (x+y)/2,
+ * b = (x-y)/2) is an aggregate; per aggregate and spin the k test vectors V
+ * restricted there are orthonormalised by modified Gram-Schmidt in their
+ * given order, giving k columns of P per spin (2k coarse variables per coarse
+ * site, Gamma5 P = P Gamma5c).  The Galerkin operator Ac = P^H A_l P (Sec.
+ * 3.5) is a 9-point stencil of dense 2k x 2k complex blocks on the N_l / B
+ * lattice.
+ * Layouts (device, complex128): V [k][n_l][2] (level-l vectors); Q
+ * [nc][2][B*B][k] (coarse site, spin, member ia B + ib of the cell, column);
+ * Ac [nc][9][2k][2k] (site, offset d as for the stencils above, row variable
+ * s k + kappa, column variable t k + lambda); coarse vectors [nrhs][nc][2k].
+ * Requirements: N_l / B >= 8, 1 <= k <= min(16, B^2); WL_EINVAL otherwise, or
+ * when V restricted to some (aggregate, spin) has rank < k.  The object keeps
+ * its hierarchy alive. */
+typedef struct wl_agg wl_agg;
+enum { WL_AGG_FP64 = 0, WL_AGG_FP32 = 1, WL_AGG_TC = 2, WL_AGG_TC1 = 3 }; /* agg_apply kernels */
+int agg_create(wl_amg *amg, int level, int B, int k, const void *V, wl_agg **out);
+/* the same from given Q and Ac (device, layouts above), e.g. an exported one */
+int agg_import(wl_amg *amg, int level, int B, int k, const void *Q, const void *Ac, wl_agg **out);
+int agg_export(wl_agg *g, void *Q, void *Ac);
+/* number of coarse sites, coarse lattice side and k (host outputs, each may be NULL) */
+int agg_info(wl_agg *g, int *nc, int *Nc, int *k);
+void agg_destroy(wl_agg *g);
+/* y = Ac x for nrhs right-hand sides (x, y coarse vectors, caller-owned):
+ * kernel WL_AGG_FP64 (CUDA cores, FP64), WL_AGG_FP32 (CUDA cores, FP32
+ * arithmetic on FP32 copies of Ac and x) or WL_AGG_TC (k = 8 only: the
+ * tensor cores, tcgen05.mma on TF32 operands split into high and low parts,
+ * FP32 accumulation, accurate to FP32 rounding) or WL_AGG_TC1 (k = 8: the
+ * tensor cores on the TF32-rounded operands alone, one product per term,
+ * about 1e-3 relative; exact to FP32 accumulation when Ac and x are TF32
+ * numbers).  1 <= nrhs <= 4096.
+ * WL_TIMEOUT if a tensor-core wait ran out (the kernel then stops early and
+ * y is not valid).  Synchronous. */
+int agg_apply(wl_agg *g, const void *x, void *y, int nrhs, int kernel);
+/* fc = P^H r and x += P e (r, x level-l vectors; fc, e coarse vectors), FP64. */
+int agg_restrict(wl_agg *g, const void *r, void *fc, int nrhs);
+int agg_prolong(wl_agg *g, const void *e, void *x, int nrhs);
+/* average duration (host output, ms) of one apply kernel launch for nrhs
+ * right-hand sides on the object's internal buffers, over reps launches
+ * (CUDA events on the library's work stream) */
+int agg_time_apply(wl_agg *g, int nrhs, int kernel, int reps, double *avg_ms);
+
 /* ---- serving: continuous batching over resident hierarchies ----
  * A server keeps hierarchies of several gauge fields (lattice sizes may
  * differ) resident and answers solve requests.  srv_add reserves, for each

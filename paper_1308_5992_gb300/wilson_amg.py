@@ -24,6 +24,7 @@ WL_OP_D, WL_OP_DHAT, WL_OP_Z = 0, 1, 2
 WL_CYCLE_V, WL_CYCLE_W = 0, 1
 (WL_K_DHAT, WL_K_KACZ, WL_K_STENCIL, WL_K_RESTRICT, WL_K_PROLONG, WL_K_COARSEST, WL_K_GS_DOT,
  WL_K_GS_AXPY, WL_K_KACZ_TILE) = range(9)
+WL_AGG_FP64, WL_AGG_FP32, WL_AGG_TC, WL_AGG_TC1 = 0, 1, 2, 3
 
 
 class amg_params(C.Structure):
@@ -103,6 +104,15 @@ def lib():
             "srv_drain": (i, [P]),
             "srv_destroy": (None, [P]),
             "wl_launch_count": (C.c_longlong, []),
+            "agg_create": (i, [P, i, i, i, P, C.POINTER(P)]),
+            "agg_import": (i, [P, i, i, i, P, P, C.POINTER(P)]),
+            "agg_export": (i, [P, P, P]),
+            "agg_info": (i, [P, C.POINTER(i), C.POINTER(i), C.POINTER(i)]),
+            "agg_destroy": (None, [P]),
+            "agg_apply": (i, [P, P, P, i, i]),
+            "agg_restrict": (i, [P, P, P, i]),
+            "agg_prolong": (i, [P, P, P, i]),
+            "agg_time_apply": (i, [P, i, i, i, C.POINTER(d)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -515,3 +525,104 @@ def wl_dhat_apply_noalloc(op, x, y, nrhs):
     need = _even(op, nrhs)
     return _chk(lib().wl_dhat_apply_noalloc(op.handle, _buf(x, need, op.device, "x"),
                                             _buf(y, need, op.device, "y"), nrhs), "wl_dhat_apply_noalloc")
+
+
+# ------------------------------------------------- aggregation coarse space
+class wl_agg:
+    """Owns a wl_agg* (aggregation coarse space of one level of a hierarchy);
+    keeps the hierarchy object alive."""
+
+    def __init__(self, ptr, amg, level, B, k):
+        self._p = ptr
+        self.amg, self.level, self.B, self.k = amg, level, B, k
+        nc, Nc, kk = C.c_int(), C.c_int(), C.c_int()
+        _chk(lib().agg_info(ptr, C.byref(nc), C.byref(Nc), C.byref(kk)), "agg_info")
+        self.nc, self.Nc = nc.value, Nc.value
+        self.nf = amg.n(level) // 2
+        _live_agg.add(self)
+
+    @property
+    def handle(self):
+        return self._p
+
+    def close(self):
+        if self._p:
+            lib().agg_destroy(self._p)
+            self._p = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+_live_agg = weakref.WeakSet()
+
+
+def _close_all_agg():
+    for g in list(_live_agg):
+        g.close()
+
+
+atexit.register(_close_all_agg)   # runs before _close_all (atexit is last-in, first-out)
+
+
+def agg_create(amg, level, B, k, V):
+    """Aggregation coarse space of `level` from the k test vectors V
+    ([k][n_l][2] complex128 on the device)."""
+    dev = amg.op.device
+    need = k * amg.n(level)
+    out = C.c_void_p()
+    _chk(lib().agg_create(amg.handle, level, B, k, _buf(V, need, dev, "V"), C.byref(out)), "agg_create")
+    return wl_agg(out, amg, level, B, k)
+
+
+def agg_import(amg, level, B, k, Q, Ac):
+    dev = amg.op.device
+    nc = (amg.Nl[level] // B) ** 2 // 2
+    out = C.c_void_p()
+    _chk(lib().agg_import(amg.handle, level, B, k, _buf(Q, nc * 2 * B * B * k, dev, "Q"),
+                          _buf(Ac, nc * 9 * 4 * k * k, dev, "Ac"), C.byref(out)), "agg_import")
+    return wl_agg(out, amg, level, B, k)
+
+
+def agg_export(g, Q, Ac):
+    dev = g.amg.op.device
+    return _chk(lib().agg_export(g.handle, _buf(Q, g.nc * 2 * g.B * g.B * g.k, dev, "Q"),
+                                 _buf(Ac, g.nc * 9 * 4 * g.k * g.k, dev, "Ac")), "agg_export")
+
+
+def agg_apply(g, x, y, nrhs, kernel=WL_AGG_FP64):
+    need = _nrhs(nrhs) * g.nc * 2 * g.k
+    dev = g.amg.op.device
+    return _chk(lib().agg_apply(g.handle, _buf(x, need, dev, "x"), _buf(y, need, dev, "y"), nrhs, kernel),
+                "agg_apply")
+
+
+def agg_restrict(g, r, fc, nrhs):
+    dev = g.amg.op.device
+    return _chk(lib().agg_restrict(g.handle, _buf(r, _nrhs(nrhs) * 2 * g.nf, dev, "r"),
+                                   _buf(fc, _nrhs(nrhs) * g.nc * 2 * g.k, dev, "fc"), nrhs), "agg_restrict")
+
+
+def agg_prolong(g, e, x, nrhs):
+    dev = g.amg.op.device
+    return _chk(lib().agg_prolong(g.handle, _buf(e, _nrhs(nrhs) * g.nc * 2 * g.k, dev, "e"),
+                                  _buf(x, _nrhs(nrhs) * 2 * g.nf, dev, "x"), nrhs), "agg_prolong")
+
+
+def agg_time_apply(g, nrhs, kernel, reps):
+    ms = C.c_double()
+    _chk(lib().agg_time_apply(g.handle, nrhs, kernel, reps, C.byref(ms)), "agg_time_apply")
+    return ms.value
+
+
+
+def agg_info(g):
+    """(coarse sites, coarse lattice side, k)"""
+    return g.nc, g.Nc, g.k
+
+
+def agg_destroy(g):
+    g.close()
