@@ -1,6 +1,9 @@
 #!/usr/bin/env python3
-"""Benchmark: Wilson-AMG solves/s at 1e-10 relative residual on one GB300
-(and on N GPUs as independent replicas).
+"""Benchmark: Wilson-AMG solves/s at 1e-10 relative error on one GB300 (and
+on N GPUs as independent replicas).  A right-hand side counts as solved at a
+relative residual of 3e-12, the tolerance whose solutions are within 1e-10
+relative error of the exact one on this workload (measured in the same run
+against a 1e-13 oracle solve: rel_err_vs_exact).
 
 A step is one call of the solver's public entry point amg_solve on one batch
 of right-hand sides: odd-even reduction, FP64 FGMRES(20) preconditioned by
@@ -34,7 +37,7 @@ METRIC = "Wilson-AMG solves/s at 1e-10 rel err (mixed+batched vs plain FP64); p9
 # roofline reports, from one ncu capture of the C4 workload at 64 right-hand sides
 # (ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum on bench.py --kernel-only);
 # None until captured for the current kernel
-TRAFFIC = {"k_mdot": 3228150000, "k_kacz_tile": 127775488}
+TRAFFIC = {"k_mdot": 3228150000, "k_kacz_tile": None}
 
 
 def parse():
@@ -50,8 +53,9 @@ def parse():
     ap.add_argument("--serve-configs", type=int, default=16,
                     help="resident configurations S00.. of the serving mix (16 = all five lattice sizes)")
     ap.add_argument("--serve-hbm-gb", type=float, default=160.0, help="device-memory budget of the server")
-    ap.add_argument("--tol", type=float, default=1e-10,
-                    help="relative residual at which a right-hand side counts as solved")
+    ap.add_argument("--tol", type=float, default=3e-12,
+                    help="relative residual at which a right-hand side counts as solved (3e-12 gives solutions "
+                         "within 1e-10 relative error on the default workload; the line reports the error)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="timed CPU work per oracle variant (at least one solve each)")
     ap.add_argument("--nrhs", type=int, default=0, help="override the workload's RHS per step")
@@ -261,7 +265,7 @@ def run_gb300(args, rank, world, local_rank):
 
     def params(precision, plain=False):
         # plain: the method as the paper states it (16-colour Kaczmarz, FP64 throughout)
-        p = W.amg_params_default(k_r=w["k"], k_e=w["k"], seed=w["seed"], zero_guess=1,
+        p = W.amg_params_default(k_r=w["k"], k_e=w["k"], seed=w["seed"], zero_guess=1, setup_mu=w["setup_mu"],
                                  precision=precision, nu_pre=w["nu"], nu_post=w["nu"],
                                  cycle=W.WL_CYCLE_W if w["cycle"] == "W" else W.WL_CYCLE_V,
                                  fgmres_m=w["fgmres_m"], gs_passes=w["gs_passes"],
@@ -387,15 +391,21 @@ def run_gb300(args, rank, world, local_rank):
                  "achieved": round(achieved, 1), "peak": hbm, "peak_source": src, "unit": "GB/s",
                  "frac": round(achieved / hbm, 4), "traffic": None, "avg_launch_ms": round(kacz_ms, 5),
                  "algorithmic_bytes": int(kacz_bytes)}
-    # k_kacz_tile: one tile colour (1/4 of the sites, a quarter of a sweep): r and x read
-    # and written once, the stencil rows and denominators read once, for 1/4 of the sites
+    # k_kacz_tile: one tile colour (1/4 of the sites, a quarter of a sweep).  Algorithmic
+    # bytes per even site and right-hand side of one Kaczmarz pass: r and x read and
+    # written once (4 x 2 spins x 8 B = 64 B in FP32), plus the site's links and column
+    # norms (40 B) shared by the right-hand sides; the kernel itself reads the explicit
+    # 9-point stencil row (288 B) in place of the links, so its own count is higher
     tile_ms = W.wl_time_kernel(amg, W.WL_K_KACZ_TILE, 0, nrhs, prec, 80)
-    tile_bytes = n0 / 4 * (nrhs * 2 * 2 * eb * 2 + 36 * sb + 2 * (eb // 2))
+    tile_bytes = n0 / 4 * (nrhs * 2 * 2 * eb * 2 + 40 * (eb // 8))
+    tile_bytes_stencil = n0 / 4 * (nrhs * 2 * 2 * eb * 2 + 36 * sb + 2 * (eb // 2))
     achieved = tile_bytes / (tile_ms * 1e-3) / 1e9
     roof_tile = {"kernel": "k_kacz_tile (fine level, one of 4 tile colours)", "bound": "hbm",
                  "achieved": round(achieved, 1), "peak": hbm, "peak_source": src, "unit": "GB/s",
                  "frac": round(achieved / hbm, 4), "traffic": TRAFFIC.get("k_kacz_tile"),
-                 "avg_launch_ms": round(tile_ms, 5), "algorithmic_bytes": int(tile_bytes)}
+                 "avg_launch_ms": round(tile_ms, 5), "algorithmic_bytes": int(tile_bytes),
+                 "bytes_per_site_per_rhs": 64, "bytes_per_site": 40,
+                 "achieved_with_stencil_rows": round(tile_bytes_stencil / (tile_ms * 1e-3) / 1e9, 1)}
     # k_stencil on level 0 (residual f - A x with the 9-point Dhat stencil; the same gather
     # computes the FP32 Arnoldi matvec): x read once (its 9 neighbours come from cache), f
     # read, y written, the stencil row (36 complex) read once per site
@@ -418,14 +428,16 @@ def run_gb300(args, rank, world, local_rank):
         "dtype": "f32 cycle + f64 Krylov" if prec != W.WL_FP64 else "f64",
         "data": "synthetic (seeded U(1) Metropolis gauge, complex Gaussian right-hand sides)",
         "config": {"workload": "%s: %dx%d lattice, beta=%g, %d Metropolis sweeps, m=%.6f (smallest |eig| %g), "
-                               "%d grids, blocks %s, k=%d, %d RHS/step, %s(%d,%d) %s Kaczmarz cycle in %s, "
-                               "FGMRES(%d) with %d Gram-Schmidt pass(es) in FP64, Arnoldi matvec %s, "
-                               "FP64 true residual at restarts, tol %g"
+                               "%d grids, blocks %s, k=%d, setup relaxations %s, %d RHS/step, %s(%d,%d) %s "
+                               "Kaczmarz cycle in %s, FGMRES(%d) with %d Gram-Schmidt pass(es) in FP64, Arnoldi "
+                               "matvec %s, FP64 true residual at restarts, relative residual %g (error vs exact "
+                               "in rel_err_vs_exact)"
                                % (args.workload, N, N, w["beta"], w["sweeps"], w["m"], w["target"],
-                                  len(w["blocks"]) + 1, w["blocks"], w["k"], nrhs, w["cycle"], w["nu"], w["nu"],
-                                  ["16-colour", "tile-coloured (8x8 tiles)"][w["kacz_order"]],
+                                  len(w["blocks"]) + 1, w["blocks"], w["k"], list(w["setup_mu"]), nrhs, w["cycle"],
+                                  w["nu"], w["nu"], ["16-colour", "tile-coloured (8x8 tiles)"][w["kacz_order"]],
                                   ["fp64", "fp32", "fp32+bf16-storage"][prec], w["fgmres_m"], w["gs_passes"],
                                   "fp32" if w["arnoldi_matvec"] and prec != W.WL_FP64 else "fp64", TOL),
+                   "tol": TOL,
                    "nrhs": nrhs, "L": N, "precision": ["fp64", "fp32", "fp32_bf16"][prec],
                    "l2": "flushed (256 MB write) between timed steps", "parallelism": "replicas"},
         "iters_mean": round(sum(iters) / len(iters), 2), "iters_max": max(iters),
@@ -437,6 +449,32 @@ def run_gb300(args, rank, world, local_rank):
         "e2e": e2e, "gpu_launches": int(launches), "roofline": roof, "roofline_more": roof_more, "clocks": clk,
         "sweep_forms": [list(W.amg_sweep_form(amg, l, nrhs, prec)) for l in range(len(w["blocks"]))],
     }
+    # Aggregation coarse space (Sec. 4's "more interpolation variables per coarse point"):
+    # the 9-point stencil of 16 x 16 blocks of 4 x 4 aggregates with k = 8 spin-split test
+    # vectors of this lattice (8192 coarse sites), applied to this batch's 64 right-hand
+    # sides on CUDA cores (FP32) and on the tensor cores (tcgen05: TF32 operands split
+    # into high and low parts, FP32 accuracy; and the single-term TF32 form)
+    if nrhs >= 16 and N % 8 == 0:
+        try:
+            from wl_inputs import cgauss
+            V = torch.from_numpy(np.stack([cgauss(92, j, N * N) for j in range(8)])).to(dev)
+            g = W.agg_create(amg, 0, 4, 8, V)
+            del V
+            ca = {"operator": "4x4 aggregates, k = 8 (16 x 16 complex blocks, 9-point stencil), %d coarse sites, "
+                              "%d right-hand sides" % (g.nc, nrhs)}
+            flops = 8.0 * g.nc * nrhs * 9 * 256
+            byts = g.nc * (9 * 256 * 8 + 2 * nrhs * 16 * 8)
+            for name, kern in (("cuda_cores_fp32", W.WL_AGG_FP32), ("tensor_cores_3xtf32", W.WL_AGG_TC),
+                               ("tensor_cores_tf32", W.WL_AGG_TC1)):
+                ms = W.agg_time_apply(g, nrhs, kern, 20)
+                ca[name] = {"ms": round(ms, 4), "tflops": round(flops / (ms * 1e-3) / 1e12, 2),
+                            "gbs": round(byts / (ms * 1e-3) / 1e9, 1), "frac_hbm": round(byts / (ms * 1e-3) / 1e9 / hbm, 4)}
+            ca["algorithmic"] = {"flops": int(flops), "bytes": int(byts)}
+            g.close()
+            out["coarse_apply"] = ca
+        except Exception as e:  # reported, never silently replaced
+            out["coarse_apply"] = {"error": repr(e)}
+
     # CPU baseline: the oracle on the host cores, after the GPU's timed region (nothing else
     # runs meanwhile), on the GPU's exported hierarchy; two builds: one thread with the
     # lexicographic Kaczmarz ordering, and every core with the 16-colour ordering.  The
@@ -514,7 +552,7 @@ def run_serving(args, rank, dev, W, torch):
             return {"unavailable": "no shift for %s" % nm}
         op = W.wilson_create(torch.from_numpy(w["U"]).to(dev), w["N"], w["m"])
         p = W.amg_params_default(k_r=w["k"], k_e=w["k"], seed=w["seed"], precision=W.WL_FP32, gs_passes=1,
-                                 nu_pre=4, nu_post=4, kacz_order=1, arnoldi_matvec=1)
+                                 nu_pre=4, nu_post=4, kacz_order=1, arnoldi_matvec=1, setup_mu=w["setup_mu"])
         p.levels = len(w["blocks"]) + 1
         for l, b in enumerate(w["blocks"]):
             p.block[l] = b
@@ -589,7 +627,8 @@ def _reference_leg(name, nsolves, tol, out_q):
         from wl_inputs import workload, rhs_batch
         O.use_variant("omp")
         w = workload(name)
-        p = O.setup_params(w["blocks"], k_r=w["k"], k_e=w["k"], seed=w["seed"])
+        p = O.setup_params(w["blocks"], k_r=w["k"], k_e=w["k"], seed=w["seed"], mu1=w["setup_mu"][0],
+                           mu2=w["setup_mu"][1])
         t0 = time.time()
         h = O.Hierarchy.setup(w["N"], w["U"], w["m"], p)
         setup_s = time.time() - t0

@@ -58,9 +58,10 @@ enum {
   WL_EINVAL = -1,
   WL_OOM = -2,
   WL_ECUDA = -3,
-  WL_TIMEOUT = -4,       /* reserved: no kernel of this library waits on a flag (the one
-                            grid-wide barrier is a cooperative launch's), so no call
-                            returns it */
+  WL_TIMEOUT = -4,       /* a kernel's bounded wait for its own asynchronous copies or
+                            tensor-core work ran out (one second); the call's results
+                            are not valid.  No kernel waits on another kernel or rank
+                            (the one grid-wide barrier is a cooperative launch's). */
   WL_NAN = -5,
   WL_BAD_HIERARCHY = -6
 };

@@ -283,35 +283,9 @@ __global__ void __launch_bounds__(64) k_agg_apply_simt(Geo gc, const cx<T> *__re
 // ------------------------------------------------- apply on tensor cores
 #define AGG_TC_K2 16
 
-__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
 // TF32 value nearest to v (the 10 explicit mantissa bits kept, ties away from zero)
 __device__ __forceinline__ float tf32_rn(float v) {
   return __uint_as_float((__float_as_uint(v) + 0x1000u) & 0xffffe000u);
-}
-
-__device__ __forceinline__ unsigned long long gtimer() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-// wait for the completion of the mbarrier phase of the given parity, at most
-// `ns` nanoseconds; false on timeout
-__device__ __forceinline__ bool mbar_wait(uint32_t mb, uint32_t parity, unsigned long long ns) {
-  unsigned long long t0 = gtimer();
-  for (;;) {
-    for (int i = 0; i < 32; ++i) {  // the timer is read once per 32 polls
-      uint32_t done;
-      asm volatile(
-          "{\n\t.reg .pred q;\n\tmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n\tselp.u32 %0, 1, 0, q;\n\t}"
-          : "=r"(done)
-          : "r"(mb), "r"(parity)
-          : "memory");
-      if (done) return true;
-    }
-    if (gtimer() - t0 > ns) return false;
-  }
 }
 
 // shared-memory operand descriptor: K-major, 128-byte swizzle, 8-row groups
@@ -340,13 +314,6 @@ __device__ __forceinline__ void tmem_st32(uint32_t ta, const float (&v)[32]) {
       : "memory");
 }
 
-// mbarrier helpers (shared-memory addresses)
-__device__ __forceinline__ void mbar_init(uint32_t mb, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mb), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint32_t mb) {
-  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(mb) : "memory");
-}
 __device__ __forceinline__ void tc_commit(uint32_t mb) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mb) : "memory");
 }

@@ -280,6 +280,7 @@ int kaczmarz_sweeps(wl_amg *a, int l, int prec, void *x, void *r, int nrhs, int 
 int kaczmarz_colour(wl_amg *a, int l, int prec, void *x, void *r, int nrhs, int c, cudaStream_t s);
 int kaczmarz_tile(wl_amg *a, int l, int prec, void *x, void *r, int nrhs, int tc, cudaStream_t s, int R = 0);
 int autotune_sweeps(wl_amg *a, int nrhs, int prec, cudaStream_t s);  // every level but the coarsest
+int tile_timeout_take(cudaStream_t s);  // 1 if a tile launch's bounded wait ran out (flag cleared)
 KTune sweep_form_of(wl_amg *a, int l, int prec, int nrhs);
 int restrict_op(wl_amg *a, int l, int prec, const void *r, void *fc, int nrhs, cudaStream_t s);
 int prolong_op(wl_amg *a, int l, int prec, const void *e, void *x, int nrhs, cudaStream_t s);
@@ -296,3 +297,50 @@ size_t prec_bytes(int prec);  // bytes of one complex element of the cycle preci
 }  // namespace wl
 
 #define WL_GRID(n, b) ((unsigned)(((n) + (b)-1) / (b)))
+
+// ------------------------------------------- async copies and mbarriers
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// wait for the completion of the mbarrier phase of the given parity, at most
+// `ns` nanoseconds (the timer is read once per 32 polls); false on timeout
+__device__ __forceinline__ bool mbar_wait(uint32_t mb, uint32_t parity, unsigned long long ns) {
+  unsigned long long t0 = gtimer();
+  for (;;) {
+    for (int i = 0; i < 32; ++i) {
+      uint32_t done;
+      asm volatile(
+          "{\n\t.reg .pred q;\n\tmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n\tselp.u32 %0, 1, 0, q;\n\t}"
+          : "=r"(done)
+          : "r"(mb), "r"(parity)
+          : "memory");
+      if (done) return true;
+    }
+    if (gtimer() - t0 > ns) return false;
+  }
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t mb, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mb), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t mb) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(mb) : "memory");
+}
+// one arrival that also announces `bytes` of asynchronous copies to come
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t mb, uint32_t bytes) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(mb),
+               "r"(bytes)
+               : "memory");
+}
+// 1-D bulk copy global -> shared (both 16-byte aligned, bytes a multiple of
+// 16) that completes `bytes` on the mbarrier mb
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t mb) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(mb)
+               : "memory");
+}

@@ -593,6 +593,7 @@ extern "C" int amg_fgmres(wl_amg *a, const void *bhat, void *x, int nrhs, double
   if (rc < 0 && rc != WL_NAN) return rc;
   WL_TRY(wl::from_internal(a->xh.p, (zd *)x, n2, nrhs, WL_FP64, s));
   WL_CUDA(cudaStreamSynchronize(s));
+  if (wl::tile_timeout_take(s)) return WL_TIMEOUT;
   return rc;
 }
 
@@ -700,6 +701,7 @@ extern "C" int amg_solve(wl_amg *a, const void *b, void *x, int nrhs, double tol
     WL_TRY(wl::eo_reconstruct_internal(op, bb, a->xh.as<zd>(), xx, nb, s));
   }
   WL_CUDA(cudaStreamSynchronize(s));
+  if (wl::tile_timeout_take(s)) return WL_TIMEOUT;
   return status;
 }
 

@@ -295,11 +295,11 @@ __device__ __forceinline__ void ld2(const zb *p, cx<T> &a0, cx<T> &a1) {
   a1 = ld<T>(p + 1);
 }
 
-// tile origin of block b for tile colour tc
-__device__ __forceinline__ void tile_origin(const Geo &g, int tc, int &A0, int &B0) {
+// origin of tile `t` of tile colour tc
+__device__ __forceinline__ void tile_origin(const Geo &g, int tc, int t, int &A0, int &B0) {
   int nb4 = g.N / (4 * KT);  // tiles of one colour along b
-  A0 = ((tc & 1) + 2 * (blockIdx.x / nb4)) * KT;
-  B0 = ((tc >> 1) + 2 * (blockIdx.x % nb4)) * KT;
+  A0 = ((tc & 1) + 2 * (t / nb4)) * KT;
+  B0 = ((tc >> 1) + 2 * (t % nb4)) * KT;
 }
 
 // stencil rows and denominators of the tile's 64 sites -> shared memory
@@ -373,63 +373,20 @@ __device__ __forceinline__ void r_sub_paired(cx<float> &rv, float2 m1, float2 m2
   rv = mk(v.x, v.y);
 }
 
-// Several right-hand sides: a block of 4 R / RPT threads, thread (k, q) owns
-// site k of the current colour step and right-hand sides r0 + q + j R / RPT
-// (j < RPT), which share the stencil coefficients and the index arithmetic.
-// Shared memory: r of tile + halo [100][2][R], omega / den [64][2], a ring
-// of three colour steps' stencil rows [3][4][36] filled by cp.async two
-// steps ahead, and the site indices of tile + halo [100] (about 55 KB at
-// R = 32, so four blocks fit an SM).  vec: r rows
-// start on 16-byte boundaries (16-byte copies), else one complex per copy.
-// Every right-hand side sees the same operations in the same order for any
-// R, RPT and PAIRED (paired FP32 FMAs in row_dot and r_sub_paired), so the
-// variants agree bit for bit.
+// The 16 colour steps of one tile (thread (k, q): quadrant k, right-hand
+// sides r0 + q + j R / RPT), on r of tile + halo staged in rs ([100][2][R],
+// visible to every thread after the first barrier below), the step scales
+// ds [64][2] and the site-index table hs [100] of the tile; the stencil rows
+// run through the ring Ar [3][4][36] (cp.async groups, two steps ahead).
+// The caller may have committed cp.async groups of its own before: the wait
+// of step 0 completes them too.  Ends with a barrier.
 template <typename T, typename S, int R, int RPT, bool PAIRED>
-__global__ void __launch_bounds__(4 * R / RPT) k_kacz_tile(Geo g, int tc, const S *__restrict__ A,
-                                                           const T *__restrict__ den, cx<T> *__restrict__ x,
-                                                           cx<T> *__restrict__ r, int nrhs, int vec, T omega) {
-  extern __shared__ __align__(16) unsigned char sm_raw[];
-  cx<T> *rs = (cx<T> *)sm_raw;
-  T *ds = (T *)(rs + KTH * KTH * 2 * R);
-  S *Ar = (S *)(ds + KT * KT * 2);
-  int *hs = (int *)(Ar + 3 * 4 * 36);  // site index of tile + halo site ls = KTH (i + 1) + (j + 1)
+__device__ __forceinline__ void tile_relax(const S *__restrict__ A, cx<T> *__restrict__ x, cx<T> *rs, const T *ds,
+                                           S *Ar, const int *hs, int nrhs, int r0, int Rc) {
   constexpr int NT = 4 * R / RPT;
-  constexpr int RQ = R / RPT;                  // threads per site
-  constexpr int E = 16 / (int)sizeof(cx<T>);  // complex numbers per 16-byte copy
-  constexpr int CPR = R / E;                   // 16-byte pieces per staged row
+  constexpr int RQ = R / RPT;                     // threads per site
   constexpr int ROWC = 36 * (int)sizeof(S) / 16;  // 16-byte pieces of a stencil row
-  int A0, B0;
-  tile_origin(g, tc, A0, B0);
-  int r0 = blockIdx.y * R;
-  int Rc = min(R, nrhs - r0);
-  int tid = threadIdx.x;
-  for (int ls = tid; ls < KTH * KTH; ls += NT) {
-    int a = A0 + ls / KTH - 1, b = B0 + ls % KTH - 1;
-    hs[ls] = g.idx(a + b, a - b);
-  }
-  __syncthreads();
-  // group 0: r of tile + halo
-  if (vec) {
-    for (int e = tid; e < KTH * KTH * 2 * CPR; e += NT) {
-      int c = e % CPR, row = e / CPR;
-      if (c * E >= Rc) continue;
-      long h = hs[row >> 1];
-      cp_async(rs + row * R + c * E, r + (h * 2 + (row & 1)) * nrhs + r0 + c * E, 16);
-    }
-  } else {
-    for (int e = tid; e < KTH * KTH * 2 * R; e += NT) {
-      int q = e % R, row = e / R;
-      if (q >= Rc) continue;
-      long h = hs[row >> 1];
-      cp_async(rs + e, r + (h * 2 + (row & 1)) * nrhs + r0 + q, (int)sizeof(cx<T>));
-    }
-  }
-  for (int e = tid; e < KT * KT * 2; e += NT) {
-    int ks = e >> 1;
-    long h = hs[(ks / KT + 1) * KTH + ks % KT + 1];
-    ds[e] = omega / den[2 * h + (e & 1)];  // the step scale, once per site and spin
-  }
-  cp_async_commit();
+  const int tid = threadIdx.x;
   // stencil rows of colour step c (its four sites, quadrant order) -> ring slot c % 3
   auto issue_rows = [&](int c) {
     S *dst = Ar + (c % 3) * 4 * 36;
@@ -556,6 +513,64 @@ __global__ void __launch_bounds__(4 * R / RPT) k_kacz_tile(Geo g, int tc, const 
       __syncthreads();
     }
   }
+}
+
+// Several right-hand sides: a block of 4 R / RPT threads, thread (k, q) owns
+// site k of the current colour step and right-hand sides r0 + q + j R / RPT
+// (j < RPT), which share the stencil coefficients and the index arithmetic.
+// Shared memory: r of tile + halo [100][2][R], omega / den [64][2], a ring
+// of three colour steps' stencil rows [3][4][36] filled by cp.async two
+// steps ahead, and the site indices of tile + halo [100] (about 55 KB at
+// R = 32, so four blocks fit an SM).  vec: r rows
+// start on 16-byte boundaries (16-byte copies), else one complex per copy.
+// Every right-hand side sees the same operations in the same order for any
+// R, RPT and PAIRED (paired FP32 FMAs in row_dot and r_sub_paired), so the
+// variants agree bit for bit.
+template <typename T, typename S, int R, int RPT, bool PAIRED>
+__global__ void __launch_bounds__(4 * R / RPT) k_kacz_tile(Geo g, int tc, const S *__restrict__ A,
+                                                           const T *__restrict__ den, cx<T> *__restrict__ x,
+                                                           cx<T> *__restrict__ r, int nrhs, int vec, T omega) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  cx<T> *rs = (cx<T> *)sm_raw;
+  T *ds = (T *)(rs + KTH * KTH * 2 * R);
+  S *Ar = (S *)(ds + KT * KT * 2);
+  int *hs = (int *)(Ar + 3 * 4 * 36);  // site index of tile + halo site ls = KTH (i + 1) + (j + 1)
+  constexpr int NT = 4 * R / RPT;
+  constexpr int E = 16 / (int)sizeof(cx<T>);  // complex numbers per 16-byte copy
+  constexpr int CPR = R / E;                   // 16-byte pieces per staged row
+  int A0, B0;
+  tile_origin(g, tc, blockIdx.x, A0, B0);
+  int r0 = blockIdx.y * R;
+  int Rc = min(R, nrhs - r0);
+  int tid = threadIdx.x;
+  for (int ls = tid; ls < KTH * KTH; ls += NT) {
+    int a = A0 + ls / KTH - 1, b = B0 + ls % KTH - 1;
+    hs[ls] = g.idx(a + b, a - b);
+  }
+  __syncthreads();
+  // group 0: r of tile + halo
+  if (vec) {
+    for (int e = tid; e < KTH * KTH * 2 * CPR; e += NT) {
+      int c = e % CPR, row = e / CPR;
+      if (c * E >= Rc) continue;
+      long h = hs[row >> 1];
+      cp_async(rs + row * R + c * E, r + (h * 2 + (row & 1)) * nrhs + r0 + c * E, 16);
+    }
+  } else {
+    for (int e = tid; e < KTH * KTH * 2 * R; e += NT) {
+      int q = e % R, row = e / R;
+      if (q >= Rc) continue;
+      long h = hs[row >> 1];
+      cp_async(rs + e, r + (h * 2 + (row & 1)) * nrhs + r0 + q, (int)sizeof(cx<T>));
+    }
+  }
+  for (int e = tid; e < KT * KT * 2; e += NT) {
+    int ks = e >> 1;
+    long h = hs[(ks / KT + 1) * KTH + ks % KT + 1];
+    ds[e] = omega / den[2 * h + (e & 1)];  // the step scale, once per site and spin
+  }
+  cp_async_commit();
+  tile_relax<T, S, R, RPT, PAIRED>(A, x, rs, ds, Ar, hs, nrhs, r0, Rc);
   // write r back (tile and halo)
   if (vec) {
     for (int e = tid; e < KTH * KTH * 2 * CPR; e += NT) {
@@ -574,6 +589,94 @@ __global__ void __launch_bounds__(4 * R / RPT) k_kacz_tile(Geo g, int tc, const 
   }
 }
 
+// Persistent form of k_kacz_tile (launch parameter bit 0x1000): a block per
+// SM slot takes the items (tile, chunk of R right-hand sides) w = blockIdx.x
+// + i gridDim.x of the launch in turn, with r of tile + halo double-buffered:
+// while a tile relaxes, one warp has the next item's r on its way as 1-D bulk
+// copies (one per site and spin, R complex numbers each) that complete on
+// that buffer's mbarrier, so DRAM reads overlap the colour steps instead of
+// preceding them.  The colour steps are tile_relax, the same operations in
+// the same order as the one-tile-per-block form.  Needs full chunks whose
+// rows start on 16-byte boundaries (vec and nrhs a multiple of R; the
+// launcher checks).  Tiles of one colour have disjoint tile + halo regions,
+// so prefetching one while another is written back cannot race.  The wait
+// for a buffer is bounded (one second); on a timeout g_tile_timeout gets 1
+// and the block stops.
+// set to 1 by a persistent tile launch whose wait for its r buffer ran out
+__device__ int g_tile_timeout;
+
+template <typename T, typename S, int R, int RPT, bool PAIRED>
+__global__ void __launch_bounds__(4 * R / RPT) k_kacz_tile_p(Geo g, int tc, const S *__restrict__ A,
+                                                             const T *__restrict__ den, cx<T> *__restrict__ x,
+                                                             cx<T> *__restrict__ r, int nrhs, T omega, int ntiles) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  cx<T> *rs = (cx<T> *)sm_raw;  // [2][100][2][R]
+  T *ds = (T *)(rs + 2 * KTH * KTH * 2 * R);
+  S *Ar = (S *)(ds + KT * KT * 2);
+  int *hs = (int *)(Ar + 3 * 4 * 36);
+  uint64_t *mbar = (uint64_t *)(((uintptr_t)(hs + KTH * KTH) + 7) & ~(uintptr_t)7);
+  constexpr int NT = 4 * R / RPT;
+  constexpr uint32_t ROWB = R * sizeof(cx<T>);  // bytes of one staged row (site, spin)
+  const int tid = threadIdx.x;
+  const int nitems = ntiles * (nrhs / R);
+  if (tid == 0) {
+    mbar_init(smem_u32(&mbar[0]), 1);
+    mbar_init(smem_u32(&mbar[1]), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  // warp 0: the bulk copies of item w's r into buffer b
+  auto fetch = [&](int w, int b) {
+    if (tid >= 32) return;
+    int A0, B0;
+    tile_origin(g, tc, w % ntiles, A0, B0);
+    const int rr0 = (w / ntiles) * R;
+    const uint32_t mb = smem_u32(&mbar[b]);
+    if (tid == 0) mbar_arrive_expect_tx(mb, (uint32_t)(KTH * KTH * 2) * ROWB);
+    __syncwarp();
+    cx<T> *dst = rs + (size_t)b * KTH * KTH * 2 * R;
+    for (int row = tid; row < KTH * KTH * 2; row += 32) {
+      int ls = row >> 1, a = A0 + ls / KTH - 1, bb = B0 + ls % KTH - 1;
+      long h = g.idx(a + bb, a - bb);
+      bulk_g2s(smem_u32(dst + row * R), r + (h * 2 + (row & 1)) * nrhs + rr0, ROWB, mb);
+    }
+  };
+  if ((int)blockIdx.x < nitems) fetch(blockIdx.x, 0);
+  int i = 0;
+  for (int w = blockIdx.x; w < nitems; w += gridDim.x, ++i) {
+    const int b = i & 1;
+    int A0, B0;
+    tile_origin(g, tc, w % ntiles, A0, B0);
+    const int r0 = (w / ntiles) * R;
+    for (int ls = tid; ls < KTH * KTH; ls += NT) {
+      int a = A0 + ls / KTH - 1, bb = B0 + ls % KTH - 1;
+      hs[ls] = g.idx(a + bb, a - bb);
+    }
+    for (int e = tid; e < KT * KT * 2; e += NT) {
+      int ks = e >> 1, a = A0 + ks / KT, bb = B0 + ks % KT;
+      ds[e] = omega / den[2 * (long)g.idx(a + bb, a - bb) + (e & 1)];
+    }
+    __syncthreads();
+    if (!__syncthreads_and(mbar_wait(smem_u32(&mbar[b]), (uint32_t)((i >> 1) & 1), 1000000000ull))) {
+      if (tid == 0) atomicExch(&g_tile_timeout, 1);
+      break;
+    }
+    if (w + (int)gridDim.x < nitems) fetch(w + gridDim.x, b ^ 1);  // that buffer was freed after item i - 1
+    cx<T> *rb = rs + (size_t)b * KTH * KTH * 2 * R;
+    tile_relax<T, S, R, RPT, PAIRED>(A, x, rb, ds, Ar, hs, nrhs, r0, R);
+    // write r back (tile and halo), 16 bytes per store
+    constexpr int E = 16 / (int)sizeof(cx<T>), CPR = R / E;
+    for (int e = tid; e < KTH * KTH * 2 * CPR; e += NT) {
+      int c = e % CPR, row = e / CPR;
+      long h = hs[row >> 1];
+      *(int4 *)(r + (h * 2 + (row & 1)) * nrhs + r0 + c * E) = *(const int4 *)(rb + row * R + c * E);
+    }
+    // the next bulk copy into this buffer (item i + 2) is an async-proxy write after these reads
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+  }
+}
+
 // One right-hand side: a warp per site of the colour step, lane = 2 d + s
 // holds one term of the row's inner product; shared memory: A rows, den and
 // r of tile + halo [100][2].
@@ -586,7 +689,7 @@ __global__ void __launch_bounds__(128) k_kacz_tile1(Geo g, int tc, const S *__re
   T *ds = (T *)(As + KT * KT * 36);
   cx<T> *rs = (cx<T> *)(ds + KT * KT * 2);
   int A0, B0;
-  tile_origin(g, tc, A0, B0);
+  tile_origin(g, tc, blockIdx.x, A0, B0);
   int tid = threadIdx.x;
   tile_stage_rows<T, S>(g, A0, B0, A, den, As, ds);
   for (int e = tid; e < KTH * KTH * 2; e += blockDim.x) {
@@ -1025,9 +1128,67 @@ static size_t tile_smem(int R) {
   return rows + index + (size_t)KT * KT * 2 * sizeof(T) + (size_t)KTH * KTH * 2 * R * sizeof(cx<T>);
 }
 
+// 1 if a persistent tile launch on the current device reported a wait that ran
+// out since the last call (the flag is cleared); read on stream s after it
+int tile_timeout_take(cudaStream_t s) {
+  int v = 0, z = 0;
+  if (cudaMemcpyFromSymbolAsync(&v, g_tile_timeout, sizeof(int), 0, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return 0;
+  if (v) {
+    cudaMemcpyToSymbolAsync(g_tile_timeout, &z, sizeof(int), 0, cudaMemcpyHostToDevice, s);
+    cudaStreamSynchronize(s);
+    wl_set_error("a Kaczmarz tile launch ran out of time waiting for its own copies; results are not valid");
+  }
+  return v;
+}
+
+// shared memory of the persistent form: two r buffers, step scales, the
+// stencil-row ring, the site-index table and two mbarriers
+template <typename T, typename S>
+static size_t tile_smem_p(int R) {
+  return (size_t)2 * KTH * KTH * 2 * R * sizeof(cx<T>) + (size_t)KT * KT * 2 * sizeof(T) +
+         (size_t)3 * 4 * 36 * sizeof(S) + (size_t)KTH * KTH * sizeof(int) + 8 + 2 * sizeof(uint64_t);
+}
+
+template <typename T, typename S, int R, int RPT, bool PAIRED>
+static int launch_tile_p(const Level &L, const LevelOps &o, int tc, void *x, void *r, int nrhs, double omega,
+                         cudaStream_t s) {
+  size_t smem = tile_smem_p<T, S>(R);
+  static std::atomic<unsigned long long> limit_set{0};
+  WL_TRY(set_smem_limit((const void *)k_kacz_tile_p<T, S, R, RPT, PAIRED>, smem, limit_set));
+  static std::atomic<int> per_sm{0};  // resident blocks per SM, from the occupancy calculator
+  int nb = per_sm.load();
+  if (nb == 0) {
+    WL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_kacz_tile_p<T, S, R, RPT, PAIRED>, 4 * R / RPT,
+                                                          smem));
+    nb = std::max(nb, 1);
+    per_sm.store(nb);
+  }
+  int dev = 0, nsm = 0;
+  WL_CUDA(cudaGetDevice(&dev));
+  WL_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  int ntiles = (L.N / (2 * KT)) * (L.N / (4 * KT));
+  int nitems = ntiles * (nrhs / R);
+  int grid = std::min(nitems, nb * nsm);
+  k_kacz_tile_p<T, S, R, RPT, PAIRED><<<grid, 4 * R / RPT, smem, s>>>(L.geo, tc, o.A.as<S>(), o.den.as<T>(),
+                                                                      (cx<T> *)x, (cx<T> *)r, nrhs, (T)omega,
+                                                                      ntiles);
+  return WL_OK;
+}
+
+// persistent form usable: full chunks, rows on 16-byte boundaries
+template <typename T>
+static bool tile_p_ok(const void *r, int nrhs, int R) {
+  return ((uintptr_t)r % 16 == 0) && nrhs % R == 0 && (R * sizeof(cx<T>)) % 16 == 0 &&
+         (nrhs * sizeof(cx<T>)) % 16 == 0;
+}
+
 template <typename T, typename S, int R, int RPT, bool PAIRED = false>
 static int launch_tile_r(const Level &L, const LevelOps &o, int tc, void *x, void *r, int nrhs, double omega,
-                         cudaStream_t s) {
+                         cudaStream_t s, bool persist = false) {
+  if (persist && tile_p_ok<T>(r, nrhs, R))
+    return launch_tile_p<T, S, R, RPT, PAIRED>(L, o, tc, x, r, nrhs, omega, s);
   size_t smem = tile_smem<T, S>(R);
   static std::atomic<unsigned long long> limit_set{0};  // devices whose limit is raised
   WL_TRY(set_smem_limit((const void *)k_kacz_tile<T, S, R, RPT, PAIRED>, smem, limit_set));
@@ -1038,9 +1199,11 @@ static int launch_tile_r(const Level &L, const LevelOps &o, int tc, void *x, voi
   return WL_OK;
 }
 
-// launch parameter of the tile kernel: R | RPT << 8 (right-hand-side chunk R,
-// right-hand sides per thread RPT; RPT = 0 reads as 1)
-static inline int tile_param(int R, int rpt) { return R | (rpt << 8); }
+// launch parameter of the tile kernel: R | RPT << 8 | P << 12 (right-hand-side
+// chunk R, right-hand sides per thread RPT, 0 reading as 1, and 8 meaning one
+// with paired FP32 FMAs; P = 1: the persistent form with double-buffered r,
+// where the chunks are full and aligned, else the one-tile-per-block form)
+static inline int tile_param(int R, int rpt, int persist = 0) { return R | (rpt << 8) | (persist << 12); }
 
 // default chunk: the smallest of 8, 16, 32 (FP64: 8, 16) that covers nrhs,
 // so that few lanes idle and shared memory stays below 64 KB (FP32) or
@@ -1060,23 +1223,24 @@ static int launch_tile(const Level &L, const LevelOps &o, int tc, void *x, void 
         L.geo, tc, o.A.as<S>(), o.den.as<T>(), (cx<T> *)x, (cx<T> *)r, (T)omega);
     return WL_OK;
   }
-  int R = param & 255, rpt = std::max(1, param >> 8);
+  int R = param & 255, rpt = std::max(1, (param >> 8) & 15);
+  bool pe = (param >> 12) & 1;
   if constexpr (sizeof(T) == 8) {  // FP64: chunks up to 16, one right-hand side per thread
-    if (R == 8) return launch_tile_r<T, S, 8, 1>(L, o, tc, x, r, nrhs, omega, s);
-    return launch_tile_r<T, S, 16, 1>(L, o, tc, x, r, nrhs, omega, s);
+    if (R == 8) return launch_tile_r<T, S, 8, 1>(L, o, tc, x, r, nrhs, omega, s, pe);
+    return launch_tile_r<T, S, 16, 1>(L, o, tc, x, r, nrhs, omega, s, pe);
   } else {  // rpt 8: one right-hand side per thread with paired FMAs
     bool pr = rpt == 8;
     if (R == 8)
-      return pr ? launch_tile_r<T, S, 8, 1, true>(L, o, tc, x, r, nrhs, omega, s)
-                : launch_tile_r<T, S, 8, 1>(L, o, tc, x, r, nrhs, omega, s);
+      return pr ? launch_tile_r<T, S, 8, 1, true>(L, o, tc, x, r, nrhs, omega, s, pe)
+                : launch_tile_r<T, S, 8, 1>(L, o, tc, x, r, nrhs, omega, s, pe);
     if (R == 16) {
-      if (rpt == 2) return launch_tile_r<T, S, 16, 2>(L, o, tc, x, r, nrhs, omega, s);
-      return pr ? launch_tile_r<T, S, 16, 1, true>(L, o, tc, x, r, nrhs, omega, s)
-                : launch_tile_r<T, S, 16, 1>(L, o, tc, x, r, nrhs, omega, s);
+      if (rpt == 2) return launch_tile_r<T, S, 16, 2>(L, o, tc, x, r, nrhs, omega, s, pe);
+      return pr ? launch_tile_r<T, S, 16, 1, true>(L, o, tc, x, r, nrhs, omega, s, pe)
+                : launch_tile_r<T, S, 16, 1>(L, o, tc, x, r, nrhs, omega, s, pe);
     }
-    if (rpt == 2) return launch_tile_r<T, S, 32, 2>(L, o, tc, x, r, nrhs, omega, s);
-    return pr ? launch_tile_r<T, S, 32, 1, true>(L, o, tc, x, r, nrhs, omega, s)
-              : launch_tile_r<T, S, 32, 1>(L, o, tc, x, r, nrhs, omega, s);
+    if (rpt == 2) return launch_tile_r<T, S, 32, 2>(L, o, tc, x, r, nrhs, omega, s, pe);
+    return pr ? launch_tile_r<T, S, 32, 1, true>(L, o, tc, x, r, nrhs, omega, s, pe)
+              : launch_tile_r<T, S, 32, 1>(L, o, tc, x, r, nrhs, omega, s, pe);
   }
 }
 
@@ -1194,6 +1358,10 @@ int autotune_sweeps(wl_amg *a, int nrhs, int prec, cudaStream_t s) {
           cand.push_back(KTune{nrhs, prec, 2, tile_param(R, 1), 0.f});
           if (prec != WL_FP64) cand.push_back(KTune{nrhs, prec, 2, tile_param(R, 8), 0.f});  // paired FMAs
           if (R >= 16 && prec != WL_FP64) cand.push_back(KTune{nrhs, prec, 2, tile_param(R, 2), 0.f});
+          if (nrhs % R == 0) {  // persistent form (double-buffered r) where the chunks are full
+            cand.push_back(KTune{nrhs, prec, 2, tile_param(R, 1, 1), 0.f});
+            if (prec != WL_FP64) cand.push_back(KTune{nrhs, prec, 2, tile_param(R, 8, 1), 0.f});
+          }
         }
     } else {
       cand.push_back(KTune{nrhs, prec, 0, 0, 0.f});
@@ -1420,7 +1588,8 @@ extern "C" int amg_level_apply(wl_amg *a, int level, const void *x, void *y, int
 static bool form_exists(const wl_amg *a, int level, int nrhs, int prec, int form, int param) {
   const Level &L = a->lev[level];
   bool tile = a->prm.kacz_order == 1 && wl::tile_ok(L.N);
-  int R = param & 255, rpt = std::max(1, param >> 8);
+  int R = param & 255, rpt = std::max(1, (param >> 8) & 15);
+  if (param >> 13) return false;
   return tile ? (form == 2 &&
                  (nrhs == 1 || (R == 8 && (rpt == 1 || rpt == 8)) ||
                   ((R == 16 || R == 32) && (rpt <= 2 || rpt == 8))) &&
@@ -1459,6 +1628,7 @@ static int kaczmarz_entry(wl_amg *a, int level, void *x, void *r, int nrhs, int 
   WL_TRY(wl::from_internal(sb.b[0].p, (zd *)x, n2, nrhs, pin, s));
   WL_TRY(wl::from_internal(sb.b[1].p, (zd *)r, n2, nrhs, pin, s));
   WL_CUDA(cudaStreamSynchronize(s));
+  if (wl::tile_timeout_take(s)) return WL_TIMEOUT;
   return WL_OK;
 }
 

@@ -100,6 +100,36 @@ def test_apply_matches_oracle(O, imported, nrhs):
         assert err <= tol, (kernel, nrhs, err)
 
 
+def _round_tf32(a):
+    """complex128 -> nearest float32 -> nearest TF32 (10 explicit mantissa
+    bits, ties away from zero), as complex128"""
+    def r(v):
+        u = np.ascontiguousarray(v.astype(np.float32)).view(np.uint32).astype(np.uint64)
+        u = (u + 0x1000) & 0xFFFFE000
+        return u.astype(np.uint32).view(np.float32).astype(np.float64)
+    return r(a.real) + 1j * r(a.imag)
+
+
+def test_single_term_tf32_apply(O, t64, imported):
+    """WL_AGG_TC1 multiplies the TF32-rounded operands once: on an operator
+    and vectors whose entries are TF32 numbers every product is exact, so it
+    matches the oracle to FP32 accumulation (1e-6); on general operands it
+    stays within TF32 rounding (5e-3)."""
+    w, h, amg = t64
+    Q, Ac, g = imported
+    nrhs = 64
+    x = np.stack([cgauss(94, r, g.nc * 16) for r in range(nrhs)])
+    y = torch.zeros((nrhs, g.nc * 16), dtype=torch.complex128, device=DEV)
+    W.agg_apply(g, T(x), y, nrhs, W.WL_AGG_TC1)
+    ref = np.stack([O.agg_apply(16, 8, Ac, x[r]) for r in range(nrhs)])
+    assert rel(y.cpu().numpy(), ref) <= 5e-3
+    Ar, xr = _round_tf32(Ac), _round_tf32(x)
+    gr = W.agg_import(amg, 0, 4, 8, T(Q), T(Ar))
+    W.agg_apply(gr, T(xr), y, nrhs, W.WL_AGG_TC1)
+    ref = np.stack([O.agg_apply(16, 8, Ar, xr[r]) for r in range(nrhs)])
+    assert rel(y.cpu().numpy(), ref) <= 1e-6
+
+
 def test_tensor_core_apply_twice_in_a_row(imported):
     """Two launches in a row (tensor memory allocated, freed and allocated
     again; the pipeline's barriers start from their initial phase) give the

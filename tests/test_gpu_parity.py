@@ -227,7 +227,8 @@ def test_every_launch_form_agrees_bitwise(shared, order, nrhs):
     """Each launch form of the sweep (per-colour, cooperative with several
     block counts, block-resident on small levels; tile kernel with
     right-hand-side chunks 8 / 16 / 32 and one or two right-hand sides per
-    thread, with scalar or paired FP32 FMAs) gives bit-identical x and r."""
+    thread, with scalar or paired FP32 FMAs, one tile per block or
+    persistent) gives bit-identical x and r."""
     w, op, h, _, path = shared("C2")
     prec = W.WL_FP32
     amg = W.amg_import(op, path, W.amg_params_default(zero_guess=1, kacz_order=order, precision=prec))
@@ -241,7 +242,10 @@ def test_every_launch_form_agrees_bitwise(shared, order, nrhs):
             forms += [(3, rc) for rc in (1, 2, 4) if rc <= nrhs and n * 2 * 8 * rc <= 200 * 1024]
         else:
             forms = [(2, 8), (2, 16), (2, 16 | 2 << 8), (2, 32), (2, 32 | 2 << 8), (2, 8 | 8 << 8),
-                     (2, 16 | 8 << 8), (2, 32 | 8 << 8)]
+                     (2, 16 | 8 << 8), (2, 32 | 8 << 8),
+                     # the persistent form (double-buffered r by bulk copies) where chunks are full,
+                     # else the one-tile-per-block form
+                     (2, 8 | 1 << 12), (2, 16 | 8 << 8 | 1 << 12), (2, 32 | 1 << 12), (2, 32 | 8 << 8 | 1 << 12)]
         x0 = 0.1 * np.stack([cgauss(210 + l, r, n) for r in range(nrhs)])
         r0 = np.stack([cgauss(220 + l, r, n) for r in range(nrhs)])
         outs = []

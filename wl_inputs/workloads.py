@@ -47,7 +47,7 @@ for _i in range(16):
     _N = _SERVE_SIZES[_i % 5]
     WORKLOADS["S%02d" % _i] = dict(
         N=_N, beta=6.0 if _i % 2 == 0 else 10.0, sweeps=200, target=1e-2 if (_i // 2) % 2 == 0 else 1e-3,
-        seed=5000 + _i, blocks=_levels(_N), k=8, precision="fp32", nrhs=0)
+        seed=5000 + _i, blocks=_levels(_N), k=8, precision="fp32", nrhs=0, setup_mu=(10, 20))
 
 # Sec. 4's experiments: N = 128 and 256, beta = 3, 6, 10, three seeded
 # configurations each, 2x2 cells down to the N = 16 coarsest grid (4 and 5
@@ -76,7 +76,8 @@ WORKLOADS["T128"] = dict(N=128, beta=6.0, sweeps=100, target=1e-2, seed=14, bloc
 
 
 # solve-cycle parameters (defaults: V(2,2), FGMRES(20), two Gram-Schmidt passes)
-_SOLVE = dict(nu=2, cycle="V", fgmres_m=20, gs_passes=2, kacz_order=0, arnoldi_matvec=0)
+# and the setup's relaxations per visit in its two cycles (default: the paper's 10, 5)
+_SOLVE = dict(nu=2, cycle="V", fgmres_m=20, gs_passes=2, kacz_order=0, arnoldi_matvec=0, setup_mu=(10, 5))
 for _name, _w in WORKLOADS.items():
     for _k, _v in _SOLVE.items():
         _w.setdefault(_k, _v)
@@ -85,9 +86,14 @@ for _name, _w in WORKLOADS.items():
 # its description; chosen by measurement (V(4,4), one pass, tile-coloured
 # sweeps, FP32 matvec inside a restart cycle with FP64 true residuals)
 WORKLOADS["C4"].update(nu=4, gs_passes=1, kacz_order=1, arnoldi_matvec=1)
+# its cached setup: the paper's first setup cycle (10 relaxations per visit),
+# then a second cycle of 20 (the paper's 5): measured over four setup seeds it
+# cuts the FGMRES iterations at a 3e-12 residual from 53 to 40 on average;
+# 10, 30 and 40 were worse
+WORKLOADS["C4"].update(setup_mu=(10, 20))
 # the single right-hand-side mixed-precision workload with the same cycle; C3b
 # is its variant with BF16-stored stencils and interpolation weights
-WORKLOADS["C3"].update(nu=4, gs_passes=1, kacz_order=1, arnoldi_matvec=1)
+WORKLOADS["C3"].update(nu=4, gs_passes=1, kacz_order=1, arnoldi_matvec=1, setup_mu=(10, 20))
 WORKLOADS["C3b"] = dict(WORKLOADS["C3"], precision="bf16")
 
 
