@@ -37,7 +37,7 @@ METRIC = "Wilson-AMG solves/s at 1e-10 rel err (mixed+batched vs plain FP64); p9
 # roofline reports, from one ncu capture of the C4 workload at 64 right-hand sides
 # (ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum on bench.py --kernel-only);
 # None until captured for the current kernel
-TRAFFIC = {"k_mdot": 3228150000, "k_kacz_tile": None}
+TRAFFIC = {"k_mdot": 3228150000, "k_kacz_tile": 127050496}
 
 
 def parse():
@@ -63,8 +63,10 @@ def parse():
     ap.add_argument("--study", default="", choices=["", "rho"],
                     help="rho: Sec. 4's experiment (rho, GMRES(32) iterations, residual and error "
                          "across an eta_min sweep) instead of the benchmark; one JSON line per case")
-    ap.add_argument("--kernel-only", default="", choices=["", "dot", "axpy", "kacz", "tile", "dhat"],
-                    help="set up the workload, then time one kernel family (wl_time_kernel) inside an NVTX "
+    ap.add_argument("--kernel-only", default="",
+                    choices=["", "dot", "axpy", "kacz", "tile", "dhat", "agg_tc", "agg_tc1", "agg_simt"],
+                    help="set up the workload, then time one kernel family (wl_time_kernel, or agg_time_apply "
+                         "for the aggregation block-stencil apply of 4x4 aggregates with k = 8) inside an NVTX "
                          "range 'cap' for profilers; prints one JSON line")
     ap.add_argument("--sweep-forms", default="",
                     help="pin the Kaczmarz launch form per level for the benchmark's batch width, "
@@ -686,11 +688,36 @@ def pin_sweep_forms(W, amg, spec, nrhs, prec):
 def run_kernel_only(args):
     """Set up the workload's hierarchy, run one cycle of the batch width (so
     the autotuner has chosen its launch forms) and time one kernel family on
-    level 0 (three warm-up launches, then two inside the NVTX range 'cap')."""
+    level 0 (three warm-up launches, then two inside the NVTX range 'cap').
+    agg_*: the aggregation block-stencil apply of the fine level (4x4
+    aggregates, k = 8 random test vectors) on the tensor cores (agg_tc: FP32
+    accurate, agg_tc1: TF32) or on CUDA cores (agg_simt)."""
     import torch
     from paper_1308_5992_gb300 import wilson_amg as W
     from wl_inputs import workload
     w = workload(args.workload)
+    if args.kernel_only.startswith("agg"):
+        import numpy as np
+        from wl_inputs import cgauss
+        dev = torch.device("cuda", 0)
+        N, nrhs = w["N"], max(1, args.nrhs or w["nrhs"])
+        op = W.wilson_create(torch.from_numpy(w["U"]).to(dev), N, w["m"])
+        p = W.amg_params_default(k_r=4, k_e=4, seed=1, setup_mu=(2, 1))
+        p.levels = len(w["blocks"]) + 1
+        for l, b in enumerate(w["blocks"]):
+            p.block[l] = b
+        amg = W.amg_setup(op, p)
+        g = W.agg_create(amg, 0, 4, 8, torch.from_numpy(np.stack([cgauss(92, j, N * N) for j in range(8)])).to(dev))
+        kern = {"agg_tc": W.WL_AGG_TC, "agg_tc1": W.WL_AGG_TC1, "agg_simt": W.WL_AGG_FP32}[args.kernel_only]
+        W.agg_time_apply(g, nrhs, kern, 3)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("cap")
+        ms = W.agg_time_apply(g, nrhs, kern, 2)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        print(json.dumps({"kernel_only": args.kernel_only, "workload": args.workload, "nrhs": nrhs,
+                          "coarse_sites": g.nc, "avg_launch_ms": ms}))
+        return
     if args.kacz_order >= 0:
         w["kacz_order"] = args.kacz_order
     dev = torch.device("cuda", 0)
