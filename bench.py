@@ -53,6 +53,9 @@ def parse():
     ap.add_argument("--serve-configs", type=int, default=16,
                     help="resident configurations S00.. of the serving mix (16 = all five lattice sizes)")
     ap.add_argument("--serve-hbm-gb", type=float, default=160.0, help="device-memory budget of the server")
+    ap.add_argument("--serving-only", action="store_true", help="run the serving leg alone (one JSON line)")
+    ap.add_argument("--serve-setup-mu", default="",
+                    help="override the serving mix's setup relaxations per visit, 'mu1,mu2'")
     ap.add_argument("--tol", type=float, default=3e-12,
                     help="relative residual at which a right-hand side counts as solved (3e-12 gives solutions "
                          "within 1e-10 relative error on the default workload; the line reports the error)")
@@ -553,8 +556,9 @@ def run_serving(args, rank, dev, W, torch):
         if w["m"] is None:
             return {"unavailable": "no shift for %s" % nm}
         op = W.wilson_create(torch.from_numpy(w["U"]).to(dev), w["N"], w["m"])
+        mu = tuple(int(v) for v in args.serve_setup_mu.split(",")) if args.serve_setup_mu else w["setup_mu"]
         p = W.amg_params_default(k_r=w["k"], k_e=w["k"], seed=w["seed"], precision=W.WL_FP32, gs_passes=1,
-                                 nu_pre=4, nu_post=4, kacz_order=1, arnoldi_matvec=1, setup_mu=w["setup_mu"])
+                                 nu_pre=4, nu_post=4, kacz_order=1, arnoldi_matvec=1, setup_mu=mu)
         p.levels = len(w["blocks"]) + 1
         for l, b in enumerate(w["blocks"]):
             p.block[l] = b
@@ -602,11 +606,13 @@ def run_serving(args, rank, dev, W, torch):
     W.srv_drain(srv)
     wall = time.perf_counter() - tstart
     lats, solved, worst = [], 0, 0.0
-    for rid, nr, x in live:
+    its = {}
+    for (rid, nr, x), (c, _, _) in zip(live, reqs):
         done, info, lat = W.srv_poll(srv, rid, nr)
         lats.append(lat)
         solved += nr
         worst = max([worst] + [i["true_relres"] for i in info])
+        its.setdefault(cfgs[c][0], []).extend(i["iters"] for i in info)
     lats.sort()
     srv.close()
     return {"configs": ["%s:%dx%d" % (nm, w["N"], w["N"]) for nm, w, _ in cfgs], "requests": len(lats),
@@ -616,7 +622,9 @@ def run_serving(args, rank, dev, W, torch):
             "solves_per_s": round(solved / wall, 2), "true_relres_max": worst,
             "cycle": "V(4,4) FP32 tile-coloured Kaczmarz, FGMRES(20) FP64 (FP32 Arnoldi matvec), 1 Gram-Schmidt "
                      "pass", "slots_per_config": slots,
-            "hbm_budget_gb": args.serve_hbm_gb, "hbm_reserved_gb": round(reserved / (1 << 30), 2)}
+            "hbm_budget_gb": args.serve_hbm_gb, "hbm_reserved_gb": round(reserved / (1 << 30), 2),
+            "setup_mu": list(mu), "tol": args.tol,
+            "mean_iters_by_config": {k: round(sum(v) / len(v), 1) for k, v in sorted(its.items())}}
 
 
 def _reference_leg(name, nsolves, tol, out_q):
@@ -844,6 +852,14 @@ def main():
     if args.study == "rho":
         if rank == 0:
             run_study_rho(args)
+        return
+    if args.serving_only:
+        if rank == 0:
+            import torch
+            from paper_1308_5992_gb300 import wilson_amg as W
+            dev = torch.device("cuda", 0)
+            torch.cuda.set_device(dev)
+            print(json.dumps({"serving": run_serving(args, 0, dev, W, torch)}))
         return
     if world > 1:
         import torch

@@ -47,7 +47,7 @@ for _i in range(16):
     _N = _SERVE_SIZES[_i % 5]
     WORKLOADS["S%02d" % _i] = dict(
         N=_N, beta=6.0 if _i % 2 == 0 else 10.0, sweeps=200, target=1e-2 if (_i // 2) % 2 == 0 else 1e-3,
-        seed=5000 + _i, blocks=_levels(_N), k=8, precision="fp32", nrhs=0, setup_mu=(10, 20))
+        seed=5000 + _i, blocks=_levels(_N), k=8, precision="fp32", nrhs=0)
 
 # Sec. 4's experiments: N = 128 and 256, beta = 3, 6, 10, three seeded
 # configurations each, 2x2 cells down to the N = 16 coarsest grid (4 and 5
