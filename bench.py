@@ -34,10 +34,10 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Wilson-AMG solves/s at 1e-10 rel err (mixed+batched vs plain FP64); p99 ms"
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the kernels the
-# roofline reports, from one ncu capture of the C4 workload at 64 right-hand sides
-# (ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum on bench.py --kernel-only);
-# None until captured for the current kernel
-TRAFFIC = {"k_mdot": 3228150000, "k_kacz_tile": 127050496}
+# roofline reports, by (kernel, right-hand sides per launch), from one ncu capture each of the
+# C4 workload (ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum on bench.py
+# --kernel-only); None until captured for the current kernel
+TRAFFIC = {("k_mdot", 64): 3228150000, ("k_kacz_tile", 64): 127050496, ("k_kacz_tile", 32): 55873536}
 
 
 def parse():
@@ -275,7 +275,8 @@ def run_gb300(args, rank, world, local_rank):
                                  cycle=W.WL_CYCLE_W if w["cycle"] == "W" else W.WL_CYCLE_V,
                                  fgmres_m=w["fgmres_m"], gs_passes=w["gs_passes"],
                                  kacz_order=0 if plain else w["kacz_order"],
-                                 arnoldi_matvec=0 if plain else w["arnoldi_matvec"])
+                                 arnoldi_matvec=0 if plain else w["arnoldi_matvec"],
+                                 overlap=0 if plain else w["overlap"])
         p.levels = len(w["blocks"]) + 1
         for l, b in enumerate(w["blocks"]):
             p.block[l] = b
@@ -301,7 +302,10 @@ def run_gb300(args, rank, world, local_rank):
             raise RuntimeError("solve did not converge: %s" % info)
         return info
 
-    pin_sweep_forms(W, amg, args.sweep_forms, nrhs, prec)
+    # right-hand sides per solve lane: with overlap the batch runs as two concurrent halves,
+    # so every kernel of the step is launched at that width
+    lane = (nrhs + 1) // 2 if w["overlap"] and nrhs >= 32 else nrhs
+    pin_sweep_forms(W, amg, args.sweep_forms, lane, prec)
     for _ in range(args.warmup):
         step(amg, b, x, nrhs)
 
@@ -371,8 +375,9 @@ def run_gb300(args, rank, world, local_rank):
     # kernel first (28 % of kernel time on level 0, 37 % over levels 0 and 1), then the
     # FP64 Gram-Schmidt update k_maxpy and the multi-dots k_mdot; with the 16-colour
     # ordering k_mdot and the colour passes lead.
+    # Every kernel is timed at the width the timed step launches it (lane right-hand sides).
     n0 = N * N // 2
-    E = 2 * n0 * nrhs
+    E = 2 * n0 * lane
     hbm, src = peaks()
     eb = 16 if prec == W.WL_FP64 else 8          # bytes of one complex value of the cycle
     sb = 16 if prec == W.WL_FP64 else (8 if prec == W.WL_FP32 else 4)  # stencil storage
@@ -380,17 +385,23 @@ def run_gb300(args, rank, world, local_rank):
     # clock x 2 flop x 2070 MHz = 1259 GFLOP/s); one launch computes kc = 11 conjugate dot
     # products of length E = 2 n0 nrhs complex numbers, 8 flop per complex term
     kc = 11
-    dot_ms = W.wl_time_kernel(amg, W.WL_K_GS_DOT, 0, nrhs, prec, 20)
+    dot_ms = W.wl_time_kernel(amg, W.WL_K_GS_DOT, 0, lane, prec, 20)
     fp64_peak = 152 * 2 * 2 * 2070e6 / 1e9
     dot_gflops = 8.0 * kc * E / (dot_ms * 1e-3) / 1e9
+    # the derived peak checked in this run: the library's FP64 FMA probe (8 blocks of 256
+    # threads per SM, 8 independent chains of 4096 FMAs per thread)
+    fma_ms = W.wl_time_kernel(amg, W.WL_K_FP64_FMA, 0, lane, prec, 5)
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    fma_gflops = nsm * 8 * 256 * 8 * 4096 * 2 / (fma_ms * 1e-3) / 1e9
     roof_dot = {"kernel": "k_mdot<double> (Gram-Schmidt, 11 dots)", "bound": "alu", "achieved": round(dot_gflops, 1),
                 "peak": round(fp64_peak, 1), "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz",
-                "unit": "GFLOP/s", "frac": round(dot_gflops / fp64_peak, 4), "traffic": TRAFFIC.get("k_mdot"),
+                "fp64_fma_probe_gflops": round(fma_gflops, 1), "frac_of_probe": round(dot_gflops / fma_gflops, 4),
+                "unit": "GFLOP/s", "frac": round(dot_gflops / fp64_peak, 4), "traffic": TRAFFIC.get(("k_mdot", lane)),
                 "avg_launch_ms": round(dot_ms, 4), "algorithmic_flops": int(8 * kc * E)}
     # k_kacz: one colour pass (1/16 of the sites): r read and written on 9/16 of the sites,
     # x on 1/16, stencil rows and denominators of 1/16 of the sites (each operand once)
-    kacz_ms = W.wl_time_kernel(amg, W.WL_K_KACZ, 0, nrhs, prec, 160)
-    kacz_bytes = n0 * nrhs * (9 / 16 * 2 * 2 * eb + 1 / 16 * 2 * 2 * eb) + n0 / 16 * (36 * sb + 2 * (eb // 2))
+    kacz_ms = W.wl_time_kernel(amg, W.WL_K_KACZ, 0, lane, prec, 160)
+    kacz_bytes = n0 * lane * (9 / 16 * 2 * 2 * eb + 1 / 16 * 2 * 2 * eb) + n0 / 16 * (36 * sb + 2 * (eb // 2))
     achieved = kacz_bytes / (kacz_ms * 1e-3) / 1e9
     roof_kacz = {"kernel": "k_kacz (fine level, one of 16 colour passes)", "bound": "hbm",
                  "achieved": round(achieved, 1), "peak": hbm, "peak_source": src, "unit": "GB/s",
@@ -401,21 +412,23 @@ def run_gb300(args, rank, world, local_rank):
     # written once (4 x 2 spins x 8 B = 64 B in FP32), plus the site's links and column
     # norms (40 B) shared by the right-hand sides; the kernel itself reads the explicit
     # 9-point stencil row (288 B) in place of the links, so its own count is higher
-    tile_ms = W.wl_time_kernel(amg, W.WL_K_KACZ_TILE, 0, nrhs, prec, 80)
-    tile_bytes = n0 / 4 * (nrhs * 2 * 2 * eb * 2 + 40 * (eb // 8))
-    tile_bytes_stencil = n0 / 4 * (nrhs * 2 * 2 * eb * 2 + 36 * sb + 2 * (eb // 2))
-    achieved = tile_bytes / (tile_ms * 1e-3) / 1e9
-    roof_tile = {"kernel": "k_kacz_tile (fine level, one of 4 tile colours)", "bound": "hbm",
-                 "achieved": round(achieved, 1), "peak": hbm, "peak_source": src, "unit": "GB/s",
-                 "frac": round(achieved / hbm, 4), "traffic": TRAFFIC.get("k_kacz_tile"),
-                 "avg_launch_ms": round(tile_ms, 5), "algorithmic_bytes": int(tile_bytes),
-                 "bytes_per_site_per_rhs": 64, "bytes_per_site": 40,
-                 "achieved_with_stencil_rows": round(tile_bytes_stencil / (tile_ms * 1e-3) / 1e9, 1)}
+    def roof_tile_at(width):  # at a width the step runs, so with the launch form it tuned or pinned
+        ms = W.wl_time_kernel(amg, W.WL_K_KACZ_TILE, 0, width, prec, 80)
+        tb = n0 / 4 * (width * 2 * 2 * eb * 2 + 40 * (eb // 8))
+        tbs = n0 / 4 * (width * 2 * 2 * eb * 2 + 36 * sb + 2 * (eb // 2))
+        ach = tb / (ms * 1e-3) / 1e9
+        return {"kernel": "k_kacz_tile (fine level, one of 4 tile colours), %d RHS" % width, "bound": "hbm",
+                "achieved": round(ach, 1), "peak": hbm, "peak_source": src, "unit": "GB/s",
+                "frac": round(ach / hbm, 4), "traffic": TRAFFIC.get(("k_kacz_tile", width)),
+                "avg_launch_ms": round(ms, 5), "algorithmic_bytes": int(tb), "nrhs": width,
+                "bytes_per_site_per_rhs": 64, "bytes_per_site": 40,
+                "achieved_with_stencil_rows": round(tbs / (ms * 1e-3) / 1e9, 1)}
+    roof_tile = roof_tile_at(lane)
     # k_stencil on level 0 (residual f - A x with the 9-point Dhat stencil; the same gather
     # computes the FP32 Arnoldi matvec): x read once (its 9 neighbours come from cache), f
     # read, y written, the stencil row (36 complex) read once per site
-    st_ms = W.wl_time_kernel(amg, W.WL_K_STENCIL, 0, nrhs, prec, 40)
-    st_bytes = n0 * (nrhs * 2 * 3 * eb + 36 * sb)
+    st_ms = W.wl_time_kernel(amg, W.WL_K_STENCIL, 0, lane, prec, 40)
+    st_bytes = n0 * (lane * 2 * 3 * eb + 36 * sb)
     achieved = st_bytes / (st_ms * 1e-3) / 1e9
     roof_st = {"kernel": "k_stencil (fine level, residual f - Dhat x)", "bound": "hbm",
                "achieved": round(achieved, 1), "peak": hbm, "peak_source": src, "unit": "GB/s",
@@ -436,13 +449,14 @@ def run_gb300(args, rank, world, local_rank):
                                "%d grids, blocks %s, k=%d, setup relaxations %s, %d RHS/step, %s(%d,%d) %s "
                                "Kaczmarz cycle in %s, FGMRES(%d) with %d Gram-Schmidt pass(es) in FP64, Arnoldi "
                                "matvec %s, FP64 true residual at restarts, relative residual %g (error vs exact "
-                               "in rel_err_vs_exact)"
+                               "in rel_err_vs_exact), %s"
                                % (args.workload, N, N, w["beta"], w["sweeps"], w["m"], w["target"],
                                   len(w["blocks"]) + 1, w["blocks"], w["k"], list(w["setup_mu"]), nrhs, w["cycle"],
                                   w["nu"], w["nu"], ["16-colour", "tile-coloured (8x8 tiles)"][w["kacz_order"]],
                                   ["fp64", "fp32", "fp32+bf16-storage"][prec], w["fgmres_m"], w["gs_passes"],
-                                  "fp32" if w["arnoldi_matvec"] and prec != W.WL_FP64 else "fp64", TOL),
-                   "tol": TOL,
+                                  "fp32" if w["arnoldi_matvec"] and prec != W.WL_FP64 else "fp64", TOL,
+                                  "two concurrent solve lanes of %d RHS" % lane if lane < nrhs else "one solve lane"),
+                   "tol": TOL, "rhs_per_lane": lane,
                    "nrhs": nrhs, "L": N, "precision": ["fp64", "fp32", "fp32_bf16"][prec],
                    "l2": "flushed (256 MB write) between timed steps", "parallelism": "replicas"},
         "iters_mean": round(sum(iters) / len(iters), 2), "iters_max": max(iters),
@@ -452,8 +466,50 @@ def run_gb300(args, rank, world, local_rank):
         "plain_fp64_single_rhs": {"value": round(1e3 / (sorted(p64)[1]), 3), "unit": "solves/s",
                                   "ms": sorted(p64)[1], "iters": inf64[0]["iters"]},
         "e2e": e2e, "gpu_launches": int(launches), "roofline": roof, "roofline_more": roof_more, "clocks": clk,
-        "sweep_forms": [list(W.amg_sweep_form(amg, l, nrhs, prec)) for l in range(len(w["blocks"]))],
+        "sweep_forms": [list(W.amg_sweep_form(amg, l, lane, prec)) for l in range(len(w["blocks"]))],
     }
+    # The other single-configuration workloads, beside the headline: C3 (this lattice, one
+    # right-hand side, the same FP32 cycle on the same hierarchy) and C2 (128x128, the plain
+    # FP64 method with one right-hand side: the plain-method GPU baseline); solves/s at the
+    # same tolerance, each solve timed with CUDA events after warm-up
+    if args.workload == "C4" and rank == 0:
+        def time_solves(amg_, bb, reps):
+            xx = torch.zeros_like(bb)
+            for _ in range(2):
+                step(amg_, bb, xx, 1)
+            ts, its = [], []
+            for _ in range(reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                inf = step(amg_, bb, xx, 1)
+                e1.record()
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+                its.append(inf[0]["iters"])
+            ts.sort()
+            return {"value": round(1e3 / ts[len(ts) // 2], 3), "unit": "solves/s", "ms_p50": round(ts[len(ts) // 2], 3),
+                    "iters": its[0]}
+        extra = {"C3": dict(time_solves(amg, b[:1].contiguous(), 5),
+                            workload="512x512, 1 RHS, FP32 V(4,4) tile-coloured cycle in FP64 FGMRES(20), "
+                                     "the C4 hierarchy")}
+        try:
+            w2 = workload("C2")
+            op2 = W.wilson_create(torch.from_numpy(w2["U"]).to(dev), w2["N"], w2["m"])
+            p2 = W.amg_params_default(k_r=w2["k"], k_e=w2["k"], seed=w2["seed"], zero_guess=1, precision=W.WL_FP64)
+            p2.levels = len(w2["blocks"]) + 1
+            for l, bk in enumerate(w2["blocks"]):
+                p2.block[l] = bk
+            amg2 = W.amg_setup(op2, p2)
+            b2 = torch.from_numpy(rhs_batch(w2["N"], 1, 100)).to(dev)
+            extra["C2"] = dict(time_solves(amg2, b2, 10),
+                               workload="128x128, beta=6, smallest |eig| 1e-3, 3 grids (4x4, 2x2), k=8, FP64 "
+                                        "V(2,2) 16-colour cycle, FGMRES(20) with two Gram-Schmidt passes, 1 RHS")
+            amg2.close()
+            op2.close()
+        except Exception as e:  # reported, never silently replaced
+            extra["C2"] = {"error": repr(e)}
+        out["other_workloads"] = extra
+
     # Aggregation coarse space (Sec. 4's "more interpolation variables per coarse point"):
     # the 9-point stencil of 16 x 16 blocks of 4 x 4 aggregates with k = 8 spin-split test
     # vectors of this lattice (8192 coarse sites), applied to this batch's 64 right-hand

@@ -107,6 +107,14 @@ typedef struct {
                              (Sec. 4.2: each grid visited once, mu 2^l relaxations
                              before and after the coarse visit on grid l, one coarsest
                              eigensolve per setup cycle) */
+  int overlap;            /* 1: amg_solve splits a batch of at least 32 right-hand sides
+                             into two halves solved at the same time on two streams (a
+                             second workspace and graph set that share the hierarchy's
+                             operators, made on first use), so that one half's FP64
+                             Gram-Schmidt runs beside the other half's FP32 cycle.  Each
+                             right-hand side computes what it computes alone (results
+                             agree with overlap = 0 up to the rounding of batch-width-
+                             dependent reductions). */
 } amg_params;
 
 typedef struct {
@@ -332,7 +340,11 @@ enum {
   WL_K_COARSEST = 5,  /* dense FP64 coarsest solve                            */
   WL_K_GS_DOT = 6,    /* FP64 multi-dot of 11 Krylov vectors (Gram-Schmidt)   */
   WL_K_GS_AXPY = 7,   /* FP64 multi-axpy of 11 Krylov vectors                 */
-  WL_K_KACZ_TILE = 8  /* one tile-colour launch (a quarter of a tile-coloured sweep) on `level` */
+  WL_K_KACZ_TILE = 8, /* one tile-colour launch (a quarter of a tile-coloured sweep) on `level` */
+  WL_K_FP64_FMA = 9   /* not an operator kernel: the FP64 FMA throughput of the device, 8 blocks
+                         of 256 threads per SM, each thread 8 independent chains of 4096
+                         dependent FMAs (2 flop each); level, nrhs and prec are checked as for
+                         the other kinds and otherwise unused */
 };
 /* Average duration (host output, milliseconds) of one launch of kernel
  * family `kind` in the launch configuration the solver uses for `nrhs`

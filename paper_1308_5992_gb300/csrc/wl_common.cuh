@@ -181,10 +181,18 @@ extern "C" long long wl_launch_count(void);
 struct DBuf {
   void *p = nullptr;
   size_t bytes = 0;
+  bool own = true;  // false: a view of another object's buffer, never freed or grown here
   int alloc(size_t b);
   void release();
   template <typename T>
   T *as() const { return (T *)p; }
+  DBuf view() const {
+    DBuf v;
+    v.p = p;
+    v.bytes = bytes;
+    v.own = false;
+    return v;
+  }
 };
 
 // ------------------------------------------------------------ host objects
@@ -252,6 +260,9 @@ struct wl_amg {
     cudaGraphExec_t exec;
   };
   std::vector<G> graphs;
+  // second solve lane (amg_params.overlap): a hierarchy that views this one's
+  // operators and has its own stream, workspace and graphs; created on demand
+  wl_amg *twin = nullptr;
 };
 
 // --------------------------------------------------------- internal C++ API
@@ -266,6 +277,7 @@ void amg_retain(wl_amg *a);
 void amg_release(wl_amg *a);
 int enter(wl_op *op);  // work stream waits for everything queued on the caller's stream
 int ensure_workspace(wl_amg *a, int nrhs, int prec);
+wl_amg *make_twin(wl_amg *a);  // the second solve lane of a (nullptr on failure, error set)
 int level_ops_build_copies(wl_amg *a);
 int coarsest_invert(wl_amg *a);
 int cycle_run(wl_amg *a, int nrhs, int prec, cudaStream_t s);  // lev[0].f -> lev[0].x

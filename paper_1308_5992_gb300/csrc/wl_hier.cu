@@ -312,8 +312,70 @@ int hier_finish(wl_amg *a) {
   return WL_OK;
 }
 
+// The second solve lane of a: a hierarchy object whose operator data (links,
+// level stencils, denominators, interpolation weights, coarsest inverse) are
+// views of a's, with a stream, an event, a workspace and cycle graphs of its
+// own.  Its operator's "caller" stream is a's work stream, so work queued on
+// the twin first waits for everything queued on a's stream.  a owns the twin
+// and frees it before its own buffers.
+wl_amg *make_twin(wl_amg *a) {
+  wl_op *src = a->op;
+  wl_op *o = new wl_op();
+  o->N = src->N;
+  o->m = src->m;
+  o->c = src->c;
+  o->device = src->device;
+  o->geo = src->geo;
+  o->gauge_hash = src->gauge_hash;
+  o->user = src->stream;
+  o->stream = nullptr;
+  o->ev = nullptr;
+  if (cudaStreamCreateWithFlags(&o->stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&o->ev, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    wl_set_error("second solve lane: cannot create a stream or an event");
+    if (o->ev) cudaEventDestroy(o->ev);
+    if (o->stream) cudaStreamDestroy(o->stream);
+    delete o;
+    return nullptr;
+  }
+  o->Uf64 = src->Uf64.view();
+  o->Uf32 = src->Uf32.view();
+  wl_amg *t = new wl_amg();
+  t->op = o;
+  t->prm = a->prm;
+  t->prm.overlap = 0;
+  t->L = a->L;
+  for (int l = 0; l < a->L; ++l) {
+    const Level &S = a->lev[l];
+    Level &D = t->lev[l];
+    D.N = S.N;
+    D.B = S.B;
+    D.n = S.n;
+    D.geo = S.geo;
+    const LevelOps *so[3] = {&S.op64, &S.op32, &S.opbf};
+    LevelOps *dn[3] = {&D.op64, &D.op32, &D.opbf};
+    for (int q = 0; q < 3; ++q) {
+      dn[q]->A = so[q]->A.view();
+      dn[q]->den = so[q]->den.view();
+      dn[q]->P = so[q]->P.view();
+    }
+  }
+  t->Ainv = a->Ainv.view();
+  t->Ainv32 = a->Ainv32.view();
+  t->nc = a->nc;
+  t->cap = 0;
+  t->cap_prec = a->cap_prec;
+  t->h_small = nullptr;
+  return t;
+}
+
 void amg_free(wl_amg *a) {
   if (!a) return;
+  if (a->twin) {  // views a's buffers: goes first
+    amg_release(a->twin);
+    a->twin = nullptr;
+  }
   if (a->op && a->op->stream) cudaStreamSynchronize(a->op->stream);
   release_graphs(a);
   for (int l = 0; l < 8; ++l) {

@@ -10,6 +10,9 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
+#include <string>
+#include <thread>
 #include <vector>
 
 #include "wl_common.cuh"
@@ -674,6 +677,96 @@ extern "C" int amg_rho(wl_amg *a, const void *x0, void *x, int nrhs, double tol,
   return (left || diverged) ? WL_NOT_CONVERGED : WL_OK;
 }
 
+// reduce, FGMRES, reconstruct for n right-hand sides on the lane L (its own
+// stream and workspace); returns the fgmres_run status or an error
+static int solve_lane(wl_amg *L, const zd *bb, zd *xx, int n, double tol, wl_info *info) {
+  wl_op *op = L->op;
+  cudaStream_t s = op->stream;
+  WL_TRY(wl::ensure_workspace(L, n, L->prm.precision));
+  WL_TRY(wl::eo_reduce_internal(op, bb, L->bh.as<zd>(), n, s));
+  if (L->prm.zero_guess)
+    WL_CUDA(cudaMemsetAsync(L->xh.p, 0, sizeof(zd) * (size_t)L->lev[0].n * 2 * n, s));
+  else
+    WL_TRY(wl::take_even_internal(op, xx, L->xh.as<zd>(), n, s));
+  int rc = wl::fgmres_run(L, L->bh.as<zd>(), L->xh.as<zd>(), n, tol, info);
+  if (rc < 0 && rc != WL_NAN) return rc;
+  WL_TRY(wl::eo_reconstruct_internal(op, bb, L->xh.as<zd>(), xx, n, s));
+  WL_CUDA(cudaStreamSynchronize(s));
+  return rc;
+}
+
+static int combine(int a, int b) {
+  if (a == WL_NAN || b == WL_NAN) return WL_NAN;
+  return (a || b) ? WL_NOT_CONVERGED : WL_OK;
+}
+
+// two halves of the batch at the same time: the first on a's stream in this
+// thread, the second on the twin's stream in a second host thread (both
+// drive their own FGMRES, with their own host synchronisations), so one
+// half's FP64 Gram-Schmidt kernels can share the GPU with the other half's
+// FP32 cycle
+static int solve_two_lanes(wl_amg *a, const zd *bb, zd *xx, int nb, double tol, wl_info *info) {
+  if (!a->twin) {
+    a->twin = wl::make_twin(a);
+    if (!a->twin) return WL_ECUDA;
+  }
+  wl_amg *t = a->twin;
+  int keep_cap = t->cap;
+  t->prm = a->prm;
+  t->prm.overlap = 0;
+  t->cap = keep_cap;
+  const int h0 = (nb + 1) / 2, h1 = nb - h0, prec = a->prm.precision;
+  const size_t fs = (size_t)a->op->N * a->op->N * 2;
+  // Workspaces, launch forms and cycle graphs of both lanes are made here,
+  // before the second thread starts, so that neither lane times kernels or
+  // captures a graph while the other one runs.  The twin takes a's launch
+  // forms for its width (measured on a, or pinned there) unless it already
+  // holds a graph of that width.
+  WL_TRY(wl::ensure_workspace(a, h0, prec));
+  WL_TRY(wl::cycle_prepare(a, h0, prec, a->op->stream, nullptr));
+  if (h1 != h0) WL_TRY(wl::autotune_sweeps(a, h1, prec, a->op->stream));
+  bool t_has_graph = false;
+  for (const auto &g : t->graphs) t_has_graph |= (g.nrhs == h1 && g.prec == prec);
+  if (!t_has_graph)
+    for (int l = 0; l < a->L; ++l) {
+      std::vector<KTune> &tv = t->lev[l].tune;
+      for (const KTune &k : a->lev[l].tune) {
+        if (k.nrhs != h1 || k.prec != prec) continue;
+        bool set = false;
+        for (KTune &q : tv)
+          if (q.nrhs == h1 && q.prec == prec && (q.form == 2) == (k.form == 2)) {
+            q = k;
+            set = true;
+          }
+        if (!set) tv.push_back(k);
+      }
+    }
+  WL_TRY(wl::enter(t->op));  // the twin's stream waits for a's (which waits for the caller's)
+  WL_TRY(wl::ensure_workspace(t, h1, prec));
+  WL_TRY(wl::cycle_prepare(t, h1, prec, t->op->stream, nullptr));
+  int rc1 = WL_OK;
+  std::string err1;
+  std::thread th([&] {
+    if (cudaSetDevice(t->op->device) != cudaSuccess) {
+      rc1 = WL_ECUDA;
+      err1 = "second solve lane: cudaSetDevice failed";
+      return;
+    }
+    rc1 = solve_lane(t, bb + h0 * fs, xx + h0 * fs, h1, tol, info ? info + h0 : nullptr);
+    if (rc1 < 0 && rc1 != WL_NAN) err1 = wl_last_error();
+  });
+  int rc0 = solve_lane(a, bb, xx, h0, tol, info);
+  th.join();
+  if (rc1 < 0 && rc1 != WL_NAN) {
+    wl_set_error("%s", err1.c_str());
+    return rc1;
+  }
+  if (rc0 < 0 && rc0 != WL_NAN) return rc0;
+  if (rc0 == WL_NAN || rc1 == WL_NAN)
+    wl_set_error("non-finite residual for some right-hand sides");
+  return combine(rc0, rc1);
+}
+
 extern "C" int amg_solve(wl_amg *a, const void *b, void *x, int nrhs, double tol, wl_info *info) {
   if (!a || !b || !x || nrhs < 1 || !(tol > 0)) {
     wl_set_error("amg_solve: invalid argument");
@@ -686,19 +779,12 @@ extern "C" int amg_solve(wl_amg *a, const void *b, void *x, int nrhs, double tol
   int status = WL_OK;
   for (int r0 = 0; r0 < nrhs; r0 += MAX_BATCH) {
     int nb = std::min(MAX_BATCH, nrhs - r0);
-    WL_TRY(wl::ensure_workspace(a, nb, a->prm.precision));
     const zd *bb = (const zd *)b + (size_t)r0 * N * N * 2;
     zd *xx = (zd *)x + (size_t)r0 * N * N * 2;
-    WL_TRY(wl::eo_reduce_internal(op, bb, a->bh.as<zd>(), nb, s));
-    if (a->prm.zero_guess)
-      WL_CUDA(cudaMemsetAsync(a->xh.p, 0, sizeof(zd) * (size_t)a->lev[0].n * 2 * nb, s));
-    else
-      WL_TRY(wl::take_even_internal(op, xx, a->xh.as<zd>(), nb, s));
-    int rc = wl::fgmres_run(a, a->bh.as<zd>(), a->xh.as<zd>(), nb, tol, info ? info + r0 : nullptr);
+    int rc = (a->prm.overlap && nb >= 32) ? solve_two_lanes(a, bb, xx, nb, tol, info ? info + r0 : nullptr)
+                                          : solve_lane(a, bb, xx, nb, tol, info ? info + r0 : nullptr);
     if (rc < 0 && rc != WL_NAN) return rc;
-    if (rc == WL_NAN || status == WL_NAN) status = WL_NAN;
-    else if (rc) status = rc;
-    WL_TRY(wl::eo_reconstruct_internal(op, bb, a->xh.as<zd>(), xx, nb, s));
+    status = combine(status, rc);
   }
   WL_CUDA(cudaStreamSynchronize(s));
   if (wl::tile_timeout_take(s)) return WL_TIMEOUT;
@@ -706,9 +792,26 @@ extern "C" int amg_solve(wl_amg *a, const void *b, void *x, int nrhs, double tol
 }
 
 // ------------------------------------------------------------ instrumentation
+// FP64 FMA throughput probe: FMA_CHAINS independent chains of FMA_STEPS
+// dependent FMAs per thread (v <- v b + c with 0 < b < 1, so every value
+// stays finite); the one conditional store keeps the chains live.
+constexpr int FMA_CHAINS = 8, FMA_STEPS = 4096, FMA_BLOCKS_PER_SM = 8;
+__global__ void __launch_bounds__(256) k_fp64_fma(double *out, double b, double c) {
+  double v[FMA_CHAINS];
+#pragma unroll
+  for (int i = 0; i < FMA_CHAINS; ++i) v[i] = 1e-3 * threadIdx.x + i;
+  for (int it = 0; it < FMA_STEPS; ++it)
+#pragma unroll
+    for (int i = 0; i < FMA_CHAINS; ++i) v[i] = fma(v[i], b, c);
+  double s = 0;
+#pragma unroll
+  for (int i = 0; i < FMA_CHAINS; ++i) s += v[i];
+  if (s == 0.0) out[0] = s;
+}
+
 extern "C" int wl_time_kernel(wl_amg *a, int kind, int level, int nrhs, int prec, int reps, double *avg_ms) {
   if (!a || !avg_ms || nrhs < 1 || nrhs > MAX_BATCH || reps < 1 || level < 0 || level >= a->L ||
-      (prec != WL_FP64 && prec != WL_FP32 && prec != WL_FP32_BF16) || kind < WL_K_DHAT || kind > WL_K_KACZ_TILE ||
+      (prec != WL_FP64 && prec != WL_FP32 && prec != WL_FP32_BF16) || kind < WL_K_DHAT || kind > WL_K_FP64_FMA ||
       ((kind == WL_K_KACZ || kind == WL_K_STENCIL || kind == WL_K_RESTRICT || kind == WL_K_PROLONG ||
         kind == WL_K_KACZ_TILE) &&
        level == a->L - 1)) {
@@ -738,6 +841,13 @@ extern "C" int wl_time_kernel(wl_amg *a, int kind, int level, int nrhs, int prec
         return wl::coarsest_apply(a, prec, a->lev[a->L - 1].f.p, a->lev[a->L - 1].x.p, nrhs, s);
       case WL_K_GS_DOT:
         return wl::mdots<double>(a, a->V.as<zd>(), E, kc, a->w.as<zd>(), E, nrhs, k.hcol, m + 1, 0, k.hpass, s);
+      case WL_K_FP64_FMA: {
+        int nsm = 0;
+        WL_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, a->op->device));
+        k_fp64_fma<<<nsm * FMA_BLOCKS_PER_SM, 256, 0, s>>>((double *)a->w.p, 0.999, 1e-3);
+        wl_count_launches(1);
+        return WL_OK;
+      }
       default:
         k_maxpy<double, 1><<<WL_GRID(E, 256), 256, 0, s>>>(a->V.as<zd>(), E, kc, k.hpass, nrhs, a->w.as<zd>(), E,
                                                             nrhs);

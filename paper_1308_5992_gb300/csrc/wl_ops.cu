@@ -27,6 +27,10 @@ extern "C" long long wl_launch_count(void) { return g_launches.load(std::memory_
 
 int DBuf::alloc(size_t b) {
   if (b <= bytes && p) return WL_OK;
+  if (!own) {
+    wl_set_error("internal: a borrowed buffer of %zu bytes cannot grow to %zu", bytes, b);
+    return WL_EINVAL;
+  }
   release();
   if (b == 0) return WL_OK;
   cudaError_t e = cudaMalloc(&p, b);
@@ -42,9 +46,10 @@ int DBuf::alloc(size_t b) {
 }
 
 void DBuf::release() {
-  if (p) cudaFree(p);
+  if (p && own) cudaFree(p);
   p = nullptr;
   bytes = 0;
+  own = true;
 }
 
 // ------------------------------------------------------------- hop algebra

@@ -23,7 +23,7 @@ WL_FP64, WL_FP32, WL_FP32_BF16 = 0, 1, 2
 WL_OP_D, WL_OP_DHAT, WL_OP_Z = 0, 1, 2
 WL_CYCLE_V, WL_CYCLE_W = 0, 1
 (WL_K_DHAT, WL_K_KACZ, WL_K_STENCIL, WL_K_RESTRICT, WL_K_PROLONG, WL_K_COARSEST, WL_K_GS_DOT,
- WL_K_GS_AXPY, WL_K_KACZ_TILE) = range(9)
+ WL_K_GS_AXPY, WL_K_KACZ_TILE, WL_K_FP64_FMA) = range(10)
 WL_AGG_FP64, WL_AGG_FP32, WL_AGG_TC, WL_AGG_TC1 = 0, 1, 2, 3
 
 
@@ -34,7 +34,7 @@ class amg_params(C.Structure):
                 ("max_restarts", C.c_int), ("precision", C.c_int), ("seed", C.c_ulonglong),
                 ("gs_passes", C.c_int), ("zero_guess", C.c_int), ("sweep_kernel", C.c_int),
                 ("kacz_order", C.c_int), ("arnoldi_matvec", C.c_int),
-                ("setup_cycle", C.c_int)]
+                ("setup_cycle", C.c_int), ("overlap", C.c_int)]
 
 
 class wl_info(C.Structure):

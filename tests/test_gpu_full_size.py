@@ -43,7 +43,7 @@ def test_c4_full_size_batch(O, c4):
     op = W.wilson_create(torch.from_numpy(U).to(DEV), N, m)
     p = W.amg_params_default(zero_guess=1, precision=W.WL_FP32, nu_pre=w["nu"], nu_post=w["nu"],
                              fgmres_m=w["fgmres_m"], gs_passes=w["gs_passes"], kacz_order=w["kacz_order"],
-                             arnoldi_matvec=w["arnoldi_matvec"])
+                             arnoldi_matvec=w["arnoldi_matvec"], overlap=w["overlap"])
     amg = W.amg_import(op, path, p)
     nrhs = 64
     b = rhs_batch(N, nrhs, 100)
@@ -70,7 +70,7 @@ def test_c4_full_size_matches_oracle_at_1e13(O, c4):
     op = W.wilson_create(torch.from_numpy(U).to(DEV), N, m)
     p = W.amg_params_default(zero_guess=1, precision=W.WL_FP32, nu_pre=w["nu"], nu_post=w["nu"],
                              fgmres_m=w["fgmres_m"], gs_passes=w["gs_passes"], kacz_order=w["kacz_order"],
-                             arnoldi_matvec=w["arnoldi_matvec"])
+                             arnoldi_matvec=w["arnoldi_matvec"], overlap=w["overlap"])
     amg = W.amg_import(op, path, p)
     nrhs = 64
     b = rhs_batch(N, nrhs, 100)

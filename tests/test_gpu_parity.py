@@ -444,6 +444,49 @@ def test_batch_equals_alone(shared):
         assert np.linalg.norm(H(one[0]) - H(psi[q])) / np.linalg.norm(H(one[0])) <= 1e-10
 
 
+@pytest.mark.parametrize("name,nb,order", [("T64", 40, 0), ("C2", 33, 1)])
+def test_two_lane_solve(O, shared, name, nb, order):
+    """amg_params.overlap: a batch of 40 (33) is solved as two halves of 20
+    and 20 (17 and 16) on two streams at the same time (a second workspace
+    viewing the same operators; with 33 the second lane's width has launch
+    forms of its own, tuned on the first lane and handed over); every
+    right-hand side matches the one-lane solve and the oracle's solve to
+    1e-10, twice in a row (the second call reuses the second lane and its
+    graphs).  The 33-wide case runs the tile-coloured sweeps."""
+    w, op, h, _, path = shared(name)
+    N = w["N"]
+    p1 = W.amg_params_default(zero_guess=1, precision=W.WL_FP32, overlap=1, kacz_order=order)
+    p0 = W.amg_params_default(zero_guess=1, precision=W.WL_FP32, overlap=0, kacz_order=order)
+    a1, a0 = W.amg_import(op, path, p1), W.amg_import(op, path, p0)
+    b = rhs_batch(N, nb, 15)
+    x0 = torch.zeros_like(T(b))
+    rc0, i0 = W.amg_solve(a0, T(b), x0, nb, 1e-13)
+    assert rc0 == W.WL_OK
+    h0 = (nb + 1) // 2
+    for _ in range(2):
+        x1 = torch.zeros_like(T(b))
+        rc1, i1 = W.amg_solve(a1, T(b), x1, nb, 1e-13)
+        assert rc1 == W.WL_OK and all(i["true_relres"] <= 1e-13 for i in i1)
+        assert float((x1 - x0).abs().max() / x0.abs().max()) <= 1e-10
+    for q in (0, h0 - 1, h0, nb - 1):
+        ref, _ = h.solve(b[q], tol=1e-13, order=O.ORDER_TILE if order else O.ORDER_COLOUR)
+        assert np.linalg.norm(H(x1[q]) - ref) / np.linalg.norm(ref) <= 1e-10, q
+
+
+def test_fp64_fma_probe(shared):
+    """wl_time_kernel's FP64 FMA probe (the check on the derived FP64 peak
+    that the Gram-Schmidt roofline uses) runs and reports a rate below the
+    unit-count bound at the top clock (152 SMs x 2 FMA x 2 flop x 2070 MHz,
+    which a probe whose chains were optimised away would exceed) and above a
+    tenth of it."""
+    w, op, h, amg, path = shared("T64")
+    ms = W.wl_time_kernel(amg, W.WL_K_FP64_FMA, 0, 1, W.WL_FP64, 3)
+    nsm = torch.cuda.get_device_properties(DEV).multi_processor_count
+    gflops = nsm * 8 * 256 * 8 * 4096 * 2 / (ms * 1e-3) / 1e9
+    bound = nsm * 2 * 2 * 2.07
+    assert 0.1 * bound <= gflops <= 1.02 * bound, (gflops, bound)
+
+
 def test_gpu_setup_quality(O, ops):
     """The GPU bootstrap setup gives a preconditioner of the same quality as
     the oracle's (iterations within a band) and solutions to 1e-10."""
