@@ -37,7 +37,8 @@ METRIC = "Wilson-AMG solves/s at 1e-10 rel err (mixed+batched vs plain FP64); p9
 # roofline reports, by (kernel, right-hand sides per launch), from one ncu capture each of the
 # C4 workload (ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum on bench.py
 # --kernel-only); None until captured for the current kernel
-TRAFFIC = {("k_mdot", 64): 3228150000, ("k_kacz_tile", 64): 127050496, ("k_kacz_tile", 32): 55873536}
+TRAFFIC = {("k_mdot", 64): 3228150000, ("k_kacz_tile", 64): 127050496, ("k_kacz_tile", 32): 55873536,
+           ("k_mdot_df", 32): 1751391232}
 
 
 def parse():
@@ -63,6 +64,9 @@ def parse():
                     help="timed CPU work per oracle variant (at least one solve each)")
     ap.add_argument("--nrhs", type=int, default=0, help="override the workload's RHS per step")
     ap.add_argument("--kacz-order", type=int, default=-1, help="override the Kaczmarz ordering (0 or 1)")
+    ap.add_argument("--set", default="",
+                    help="override integer solve parameters of the workload, 'key=value,...' (e.g. "
+                         "'overlap=0,gs_arith=1')")
     ap.add_argument("--study", default="", choices=["", "rho"],
                     help="rho: Sec. 4's experiment (rho, GMRES(32) iterations, residual and error "
                          "across an eta_min sweep) instead of the benchmark; one JSON line per case")
@@ -262,6 +266,11 @@ def run_gb300(args, rank, world, local_rank):
         raise SystemExit("no shift for workload %s (run oracle/make_shifts.py)" % args.workload)
     if args.kacz_order >= 0:
         w["kacz_order"] = args.kacz_order
+    for kv in filter(None, args.set.split(",")):
+        key, _, val = kv.partition("=")
+        if key not in w:
+            raise SystemExit("--set: unknown workload parameter %r" % key)
+        w[key] = int(val)
     N, nrhs = w["N"], max(1, args.nrhs or w["nrhs"])
     prec = {"fp64": W.WL_FP64, "fp32": W.WL_FP32, "bf16": W.WL_FP32_BF16}[w["precision"]]
 
@@ -276,7 +285,8 @@ def run_gb300(args, rank, world, local_rank):
                                  fgmres_m=w["fgmres_m"], gs_passes=w["gs_passes"],
                                  kacz_order=0 if plain else w["kacz_order"],
                                  arnoldi_matvec=0 if plain else w["arnoldi_matvec"],
-                                 overlap=0 if plain else w["overlap"])
+                                 overlap=0 if plain else w["overlap"],
+                                 gs_arith=0 if plain else w["gs_arith"])
         p.levels = len(w["blocks"]) + 1
         for l, b in enumerate(w["blocks"]):
             p.block[l] = b
@@ -319,7 +329,9 @@ def run_gb300(args, rank, world, local_rank):
     launches0 = W.wl_launch_count()
     times, infos = [], []
     barrier()
-    torch.cuda.nvtx.range_push("timed")   # profilers select the timed steps by this range
+    # profilers select the timed steps by this range: a start/end range, which (unlike a push/pop
+    # range) covers the kernels every host thread launches, the second solve lane's included
+    timed_range = torch.cuda.nvtx.range_start("timed")
     for _ in range(args.steps):
         flush.fill_(1.0)
         torch.cuda.synchronize()
@@ -329,7 +341,7 @@ def run_gb300(args, rank, world, local_rank):
         e1.record()
         torch.cuda.synchronize()
         times.append(e0.elapsed_time(e1))
-    torch.cuda.nvtx.range_pop()
+    torch.cuda.nvtx.range_end(timed_range)
     barrier()
     launches = W.wl_launch_count() - launches0
     clk = clocks.stop()
@@ -393,11 +405,26 @@ def run_gb300(args, rank, world, local_rank):
     fma_ms = W.wl_time_kernel(amg, W.WL_K_FP64_FMA, 0, lane, prec, 5)
     nsm = torch.cuda.get_device_properties(dev).multi_processor_count
     fma_gflops = nsm * 8 * 256 * 8 * 4096 * 2 / (fma_ms * 1e-3) / 1e9
-    roof_dot = {"kernel": "k_mdot<double> (Gram-Schmidt, 11 dots)", "bound": "alu", "achieved": round(dot_gflops, 1),
-                "peak": round(fp64_peak, 1), "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz",
-                "fp64_fma_probe_gflops": round(fma_gflops, 1), "frac_of_probe": round(dot_gflops / fma_gflops, 4),
-                "unit": "GFLOP/s", "frac": round(dot_gflops / fp64_peak, 4), "traffic": TRAFFIC.get(("k_mdot", lane)),
-                "avg_launch_ms": round(dot_ms, 4), "algorithmic_flops": int(8 * kc * E)}
+    if w["gs_arith"]:
+        # double-float Gram-Schmidt on the FP32 pipes: bound by HBM; the 11 dots run as two
+        # launches (at most 8 per launch), each reading w once: (11 + 2) vectors of E complex
+        # double-floats (16 B)
+        nl = -(-kc // 8)
+        dot_bytes = (kc + nl) * E * 16
+        ach = dot_bytes / (dot_ms * 1e-3) / 1e9
+        roof_dot = {"kernel": "k_mdot_df (double-float Gram-Schmidt, 11 dots in %d launches)" % nl, "bound": "hbm",
+                    "achieved": round(ach, 1), "peak": hbm, "peak_source": src, "unit": "GB/s",
+                    "frac": round(ach / hbm, 4), "traffic": TRAFFIC.get(("k_mdot_df", lane)),
+                    "avg_launch_ms": round(dot_ms, 4), "algorithmic_bytes": int(dot_bytes),
+                    "fp64_equivalent_gflops": round(dot_gflops, 1), "fp64_fma_probe_gflops": round(fma_gflops, 1)}
+    else:
+        roof_dot = {"kernel": "k_mdot<double> (Gram-Schmidt, 11 dots)", "bound": "alu",
+                    "achieved": round(dot_gflops, 1), "peak": round(fp64_peak, 1),
+                    "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz",
+                    "fp64_fma_probe_gflops": round(fma_gflops, 1), "frac_of_probe": round(dot_gflops / fma_gflops, 4),
+                    "unit": "GFLOP/s", "frac": round(dot_gflops / fp64_peak, 4),
+                    "traffic": TRAFFIC.get(("k_mdot", lane)), "avg_launch_ms": round(dot_ms, 4),
+                    "algorithmic_flops": int(8 * kc * E)}
     # k_kacz: one colour pass (1/16 of the sites): r read and written on 9/16 of the sites,
     # x on 1/16, stencil rows and denominators of 1/16 of the sites (each operand once)
     kacz_ms = W.wl_time_kernel(amg, W.WL_K_KACZ, 0, lane, prec, 160)
@@ -443,17 +470,20 @@ def run_gb300(args, rank, world, local_rank):
         "metric": METRIC, "value": round(value, 3), "unit": "solves/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32 cycle + f64 Krylov" if prec != W.WL_FP64 else "f64",
+        "dtype": ("f64" if prec == W.WL_FP64 else
+                  "f32 cycle + f32-pair (double-float) Gram-Schmidt + f64 Hessenberg and true residual"
+                  if w["gs_arith"] else "f32 cycle + f64 Krylov"),
         "data": "synthetic (seeded U(1) Metropolis gauge, complex Gaussian right-hand sides)",
         "config": {"workload": "%s: %dx%d lattice, beta=%g, %d Metropolis sweeps, m=%.6f (smallest |eig| %g), "
                                "%d grids, blocks %s, k=%d, setup relaxations %s, %d RHS/step, %s(%d,%d) %s "
-                               "Kaczmarz cycle in %s, FGMRES(%d) with %d Gram-Schmidt pass(es) in FP64, Arnoldi "
+                               "Kaczmarz cycle in %s, FGMRES(%d) with %d Gram-Schmidt pass(es) in %s, Arnoldi "
                                "matvec %s, FP64 true residual at restarts, relative residual %g (error vs exact "
                                "in rel_err_vs_exact), %s"
                                % (args.workload, N, N, w["beta"], w["sweeps"], w["m"], w["target"],
                                   len(w["blocks"]) + 1, w["blocks"], w["k"], list(w["setup_mu"]), nrhs, w["cycle"],
                                   w["nu"], w["nu"], ["16-colour", "tile-coloured (8x8 tiles)"][w["kacz_order"]],
                                   ["fp64", "fp32", "fp32+bf16-storage"][prec], w["fgmres_m"], w["gs_passes"],
+                                  "double-float" if w["gs_arith"] else "FP64",
                                   "fp32" if w["arnoldi_matvec"] and prec != W.WL_FP64 else "fp64", TOL,
                                   "two concurrent solve lanes of %d RHS" % lane if lane < nrhs else "one solve lane"),
                    "tol": TOL, "rhs_per_lane": lane,
@@ -490,8 +520,9 @@ def run_gb300(args, rank, world, local_rank):
             return {"value": round(1e3 / ts[len(ts) // 2], 3), "unit": "solves/s", "ms_p50": round(ts[len(ts) // 2], 3),
                     "iters": its[0]}
         extra = {"C3": dict(time_solves(amg, b[:1].contiguous(), 5),
-                            workload="512x512, 1 RHS, FP32 V(4,4) tile-coloured cycle in FP64 FGMRES(20), "
-                                     "the C4 hierarchy")}
+                            workload="512x512, 1 RHS, FP32 V(4,4) tile-coloured cycle in FGMRES(20) with "
+                                     "%s Gram-Schmidt, the C4 hierarchy"
+                                     % ("double-float" if w["gs_arith"] else "FP64"))}
         try:
             w2 = workload("C2")
             op2 = W.wilson_create(torch.from_numpy(w2["U"]).to(dev), w2["N"], w2["m"])
@@ -614,7 +645,7 @@ def run_serving(args, rank, dev, W, torch):
         op = W.wilson_create(torch.from_numpy(w["U"]).to(dev), w["N"], w["m"])
         mu = tuple(int(v) for v in args.serve_setup_mu.split(",")) if args.serve_setup_mu else w["setup_mu"]
         p = W.amg_params_default(k_r=w["k"], k_e=w["k"], seed=w["seed"], precision=W.WL_FP32, gs_passes=1,
-                                 nu_pre=4, nu_post=4, kacz_order=1, arnoldi_matvec=1, setup_mu=mu)
+                                 nu_pre=4, nu_post=4, kacz_order=1, arnoldi_matvec=1, setup_mu=mu, gs_arith=1)
         p.levels = len(w["blocks"]) + 1
         for l, b in enumerate(w["blocks"]):
             p.block[l] = b
@@ -676,8 +707,8 @@ def run_serving(args, rank, dev, W, torch):
             "closed-loop capacity)" % (rate, cap), "p50_ms": round(lats[len(lats) // 2], 2),
             "p99_ms": round(lats[min(len(lats) - 1, int(0.99 * len(lats)))], 2),
             "solves_per_s": round(solved / wall, 2), "true_relres_max": worst,
-            "cycle": "V(4,4) FP32 tile-coloured Kaczmarz, FGMRES(20) FP64 (FP32 Arnoldi matvec), 1 Gram-Schmidt "
-                     "pass", "slots_per_config": slots,
+            "cycle": "V(4,4) FP32 tile-coloured Kaczmarz, FGMRES(20) (FP32 Arnoldi matvec, one double-float "
+                     "Gram-Schmidt pass, FP64 true residual)", "slots_per_config": slots,
             "hbm_budget_gb": args.serve_hbm_gb, "hbm_reserved_gb": round(reserved / (1 << 30), 2),
             "setup_mu": list(mu), "tol": args.tol,
             "mean_iters_by_config": {k: round(sum(v) / len(v), 1) for k, v in sorted(its.items())}}
@@ -784,6 +815,11 @@ def run_kernel_only(args):
         return
     if args.kacz_order >= 0:
         w["kacz_order"] = args.kacz_order
+    for kv in filter(None, args.set.split(",")):
+        key, _, val = kv.partition("=")
+        if key not in w:
+            raise SystemExit("--set: unknown workload parameter %r" % key)
+        w[key] = int(val)
     dev = torch.device("cuda", 0)
     N, nrhs = w["N"], max(1, args.nrhs or w["nrhs"])
     prec = {"fp64": W.WL_FP64, "fp32": W.WL_FP32, "bf16": W.WL_FP32_BF16}[w["precision"]]
@@ -791,7 +827,8 @@ def run_kernel_only(args):
             "dhat": W.WL_K_DHAT}[args.kernel_only]
     op = W.wilson_create(torch.from_numpy(w["U"]).to(dev), N, w["m"])
     p = W.amg_params_default(k_r=w["k"], k_e=w["k"], seed=w["seed"], zero_guess=1, precision=prec,
-                             kacz_order=w["kacz_order"])
+                             kacz_order=w["kacz_order"], arnoldi_matvec=w["arnoldi_matvec"],
+                             gs_arith=w["gs_arith"])
     p.levels = len(w["blocks"]) + 1
     for l, b in enumerate(w["blocks"]):
         p.block[l] = b

@@ -115,6 +115,15 @@ typedef struct {
                              right-hand side computes what it computes alone (results
                              agree with overlap = 0 up to the rounding of batch-width-
                              dependent reductions). */
+  int gs_arith;           /* arithmetic of the Gram-Schmidt process (the Krylov basis,
+                             its dots, updates and norms): 0 = FP64; 1 = double-float,
+                             each value an unevaluated sum of two floats (about 48
+                             significant bits) computed on the FP32 pipes with
+                             error-free transformations, the Hessenberg matrix, Givens
+                             rotations and the solution update staying FP64.  Requires
+                             an FP32 or BF16 cycle with arnoldi_matvec = 1 (EINVAL
+                             otherwise).  The true residual at every restart stays
+                             FP64, so the accuracy a solve reaches is unchanged. */
 } amg_params;
 
 typedef struct {

@@ -104,6 +104,40 @@ __device__ __forceinline__ cx<To> widen(cx<From> a) {
   return Widen<To, From>::get(a);
 }
 
+// A complex number held as the unevaluated sum hi + lo of two complex floats
+// (|lo| at most half an ulp of hi, per component): about 48 significant bits
+// carried on the FP32 pipes.  The storage of the Krylov vectors of the
+// Gram-Schmidt process when amg_params.gs_arith = 1.
+struct alignas(16) zdf {
+  zf hi, lo;
+};
+
+// a result computed in cx<T>, stored as Y: itself, widened to zd, or as a
+// double-float with lo = 0 (exact in every case)
+template <typename Y, typename T>
+struct Store;
+template <typename T>
+struct Store<cx<T>, T> {
+  __device__ __forceinline__ static cx<T> get(cx<T> v) { return v; }
+};
+template <>
+struct Store<zd, float> {
+  __device__ __forceinline__ static zd get(zf v) { return widen<double>(v); }
+};
+template <>
+struct Store<zdf, float> {
+  __device__ __forceinline__ static zdf get(zf v) {
+    zdf z;
+    z.hi = v;
+    z.lo = mk(0.f, 0.f);
+    return z;
+  }
+};
+template <typename Y, typename T>
+__device__ __forceinline__ Y store_as(cx<T> v) {
+  return Store<Y, T>::get(v);
+}
+
 // storage of operator coefficients: complex double, complex float or bf16 pair
 struct zb {
   __nv_bfloat162 v;
@@ -285,6 +319,7 @@ int cycle_prepare(wl_amg *a, int nrhs, int prec, cudaStream_t s, const wl_amg::G
 int cycle_direct(wl_amg *a, int nrhs, int prec, cudaStream_t s);
 int dhat_apply_dev(wl_op *op, const void *x, int x_is_f32, zd *y, int nrhs, cudaStream_t s);
 int stencil_apply32_to64(wl_amg *a, const void *x, zd *y, int nrhs, cudaStream_t s);
+int stencil_apply32_to_df(wl_amg *a, const void *x, zdf *y, int nrhs, cudaStream_t s);  // lo = 0
 int stencil_apply(wl_amg *a, int l, int prec, const void *x, void *y, const void *f, int nrhs,
                   cudaStream_t s);
 int kaczmarz_sweeps(wl_amg *a, int l, int prec, void *x, void *r, int nrhs, int sweeps,

@@ -70,7 +70,8 @@ int resolve_levels(int N, amg_params *p, int *Nl) {
   if (p->fgmres_m < 1 || p->fgmres_m > 32 || p->max_restarts < 1 || p->nu_pre < 0 ||
       p->nu_post < 0 || p->gs_passes < 1 || p->gs_passes > 2 || p->sweep_kernel < 0 || p->sweep_kernel > 2 ||
       p->kacz_order < 0 || p->kacz_order > 1 || p->arnoldi_matvec < 0 || p->arnoldi_matvec > 1 ||
-      p->setup_cycle < 0 || p->setup_cycle > 1 ||
+      p->setup_cycle < 0 || p->setup_cycle > 1 || p->gs_arith < 0 || p->gs_arith > 1 ||
+      (p->gs_arith == 1 && (p->precision == WL_FP64 || p->arnoldi_matvec != 1)) ||
       (p->precision != WL_FP64 && p->precision != WL_FP32 && p->precision != WL_FP32_BF16) ||
       (p->cycle != WL_CYCLE_V && p->cycle != WL_CYCLE_W)) {
     wl_set_error("invalid solve parameters");

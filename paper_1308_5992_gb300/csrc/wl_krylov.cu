@@ -39,6 +39,8 @@ struct KS {
   int *active, *stop, *jend, *iters;  // [nrhs]
   int *nanf;                          // [nrhs] non-finite value seen (Arnoldi residual, or masked input)
   int *running;                       // [1]
+  float4 *hpd;   // [m+1][nrhs][2] the coefficients of hpass as double-floats, for k_maxpy_df
+  float2 *invdf; // [nrhs] inv as a double-float (hi, lo)
 };
 
 static KS ks_layout(void *base, int m, int nrhs) {
@@ -69,6 +71,8 @@ static KS ks_layout(void *base, int m, int nrhs) {
   k.iters = (int *)take(sizeof(int) * nrhs);
   k.nanf = (int *)take(sizeof(int) * nrhs);
   k.running = (int *)take(sizeof(int) * 4);
+  k.hpd = (float4 *)take(sizeof(float4) * 2 * nrhs * (m + 1));
+  k.invdf = (float2 *)take(sizeof(float2) * nrhs);
   return k;
 }
 
@@ -228,6 +232,282 @@ __global__ void k_cast(const cx<Ti> *__restrict__ a, cx<To> *__restrict__ b, lon
   if (e < E) b[e] = ccast<To>(a[e]);
 }
 
+// ------------------------------------------------ double-float Gram-Schmidt
+// With amg_params.gs_arith = 1 the Krylov vectors v_j and w are zdf (hi + lo
+// pairs of complex floats) and the Gram-Schmidt dots, updates and norms run
+// on the FP32 pipes, whose rate on this GPU is 64 times the FP64 rate.  The
+// arithmetic is built from two error-free transformations, applied to the
+// (re, im) components of a pair at once through the paired round-to-nearest
+// intrinsics (which the compiler never contracts into other operations):
+//   two_sum (Knuth):  s + e = a + b exactly, six additions;
+//   two_prod (FMA):   p + e = a * b exactly, e = fma(a, b, -p).
+// A product of double-floats keeps hi * hi exactly and the cross terms
+// hi * lo + lo * hi in FP32 (lo * lo, below 2^-48 of the product, is
+// dropped); a running sum is a pair (s, c) renormalised after every step
+// (|c| <= ulp(s) / 2).  Every step is exact to about 2^-47 of its result,
+// against 2^-53 for FP64.
+
+__host__ __device__ __forceinline__ float2 split_df(double v) {
+  float h = (float)v;
+  return make_float2(h, (float)(v - (double)h));
+}
+
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, neg2(b)); }
+__device__ __forceinline__ float2 swap2(float2 a) { return make_float2(a.y, a.x); }
+
+struct DF2 {
+  float2 s, c;  // the value s + c, per component
+};
+
+// s + e = a + b exactly
+__device__ __forceinline__ void two_sum2(float2 a, float2 b, float2 &s, float2 &e) {
+  s = add2(a, b);
+  float2 bv = sub2(s, a);
+  float2 av = sub2(s, bv);
+  e = add2(sub2(a, av), sub2(b, bv));
+}
+
+// (s, c) <- the renormalised pair of s + t, given |t| small against |s|
+__device__ __forceinline__ void renorm2(float2 s, float2 t, DF2 &out) {
+  float2 h = add2(s, t);
+  out.c = sub2(t, sub2(h, s));
+  out.s = h;
+}
+
+// acc += x * y componentwise, x = xh + xl, y = yh + yl
+__device__ __forceinline__ void df_acc(DF2 &acc, float2 xh, float2 xl, float2 yh, float2 yl) {
+  float2 p = __fmul2_rn(xh, yh);
+  float2 e = __ffma2_rn(xh, yh, neg2(p));
+  e = __ffma2_rn(xh, yl, e);
+  e = __ffma2_rn(xl, yh, e);
+  float2 s, t;
+  two_sum2(acc.s, p, s, t);
+  renorm2(s, add2(t, add2(acc.c, e)), acc);
+}
+
+// a += b
+__device__ __forceinline__ void df_add(DF2 &a, DF2 b) {
+  float2 s, t;
+  two_sum2(a.s, b.s, s, t);
+  renorm2(s, add2(t, add2(a.c, b.c)), a);
+}
+
+__device__ __forceinline__ float4 ld4(const zdf *p) { return *(const float4 *)p; }
+__device__ __forceinline__ void st4(zdf *p, float2 h, float2 l) { *(float4 *)p = make_float4(h.x, h.y, l.x, l.y); }
+
+#define KCH_DF 8  // dots per launch of k_mdot_df (registers: two running sums per dot)
+
+// part[b][k][r][0..1] = this block's (A, B) sums for V_k^H w:
+// A = sum (vr wr, vi wi), B = sum (vr wi, vi wr), so that
+// Re = A.x + A.y and Im = B.x - B.y.  Same thread layout as k_mdot.
+template <int KC>
+__global__ void __launch_bounds__(256, 2) k_mdot_df(const zdf *__restrict__ V, long vstride,
+                                                    const zdf *__restrict__ w, long E, int R,
+                                                    float4 *__restrict__ part) {
+  __shared__ float4 sm[2][256];
+  int t = threadIdx.x, nt = blockDim.x;
+  int G = nt / R, q = t / R;
+  DF2 A[KC], B[KC];
+#pragma unroll
+  for (int k = 0; k < KC; ++k) A[k] = B[k] = DF2{make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+  long stride = (long)gridDim.x * nt;
+  for (long e = (long)blockIdx.x * nt + t; e < E; e += stride) {
+    float4 wv = ld4(w + e);
+    float2 wh = make_float2(wv.x, wv.y), wl = make_float2(wv.z, wv.w);
+    float2 sh = swap2(wh), sl = swap2(wl);
+    float4 v[KC];
+#pragma unroll
+    for (int k = 0; k < KC; ++k) v[k] = ld4(V + k * vstride + e);
+#pragma unroll
+    for (int k = 0; k < KC; ++k) {
+      float2 vh = make_float2(v[k].x, v[k].y), vl = make_float2(v[k].z, v[k].w);
+      df_acc(A[k], vh, vl, wh, wl);
+      df_acc(B[k], vh, vl, sh, sl);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < KC; ++k) {
+    sm[0][t] = make_float4(A[k].s.x, A[k].s.y, A[k].c.x, A[k].c.y);
+    sm[1][t] = make_float4(B[k].s.x, B[k].s.y, B[k].c.x, B[k].c.y);
+    __syncthreads();
+    for (int s = G >> 1; s > 0; s >>= 1) {
+      if (q < s)
+        for (int h = 0; h < 2; ++h) {
+          float4 x = sm[h][t], y = sm[h][t + s * R];
+          DF2 a{make_float2(x.x, x.y), make_float2(x.z, x.w)};
+          df_add(a, DF2{make_float2(y.x, y.y), make_float2(y.z, y.w)});
+          sm[h][t] = make_float4(a.s.x, a.s.y, a.c.x, a.c.y);
+        }
+      __syncthreads();
+    }
+    if (q == 0) {
+      float4 *o = part + (((long)blockIdx.x * KC + k) * R + t) * 2;
+      o[0] = sm[0][t];
+      o[1] = sm[1][t];
+    }
+    __syncthreads();
+  }
+}
+
+// |w_r|^2 per right-hand side in the layout of k_mdot_df with one dot (B = 0)
+__global__ void __launch_bounds__(256) k_norm2_df(const zdf *__restrict__ w, long E, int R,
+                                                  float4 *__restrict__ part) {
+  __shared__ float4 sm[256];
+  int t = threadIdx.x, nt = blockDim.x;
+  int G = nt / R, q = t / R;
+  DF2 A{make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+  long stride = (long)gridDim.x * nt;
+  for (long e = (long)blockIdx.x * nt + t; e < E; e += stride) {
+    float4 wv = ld4(w + e);
+    float2 wh = make_float2(wv.x, wv.y), wl = make_float2(wv.z, wv.w);
+    df_acc(A, wh, wl, wh, wl);
+  }
+  sm[t] = make_float4(A.s.x, A.s.y, A.c.x, A.c.y);
+  __syncthreads();
+  for (int s = G >> 1; s > 0; s >>= 1) {
+    if (q < s) {
+      float4 x = sm[t], y = sm[t + s * R];
+      DF2 a{make_float2(x.x, x.y), make_float2(x.z, x.w)};
+      df_add(a, DF2{make_float2(y.x, y.y), make_float2(y.z, y.w)});
+      sm[t] = make_float4(a.s.x, a.s.y, a.c.x, a.c.y);
+    }
+    __syncthreads();
+  }
+  if (q == 0) {
+    float4 *o = part + ((long)blockIdx.x * R + t) * 2;
+    o[0] = sm[t];
+    o[1] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+}
+
+static void launch_mdot_df(int kc, int nblk, int nt, cudaStream_t s, const zdf *V, long vstride, const zdf *w,
+                           long E, int R, float4 *part) {
+  switch (kc) {
+#define WL_MDOT_DF(K) \
+  case K: k_mdot_df<K><<<nblk, nt, 0, s>>>(V, vstride, w, E, R, part); break;
+    WL_MDOT_DF(1) WL_MDOT_DF(2) WL_MDOT_DF(3) WL_MDOT_DF(4) WL_MDOT_DF(5) WL_MDOT_DF(6) WL_MDOT_DF(7) WL_MDOT_DF(8)
+#undef WL_MDOT_DF
+    default: break;
+  }
+}
+
+// the sums of k_mdot_df over blocks, one warp per (k, r) in a fixed order,
+// converted to FP64: out[r][k0 + k] (= or +=) V_k^H w; with coef, the
+// coefficients for k_maxpy_df: {crh, crh, crl, crl} and {cih, -cih, cil, -cil}
+__global__ void k_mdot_final_df(const float4 *__restrict__ part, int nblk, int kc, int R, zd *out, int ostride,
+                                int k0, int accumulate, float4 *coef) {
+  int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (wid >= kc * R) return;
+  int k = wid / R, r = wid % R;
+  DF2 A{make_float2(0.f, 0.f), make_float2(0.f, 0.f)}, B = A;
+  for (int b = lane; b < nblk; b += 32) {
+    const float4 *p = part + (((long)b * kc + k) * R + r) * 2;
+    float4 x = p[0], y = p[1];
+    df_add(A, DF2{make_float2(x.x, x.y), make_float2(x.z, x.w)});
+    df_add(B, DF2{make_float2(y.x, y.y), make_float2(y.z, y.w)});
+  }
+#pragma unroll
+  for (int off = 16; off; off >>= 1) {
+    DF2 a2, b2;
+    a2.s.x = __shfl_down_sync(0xffffffffu, A.s.x, off);
+    a2.s.y = __shfl_down_sync(0xffffffffu, A.s.y, off);
+    a2.c.x = __shfl_down_sync(0xffffffffu, A.c.x, off);
+    a2.c.y = __shfl_down_sync(0xffffffffu, A.c.y, off);
+    b2.s.x = __shfl_down_sync(0xffffffffu, B.s.x, off);
+    b2.s.y = __shfl_down_sync(0xffffffffu, B.s.y, off);
+    b2.c.x = __shfl_down_sync(0xffffffffu, B.c.x, off);
+    b2.c.y = __shfl_down_sync(0xffffffffu, B.c.y, off);
+    df_add(A, a2);
+    df_add(B, b2);
+  }
+  if (lane) return;
+  zd s = mk(((double)A.s.x + (double)A.s.y) + ((double)A.c.x + (double)A.c.y),
+            ((double)B.s.x - (double)B.s.y) + ((double)B.c.x - (double)B.c.y));
+  zd *o = out + (long)r * ostride + k0 + k;
+  *o = accumulate ? (*o + s) : s;
+  if (coef) {
+    float2 cr = split_df(s.re), cim = split_df(s.im);
+    float4 *c = coef + ((long)(k0 + k) * R + r) * 2;
+    c[0] = make_float4(cr.x, cr.x, cr.y, cr.y);
+    c[1] = make_float4(cim.x, -cim.x, cim.y, -cim.y);
+  }
+}
+
+// w -= sum_k V_k c_k[r] in double-float (c from k_mdot_final_df): P sums
+// (cr vr, cr vi) and Q sums (ci vr, -ci vi), so Re = P.x + Q.y and
+// Im = P.y + Q.x; the k loop is unrolled by 4 with the loads issued first
+__global__ void __launch_bounds__(256) k_maxpy_df(const zdf *__restrict__ V, long vstride, int kc,
+                                                  const float4 *__restrict__ coef, zdf *__restrict__ w, long E,
+                                                  int R) {
+  long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= E) return;
+  int r = (int)(e % R);
+  DF2 P{make_float2(0.f, 0.f), make_float2(0.f, 0.f)}, Q = P;
+  auto step = [&](float4 v, float4 c0, float4 c1) {
+    float2 vh = make_float2(v.x, v.y), vl = make_float2(v.z, v.w);
+    df_acc(P, make_float2(c0.x, c0.y), make_float2(c0.z, c0.w), vh, vl);
+    df_acc(Q, make_float2(c1.x, c1.y), make_float2(c1.z, c1.w), vh, vl);
+  };
+  int k = 0;
+  for (; k + 4 <= kc; k += 4) {
+    float4 v[4], c[4][2];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) v[u] = ld4(V + (k + u) * vstride + e);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const float4 *cp = coef + ((long)(k + u) * R + r) * 2;
+      c[u][0] = cp[0];
+      c[u][1] = cp[1];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) step(v[u], c[u][0], c[u][1]);
+  }
+  for (; k < kc; ++k) {
+    const float4 *cp = coef + ((long)k * R + r) * 2;
+    step(ld4(V + k * vstride + e), cp[0], cp[1]);
+  }
+  df_add(P, DF2{swap2(Q.s), swap2(Q.c)});
+  float4 wv = ld4(w + e);
+  DF2 W{make_float2(wv.x, wv.y), make_float2(wv.z, wv.w)};
+  df_add(W, DF2{neg2(P.s), neg2(P.c)});
+  st4(w + e, W.s, W.c);
+}
+
+// v_{j+1} = f[rhs] w in double-float and its FP32 copy (the next cycle's
+// input, the nearest float of hi + lo)
+__global__ void k_scale_df(const zdf *__restrict__ in, zdf *__restrict__ out, zf *__restrict__ cyc,
+                           const float2 *__restrict__ f, long E, int R) {
+  long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= E) return;
+  float2 fr = f[e % R];
+  float2 ih = make_float2(fr.x, fr.x), il = make_float2(fr.y, fr.y);
+  float4 wv = ld4(in + e);
+  float2 wh = make_float2(wv.x, wv.y), wl = make_float2(wv.z, wv.w);
+  float2 p = __fmul2_rn(wh, ih);
+  float2 x = __ffma2_rn(wh, ih, neg2(p));
+  x = __ffma2_rn(wh, il, x);
+  x = __ffma2_rn(wl, ih, x);
+  DF2 v;
+  renorm2(p, x, v);
+  st4(out + e, v.s, v.c);
+  float2 c = add2(v.s, v.c);
+  cyc[e] = mk(c.x, c.y);
+}
+
+// v_0 = f[rhs] r (r in FP64: the true residual) as a double-float, and its
+// FP32 copy (the nearest float, as k_scale_rhs_cyc rounds)
+__global__ void k_scale_first_df(const zd *__restrict__ in, zdf *__restrict__ out, zf *__restrict__ cyc,
+                                 const double *__restrict__ f, long E, int R) {
+  long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= E) return;
+  zd v = f[e % R] * in[e];
+  float2 re = split_df(v.re), im = split_df(v.im);
+  st4(out + e, make_float2(re.x, im.x), make_float2(re.y, im.y));
+  cyc[e] = mk(re.x, im.x);
+}
+
 // ------------------------------------------------------------------ Givens
 // column j of the Arnoldi process for every active right-hand side
 __global__ void k_givens(KS k, int j, double tol) {
@@ -236,6 +516,7 @@ __global__ void k_givens(KS k, int j, double tol) {
   int m = k.m;
   if (!k.active[r] || k.stop[r]) {
     k.inv[r] = 0.0;
+    k.invdf[r] = make_float2(0.f, 0.f);
     return;
   }
   zd *hc = k.hcol + (long)r * (m + 1);
@@ -280,6 +561,7 @@ __global__ void k_givens(KS k, int j, double tol) {
     k.nanf[r] = 1;
   }
   k.inv[r] = (done || hn == 0.0) ? 0.0 : 1.0 / hn;
+  k.invdf[r] = split_df(k.inv[r]);
   if (done) k.stop[r] = 1;
   else atomicAdd(k.running, 1);
 }
@@ -315,6 +597,7 @@ __global__ void k_cycle_start(KS k) {
   k.beta[r] = beta;
   bool act = k.active[r] && beta > 0.0;
   k.inv[r] = act ? 1.0 / beta : 0.0;
+  k.invdf[r] = split_df(k.inv[r]);
   for (int i = 0; i <= m; ++i) k.g[(long)r * (m + 1) + i] = mk(0.0, 0.0);
   k.g[(long)r * (m + 1)] = mk(act ? beta : 0.0, 0.0);
   k.stop[r] = act ? 0 : 1;
@@ -372,6 +655,33 @@ static int mdots(wl_amg *a, const cx<Tv> *V, long vstride, int kc, const zd *w, 
     k_mdot_final<<<WL_GRID(kk * R * 32, 256), 256, 0, s>>>(a->red.as<zd>(), c.nblk, kk, R, out, ostride, k0,
                                                            accumulate, copy_to);
   }
+  WL_CUDA(cudaGetLastError());
+  return WL_OK;
+}
+
+// the same with double-float vectors; coef (or NULL) receives the
+// coefficients for k_maxpy_df
+static int mdots_df(wl_amg *a, const zdf *V, long vstride, int kc, const zdf *w, long E, int R, zd *out,
+                    int ostride, int accumulate, float4 *coef, cudaStream_t s) {
+  RedCfg c = red_cfg(E, R);
+  int nl = (kc + KCH_DF - 1) / KCH_DF;
+  for (int k0 = 0, l = 0, kk = 0; k0 < kc; k0 += kk, ++l) {
+    kk = (kc - k0 + (nl - l) - 1) / (nl - l);
+    wl_count_launches(2);
+    launch_mdot_df(kk, c.nblk, c.nt, s, V + k0 * vstride, vstride, w, E, R, a->red.as<float4>());
+    k_mdot_final_df<<<WL_GRID(kk * R * 32, 256), 256, 0, s>>>(a->red.as<float4>(), c.nblk, kk, R, out, ostride, k0,
+                                                              accumulate, coef);
+  }
+  WL_CUDA(cudaGetLastError());
+  return WL_OK;
+}
+
+static int norms2_df(wl_amg *a, const zdf *w, long E, int R, zd *tmp, double *out, cudaStream_t s) {
+  RedCfg c = red_cfg(E, R);
+  k_norm2_df<<<c.nblk, c.nt, 0, s>>>(w, E, R, a->red.as<float4>());
+  k_mdot_final_df<<<WL_GRID(R * 32, 256), 256, 0, s>>>(a->red.as<float4>(), c.nblk, 1, R, tmp, 1, 0, 0, nullptr);
+  k_re_of<<<WL_GRID(R, 128), 128, 0, s>>>(tmp, out, R);
+  wl_count_launches(3);
   WL_CUDA(cudaGetLastError());
   return WL_OK;
 }
@@ -455,6 +765,8 @@ int fg_cycle(wl_amg *a, const zd *bnorm_h, zd *xh, int nrhs, double tol, const i
   long vs = E;
   KS k = ks_layout(a->small.p, m, nrhs);
   zd *V = a->V.as<zd>(), *w = a->w.as<zd>(), *rr = a->rr.as<zd>();
+  zdf *Vd = a->V.as<zdf>(), *wd = a->w.as<zdf>();  // the same buffers with gs_arith = 1
+  const bool df = a->prm.gs_arith == 1;
   size_t zb_ = prec_bytes(prec);
   char *Zb = (char *)a->Z.p;
   unsigned gE = WL_GRID(E, 256);
@@ -472,7 +784,12 @@ int fg_cycle(wl_amg *a, const zd *bnorm_h, zd *xh, int nrhs, double tol, const i
   };
   k_cycle_start<<<WL_GRID(nrhs, 128), 128, 0, s>>>(k);
   wl_count_launches(1);
-  scale_next(rr, V);
+  if (df) {
+    k_scale_first_df<<<gE, 256, 0, s>>>(rr, Vd, a->lev[0].f.as<zf>(), k.inv, E, nrhs);
+    wl_count_launches(1);
+  } else {
+    scale_next(rr, V);
+  }
   int jdone = 0;
   for (int j = 0; j < m; ++j) {
     void *zj = Zb + (size_t)j * vs * zb_;
@@ -480,22 +797,36 @@ int fg_cycle(wl_amg *a, const zd *bnorm_h, zd *xh, int nrhs, double tol, const i
     WL_TRY(cycle_run(a, nrhs, prec, s));
     WL_CUDA(cudaMemcpyAsync(zj, a->lev[0].x.p, zb_ * E, cudaMemcpyDeviceToDevice, s));
     // w = Dhat z_j (FP64)
-    if (prec != WL_FP64 && a->prm.arnoldi_matvec == 1) WL_TRY(stencil_apply32_to64(a, zj, w, nrhs, s));
+    if (df) WL_TRY(stencil_apply32_to_df(a, zj, wd, nrhs, s));
+    else if (prec != WL_FP64 && a->prm.arnoldi_matvec == 1) WL_TRY(stencil_apply32_to64(a, zj, w, nrhs, s));
     else WL_TRY(dhat_apply_dev(op, zj, prec != WL_FP64, w, nrhs, s));
     // Gram-Schmidt against v_0 .. v_j
     k_zero_hcol<<<WL_GRID(nrhs, 128), 128, 0, s>>>(k);
     wl_count_launches(1);
     for (int pass = 0; pass < a->prm.gs_passes; ++pass) {
-      WL_TRY(mdots<double>(a, V, vs, j + 1, w, E, nrhs, k.hcol, m + 1, 1, k.hpass, s));
-      k_maxpy<double, 1><<<gE, 256, 0, s>>>(V, vs, j + 1, k.hpass, nrhs, w, E, nrhs);
+      if (df) {
+        WL_TRY(mdots_df(a, Vd, vs, j + 1, wd, E, nrhs, k.hcol, m + 1, 1, k.hpd, s));
+        k_maxpy_df<<<gE, 256, 0, s>>>(Vd, vs, j + 1, k.hpd, wd, E, nrhs);
+      } else {
+        WL_TRY(mdots<double>(a, V, vs, j + 1, w, E, nrhs, k.hcol, m + 1, 1, k.hpass, s));
+        k_maxpy<double, 1><<<gE, 256, 0, s>>>(V, vs, j + 1, k.hpass, nrhs, w, E, nrhs);
+      }
       wl_count_launches(1);
     }
     zd *tmpc = a->small.as<zd>() + (a->small.bytes / sizeof(zd)) - 2 * (size_t)nrhs - 8;
-    WL_TRY(norms2(a, w, E, nrhs, tmpc, k.nrm2, s));
+    if (df) WL_TRY(norms2_df(a, wd, E, nrhs, tmpc, k.nrm2, s));
+    else WL_TRY(norms2(a, w, E, nrhs, tmpc, k.nrm2, s));
     WL_CUDA(cudaMemsetAsync(k.running, 0, sizeof(int) * 2, s));
     k_givens<<<WL_GRID(nrhs, 128), 128, 0, s>>>(k, j, tol);
     wl_count_launches(1);
-    if (j + 1 < m) scale_next(w, V + (j + 1) * vs);
+    if (j + 1 < m) {
+      if (df) {
+        k_scale_df<<<gE, 256, 0, s>>>(wd, Vd + (j + 1) * vs, a->lev[0].f.as<zf>(), k.invdf, E, nrhs);
+        wl_count_launches(1);
+      } else {
+        scale_next(w, V + (j + 1) * vs);
+      }
+    }
     WL_CUDA(cudaGetLastError());
     int run[2];
     WL_CUDA(cudaMemcpyAsync(h_d + nrhs, k.running, sizeof(int) * 2, cudaMemcpyDeviceToHost, s));
@@ -839,7 +1170,9 @@ extern "C" int wl_time_kernel(wl_amg *a, int kind, int level, int nrhs, int prec
       case WL_K_PROLONG: return wl::prolong_op(a, level, prec, a->lev[level + 1].x.p, L.x.p, nrhs, s);
       case WL_K_COARSEST:
         return wl::coarsest_apply(a, prec, a->lev[a->L - 1].f.p, a->lev[a->L - 1].x.p, nrhs, s);
-      case WL_K_GS_DOT:
+      case WL_K_GS_DOT:  // the Gram-Schmidt arithmetic the hierarchy's solves use
+        if (a->prm.gs_arith == 1)
+          return wl::mdots_df(a, a->V.as<zdf>(), E, kc, a->w.as<zdf>(), E, nrhs, k.hcol, m + 1, 0, k.hpd, s);
         return wl::mdots<double>(a, a->V.as<zd>(), E, kc, a->w.as<zd>(), E, nrhs, k.hcol, m + 1, 0, k.hpass, s);
       case WL_K_FP64_FMA: {
         int nsm = 0;
@@ -849,8 +1182,11 @@ extern "C" int wl_time_kernel(wl_amg *a, int kind, int level, int nrhs, int prec
         return WL_OK;
       }
       default:
-        k_maxpy<double, 1><<<WL_GRID(E, 256), 256, 0, s>>>(a->V.as<zd>(), E, kc, k.hpass, nrhs, a->w.as<zd>(), E,
-                                                            nrhs);
+        if (a->prm.gs_arith == 1)
+          k_maxpy_df<<<WL_GRID(E, 256), 256, 0, s>>>(a->V.as<zdf>(), E, kc, k.hpd, a->w.as<zdf>(), E, nrhs);
+        else
+          k_maxpy<double, 1><<<WL_GRID(E, 256), 256, 0, s>>>(a->V.as<zd>(), E, kc, k.hpass, nrhs, a->w.as<zd>(), E,
+                                                              nrhs);
         wl_count_launches(1);
         return WL_OK;
     }

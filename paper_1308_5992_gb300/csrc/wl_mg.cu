@@ -20,10 +20,11 @@ namespace cg = cooperative_groups;
 
 // ------------------------------------------------------------ stencil apply
 // y = A x, or y = f - A x when f != nullptr (y may alias f); arithmetic in T,
-// y stored as To (the Arnoldi matvec widens an FP32 result to FP64).
-template <typename T, typename S, typename To = T>
+// y stored as Y (the Arnoldi matvec widens an FP32 result to FP64, or keeps
+// it as the high part of a double-float).
+template <typename T, typename S, typename Y = cx<T>>
 __global__ void __launch_bounds__(256) k_stencil(Geo g, const S *__restrict__ A, const cx<T> *__restrict__ x,
-                                                 const cx<To> *f, cx<To> *y, int nrhs) {
+                                                 const Y *f, Y *y, int nrhs) {
   long tid = (long)blockIdx.x * blockDim.x + threadIdx.x;
   int n = g.nsites();
   if (tid >= (long)n * nrhs) return;
@@ -42,10 +43,12 @@ __global__ void __launch_bounds__(256) k_stencil(Geo g, const S *__restrict__ A,
     cfma(y1, ld<T>(Ah + d * 4 + 3), x1);
   }
   long o = (long)h * 2 * nrhs + r;
-  cx<To> z0 = widen<To>(y0), z1 = widen<To>(y1);
-  if (f) {
-    z0 = f[o] - z0;
-    z1 = f[o + nrhs] - z1;
+  Y z0 = store_as<Y>(y0), z1 = store_as<Y>(y1);
+  if constexpr (!std::is_same<Y, zdf>::value) {
+    if (f) {
+      z0 = f[o] - z0;
+      z1 = f[o + nrhs] - z1;
+    }
   }
   y[o] = z0;
   y[o + nrhs] = z1;
@@ -944,9 +947,9 @@ static int launch_coop(const Level &L, const LevelOps &o, int sweeps, void *x, v
 // tile's stencil rows are staged once (cp.async), so each x value crosses
 // L2 once per tile instead of once per neighbour.  Same arithmetic, in the
 // same order, as k_stencil.  x must not alias y.
-template <typename T, typename S, typename To, int R, int WF>
+template <typename T, typename S, typename Y, int R, int WF>
 __global__ void __launch_bounds__(256) k_stencil_tile(Geo g, const S *__restrict__ A, const cx<T> *__restrict__ x,
-                                                      const cx<To> *f, cx<To> *y, int nrhs, int vec) {
+                                                      const Y *f, Y *y, int nrhs, int vec) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   cx<T> *xs = (cx<T> *)sm_raw;                  // [100][2][R]
   S *As = (S *)(xs + KTH * KTH * 2 * R);        // [64][36]
@@ -986,8 +989,8 @@ __global__ void __launch_bounds__(256) k_stencil_tile(Geo g, const S *__restrict
   }
   // f of this thread's outputs is loaded while the staging copies fly
   constexpr int PER = KT * KT * R / NT;  // outputs per thread
-  cx<To> fv[WF ? PER : 1][2];
-  if (WF) {
+  Y fv[WF ? PER : 1][2];
+  if constexpr (WF) {
 #pragma unroll
     for (int u = 0; u < PER; ++u) {
       int it = tid + u * NT, q = it % R, ks = it / R;
@@ -1018,10 +1021,10 @@ __global__ void __launch_bounds__(256) k_stencil_tile(Geo g, const S *__restrict
       cfma(y1, ld<T>(Ah + d * 4 + 3), x1);
     }
     long o = (long)hs[(i + 1) * KTH + j + 1] * 2 * nrhs + r0 + q;
-    cx<To> z0 = widen<To>(y0), z1 = widen<To>(y1);
-    if (WF) {
-      z0 = fv[WF ? u : 0][0] - z0;
-      z1 = fv[WF ? u : 0][1] - z1;
+    Y z0 = store_as<Y>(y0), z1 = store_as<Y>(y1);
+    if constexpr (WF) {
+      z0 = fv[u][0] - z0;
+      z1 = fv[u][1] - z1;
     }
     y[o] = z0;
     y[o + nrhs] = z1;
@@ -1033,7 +1036,7 @@ static size_t stencil_tile_smem(int R) {
   return (size_t)KTH * KTH * 2 * R * sizeof(cx<T>) + (size_t)KT * KT * 36 * sizeof(S) + KTH * KTH * sizeof(int);
 }
 
-template <typename T, typename S, typename To, int R>
+template <typename T, typename S, typename Y, int R>
 static int launch_stencil_tile_r(const Level &L, const S *A, const void *x, const void *f, void *y, int nrhs,
                                  cudaStream_t s) {
   size_t smem = stencil_tile_smem<T, S>(R);
@@ -1041,30 +1044,33 @@ static int launch_stencil_tile_r(const Level &L, const S *A, const void *x, cons
   int vec = ((uintptr_t)x % 16 == 0) && (sizeof(T) == 8 || nrhs % 2 == 0);
   dim3 grid((L.N / KT) * (L.N / (2 * KT)), (nrhs + R - 1) / R);
   if (f) {
-    WL_TRY(set_smem_limit((const void *)k_stencil_tile<T, S, To, R, 1>, smem, limit_set[1]));
-    k_stencil_tile<T, S, To, R, 1><<<grid, 256, smem, s>>>(L.geo, A, (const cx<T> *)x, (const cx<To> *)f,
-                                                            (cx<To> *)y, nrhs, vec);
+    if constexpr (std::is_same<Y, zdf>::value) {
+      return WL_EINVAL;  // no residual form for double-float output
+    } else {
+      WL_TRY(set_smem_limit((const void *)k_stencil_tile<T, S, Y, R, 1>, smem, limit_set[1]));
+      k_stencil_tile<T, S, Y, R, 1><<<grid, 256, smem, s>>>(L.geo, A, (const cx<T> *)x, (const Y *)f, (Y *)y, nrhs,
+                                                             vec);
+    }
   } else {
-    WL_TRY(set_smem_limit((const void *)k_stencil_tile<T, S, To, R, 0>, smem, limit_set[0]));
-    k_stencil_tile<T, S, To, R, 0><<<grid, 256, smem, s>>>(L.geo, A, (const cx<T> *)x, nullptr, (cx<To> *)y, nrhs,
-                                                            vec);
+    WL_TRY(set_smem_limit((const void *)k_stencil_tile<T, S, Y, R, 0>, smem, limit_set[0]));
+    k_stencil_tile<T, S, Y, R, 0><<<grid, 256, smem, s>>>(L.geo, A, (const cx<T> *)x, nullptr, (Y *)y, nrhs, vec);
   }
   return WL_OK;
 }
 
 // the tiled form for grids the tiling covers and batches of at least 8
-template <typename T, typename S, typename To>
+template <typename T, typename S, typename Y>
 static bool launch_stencil_tile(const Level &L, const S *A, const void *x, const void *f, void *y, int nrhs,
                                 cudaStream_t s, int *rc) {
   if (L.N < 64 || L.N % (4 * KT) || nrhs < 8) return false;
   if constexpr (sizeof(T) == 4) {
     if (nrhs >= 32) {
-      *rc = launch_stencil_tile_r<T, S, To, 32>(L, A, x, f, y, nrhs, s);
+      *rc = launch_stencil_tile_r<T, S, Y, 32>(L, A, x, f, y, nrhs, s);
       return true;
     }
   }
-  if (nrhs >= 16) *rc = launch_stencil_tile_r<T, S, To, 16>(L, A, x, f, y, nrhs, s);
-  else *rc = launch_stencil_tile_r<T, S, To, 8>(L, A, x, f, y, nrhs, s);
+  if (nrhs >= 16) *rc = launch_stencil_tile_r<T, S, Y, 16>(L, A, x, f, y, nrhs, s);
+  else *rc = launch_stencil_tile_r<T, S, Y, 8>(L, A, x, f, y, nrhs, s);
   return true;
 }
 
@@ -1077,13 +1083,13 @@ int stencil_apply(wl_amg *a, int l, int prec, const void *x, void *y, const void
   wl_count_launches(1);
   int rc = WL_OK;
   if (prec == WL_FP64) {
-    if (!launch_stencil_tile<double, zd, double>(L, o.A.as<zd>(), x, f, y, nrhs, s, &rc))
+    if (!launch_stencil_tile<double, zd, zd>(L, o.A.as<zd>(), x, f, y, nrhs, s, &rc))
       k_stencil<double, zd><<<grid, 256, 0, s>>>(L.geo, o.A.as<zd>(), (const zd *)x, (const zd *)f, (zd *)y, nrhs);
   } else if (prec == WL_FP32) {
-    if (!launch_stencil_tile<float, zf, float>(L, o.A.as<zf>(), x, f, y, nrhs, s, &rc))
+    if (!launch_stencil_tile<float, zf, zf>(L, o.A.as<zf>(), x, f, y, nrhs, s, &rc))
       k_stencil<float, zf><<<grid, 256, 0, s>>>(L.geo, o.A.as<zf>(), (const zf *)x, (const zf *)f, (zf *)y, nrhs);
   } else {
-    if (!launch_stencil_tile<float, zb, float>(L, o.A.as<zb>(), x, f, y, nrhs, s, &rc))
+    if (!launch_stencil_tile<float, zb, zf>(L, o.A.as<zb>(), x, f, y, nrhs, s, &rc))
       k_stencil<float, zb><<<grid, 256, 0, s>>>(L.geo, o.A.as<zb>(), (const zf *)x, (const zf *)f, (zf *)y, nrhs);
   }
   WL_TRY(rc);
@@ -1407,18 +1413,26 @@ int autotune_sweeps(wl_amg *a, int nrhs, int prec, cudaStream_t s) {
 }
 
 // y = A_0 x in FP32 arithmetic from the FP32 copy of the level-0 stencil
-// (Dhat), x float, y widened to double: the Arnoldi matvec of an FP32 cycle
-int stencil_apply32_to64(wl_amg *a, const void *x, zd *y, int nrhs, cudaStream_t s) {
+// (Dhat), x float, y widened to double or stored as a double-float with a
+// zero low part: the Arnoldi matvec of an FP32 cycle
+template <typename Y>
+static int stencil_apply32_to(wl_amg *a, const void *x, Y *y, int nrhs, cudaStream_t s) {
   const Level &L = a->lev[0];
   long tot = (long)L.n * nrhs;
   wl_count_launches(1);
   int rc = WL_OK;
-  if (!launch_stencil_tile<float, zf, double>(L, L.op32.A.as<zf>(), x, nullptr, y, nrhs, s, &rc))
-    k_stencil<float, zf, double><<<WL_GRID(tot, 256), 256, 0, s>>>(L.geo, L.op32.A.as<zf>(), (const zf *)x, nullptr,
-                                                                   y, nrhs);
+  if (!launch_stencil_tile<float, zf, Y>(L, L.op32.A.as<zf>(), x, nullptr, y, nrhs, s, &rc))
+    k_stencil<float, zf, Y><<<WL_GRID(tot, 256), 256, 0, s>>>(L.geo, L.op32.A.as<zf>(), (const zf *)x, nullptr, y,
+                                                              nrhs);
   WL_TRY(rc);
   WL_CUDA(cudaGetLastError());
   return WL_OK;
+}
+int stencil_apply32_to64(wl_amg *a, const void *x, zd *y, int nrhs, cudaStream_t s) {
+  return stencil_apply32_to<zd>(a, x, y, nrhs, s);
+}
+int stencil_apply32_to_df(wl_amg *a, const void *x, zdf *y, int nrhs, cudaStream_t s) {
+  return stencil_apply32_to<zdf>(a, x, y, nrhs, s);
 }
 
 int restrict_op(wl_amg *a, int l, int prec, const void *r, void *fc, int nrhs, cudaStream_t s) {

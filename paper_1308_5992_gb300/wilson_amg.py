@@ -34,7 +34,7 @@ class amg_params(C.Structure):
                 ("max_restarts", C.c_int), ("precision", C.c_int), ("seed", C.c_ulonglong),
                 ("gs_passes", C.c_int), ("zero_guess", C.c_int), ("sweep_kernel", C.c_int),
                 ("kacz_order", C.c_int), ("arnoldi_matvec", C.c_int),
-                ("setup_cycle", C.c_int), ("overlap", C.c_int)]
+                ("setup_cycle", C.c_int), ("overlap", C.c_int), ("gs_arith", C.c_int)]
 
 
 class wl_info(C.Structure):

@@ -1,7 +1,8 @@
 """Full-size parity on the benchmark workload: C4 (512x512, beta = 10, four
 grids with 4x4, 4x4, 2x2 cells, k = 12), 64 right-hand sides in one call, in
 the launch configuration bench.py times (FP32 V(4,4) tile-coloured cycle,
-FGMRES(20) with one Gram-Schmidt pass, FP32 Arnoldi matvec, FP64 restarts).
+FGMRES(20) with one double-float Gram-Schmidt pass, FP32 Arnoldi matvec,
+FP64 restarts, the batch in two concurrent lanes of 32).
 The hierarchy is the oracle's (shared file), so the solve phase is compared
 on the same operators.  Checked: every right-hand side's full-system residual
 |b - D psi| / |b|, recomputed with the oracle's FP64 D, stays at the
@@ -43,7 +44,8 @@ def test_c4_full_size_batch(O, c4):
     op = W.wilson_create(torch.from_numpy(U).to(DEV), N, m)
     p = W.amg_params_default(zero_guess=1, precision=W.WL_FP32, nu_pre=w["nu"], nu_post=w["nu"],
                              fgmres_m=w["fgmres_m"], gs_passes=w["gs_passes"], kacz_order=w["kacz_order"],
-                             arnoldi_matvec=w["arnoldi_matvec"], overlap=w["overlap"])
+                             arnoldi_matvec=w["arnoldi_matvec"], overlap=w["overlap"],
+                             gs_arith=w["gs_arith"])
     amg = W.amg_import(op, path, p)
     nrhs = 64
     b = rhs_batch(N, nrhs, 100)
@@ -70,7 +72,8 @@ def test_c4_full_size_matches_oracle_at_1e13(O, c4):
     op = W.wilson_create(torch.from_numpy(U).to(DEV), N, m)
     p = W.amg_params_default(zero_guess=1, precision=W.WL_FP32, nu_pre=w["nu"], nu_post=w["nu"],
                              fgmres_m=w["fgmres_m"], gs_passes=w["gs_passes"], kacz_order=w["kacz_order"],
-                             arnoldi_matvec=w["arnoldi_matvec"], overlap=w["overlap"])
+                             arnoldi_matvec=w["arnoldi_matvec"], overlap=w["overlap"],
+                             gs_arith=w["gs_arith"])
     amg = W.amg_import(op, path, p)
     nrhs = 64
     b = rhs_batch(N, nrhs, 100)

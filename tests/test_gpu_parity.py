@@ -430,6 +430,40 @@ def test_mixed_precision_solve(O, ops, shared, prec, order, matvec):
     assert np.linalg.norm(H(psi[0]) - ref) / np.linalg.norm(ref) <= 1e-10
 
 
+@pytest.mark.parametrize("name,nrhs,order,passes", [("T64", 3, 0, 2), ("C2", 40, 1, 1), ("C2", 9, 1, 2)])
+def test_double_float_gram_schmidt(O, shared, name, nrhs, order, passes):
+    """gs_arith = 1 (Krylov basis, dots, updates and norms in double-float on
+    the FP32 pipes): every right-hand side reaches the FP64 true residual
+    1e-13 and the oracle's solution to 1e-10, with iteration counts within 2
+    of the FP64 Gram-Schmidt on the same cycle.  40 right-hand sides take
+    mdot launches of up to 8 dots and the tiled Arnoldi matvec; 3 and 9 the
+    per-site one, one and two Gram-Schmidt passes."""
+    w, op, h, _, path = shared(name)
+    kw = dict(zero_guess=1, precision=W.WL_FP32, kacz_order=order, arnoldi_matvec=1, gs_passes=passes)
+    a64 = W.amg_import(op, path, W.amg_params_default(gs_arith=0, **kw))
+    adf = W.amg_import(op, path, W.amg_params_default(gs_arith=1, **kw))
+    b = rhs_batch(w["N"], nrhs, 31)
+    x64, xdf = torch.zeros_like(T(b)), torch.zeros_like(T(b))
+    rc64, i64 = W.amg_solve(a64, T(b), x64, nrhs, 1e-13)
+    rcdf, idf = W.amg_solve(adf, T(b), xdf, nrhs, 1e-13)
+    assert rc64 == W.WL_OK and rcdf == W.WL_OK
+    assert all(i["true_relres"] <= 1e-13 for i in idf)
+    for q in range(nrhs):
+        assert abs(idf[q]["iters"] - i64[q]["iters"]) <= 2, (q, idf[q], i64[q])
+    for q in sorted({0, nrhs // 2, nrhs - 1}):
+        ref, _ = h.solve(b[q], tol=1e-13, order=O.ORDER_TILE if order else O.ORDER_COLOUR)
+        assert np.linalg.norm(H(xdf[q]) - ref) / np.linalg.norm(ref) <= 1e-10, q
+
+
+def test_double_float_gram_schmidt_needs_an_fp32_matvec(ops):
+    """gs_arith = 1 is refused with an FP64 cycle or an FP64 Arnoldi matvec."""
+    w, op = ops("T64")
+    for kw in (dict(precision=W.WL_FP64, arnoldi_matvec=1), dict(precision=W.WL_FP32, arnoldi_matvec=0)):
+        with pytest.raises(W.WilsonAMGError) as e:
+            W.amg_setup(op, W.amg_params_default(gs_arith=1, **kw))
+        assert e.value.code == W.WL_EINVAL
+
+
 def test_batch_equals_alone(shared):
     """Each right-hand side gives the same result alone and in a batch."""
     w, op, h, amg, _ = shared("T64")

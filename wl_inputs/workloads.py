@@ -78,7 +78,7 @@ WORKLOADS["T128"] = dict(N=128, beta=6.0, sweeps=100, target=1e-2, seed=14, bloc
 # solve-cycle parameters (defaults: V(2,2), FGMRES(20), two Gram-Schmidt passes)
 # and the setup's relaxations per visit in its two cycles (default: the paper's 10, 5)
 _SOLVE = dict(nu=2, cycle="V", fgmres_m=20, gs_passes=2, kacz_order=0, arnoldi_matvec=0, setup_mu=(10, 5),
-              overlap=0)
+              overlap=0, gs_arith=0)
 for _name, _w in WORKLOADS.items():
     for _k, _v in _SOLVE.items():
         _w.setdefault(_k, _v)
@@ -96,9 +96,13 @@ WORKLOADS["C4"].update(setup_mu=(10, 20))
 # FP64 Gram-Schmidt shares the GPU with the other half's FP32 cycle; measured 319.5 against 300.7
 # solves/s for one lane
 WORKLOADS["C4"].update(overlap=1)
+# and its Gram-Schmidt in double-float on the FP32 pipes (amg_params.gs_arith): the FP64 dots and
+# updates were bound by the FP64 rate (1.2 TFLOP/s), the double-float ones are bound by HBM;
+# measured 389.8 against 323.5 solves/s (two lanes), 374.2 with one lane
+WORKLOADS["C4"].update(gs_arith=1)
 # the single right-hand-side mixed-precision workload with the same cycle; C3b
 # is its variant with BF16-stored stencils and interpolation weights
-WORKLOADS["C3"].update(nu=4, gs_passes=1, kacz_order=1, arnoldi_matvec=1, setup_mu=(10, 20))
+WORKLOADS["C3"].update(nu=4, gs_passes=1, kacz_order=1, arnoldi_matvec=1, setup_mu=(10, 20), gs_arith=1)
 WORKLOADS["C3b"] = dict(WORKLOADS["C3"], precision="bf16")
 
 
