@@ -119,8 +119,9 @@ typedef struct {
                              its dots, updates and norms): 0 = FP64; 1 = double-float,
                              each value an unevaluated sum of two floats (about 48
                              significant bits) computed on the FP32 pipes with
-                             error-free transformations, the Hessenberg matrix, Givens
-                             rotations and the solution update staying FP64.  Requires
+                             error-free transformations; the restart update x += Z y
+                             sums Z y the same way and adds it to x in FP64; the
+                             Hessenberg matrix and Givens rotations stay FP64.  Requires
                              an FP32 or BF16 cycle with arnoldi_matvec = 1 (EINVAL
                              otherwise).  The true residual at every restart stays
                              FP64, so the accuracy a solve reaches is unchanged. */

@@ -351,37 +351,6 @@ __global__ void __launch_bounds__(256, 2) k_mdot_df(const zdf *__restrict__ V, l
   }
 }
 
-// |w_r|^2 per right-hand side in the layout of k_mdot_df with one dot (B = 0)
-__global__ void __launch_bounds__(256) k_norm2_df(const zdf *__restrict__ w, long E, int R,
-                                                  float4 *__restrict__ part) {
-  __shared__ float4 sm[256];
-  int t = threadIdx.x, nt = blockDim.x;
-  int G = nt / R, q = t / R;
-  DF2 A{make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-  long stride = (long)gridDim.x * nt;
-  for (long e = (long)blockIdx.x * nt + t; e < E; e += stride) {
-    float4 wv = ld4(w + e);
-    float2 wh = make_float2(wv.x, wv.y), wl = make_float2(wv.z, wv.w);
-    df_acc(A, wh, wl, wh, wl);
-  }
-  sm[t] = make_float4(A.s.x, A.s.y, A.c.x, A.c.y);
-  __syncthreads();
-  for (int s = G >> 1; s > 0; s >>= 1) {
-    if (q < s) {
-      float4 x = sm[t], y = sm[t + s * R];
-      DF2 a{make_float2(x.x, x.y), make_float2(x.z, x.w)};
-      df_add(a, DF2{make_float2(y.x, y.y), make_float2(y.z, y.w)});
-      sm[t] = make_float4(a.s.x, a.s.y, a.c.x, a.c.y);
-    }
-    __syncthreads();
-  }
-  if (q == 0) {
-    float4 *o = part + ((long)blockIdx.x * R + t) * 2;
-    o[0] = sm[t];
-    o[1] = make_float4(0.f, 0.f, 0.f, 0.f);
-  }
-}
-
 static void launch_mdot_df(int kc, int nblk, int nt, cudaStream_t s, const zdf *V, long vstride, const zdf *w,
                            long E, int R, float4 *part) {
   switch (kc) {
@@ -391,6 +360,14 @@ static void launch_mdot_df(int kc, int nblk, int nt, cudaStream_t s, const zdf *
 #undef WL_MDOT_DF
     default: break;
   }
+}
+
+// a coefficient c as the two pre-broadcast double-float pairs k_maxpy_df and
+// k_xupd_df read: {crh, crh, crl, crl} and {cih, -cih, cil, -cil}
+__device__ __forceinline__ void put_coef_df(float4 *c, zd s) {
+  float2 cr = split_df(s.re), cim = split_df(s.im);
+  c[0] = make_float4(cr.x, cr.x, cr.y, cr.y);
+  c[1] = make_float4(cim.x, -cim.x, cim.y, -cim.y);
 }
 
 // the sums of k_mdot_df over blocks, one warp per (k, r) in a fixed order,
@@ -427,34 +404,107 @@ __global__ void k_mdot_final_df(const float4 *__restrict__ part, int nblk, int k
             ((double)B.s.x - (double)B.s.y) + ((double)B.c.x - (double)B.c.y));
   zd *o = out + (long)r * ostride + k0 + k;
   *o = accumulate ? (*o + s) : s;
-  if (coef) {
-    float2 cr = split_df(s.re), cim = split_df(s.im);
-    float4 *c = coef + ((long)(k0 + k) * R + r) * 2;
-    c[0] = make_float4(cr.x, cr.x, cr.y, cr.y);
-    c[1] = make_float4(cim.x, -cim.x, cim.y, -cim.y);
-  }
+  if (coef) put_coef_df(coef + ((long)(k0 + k) * R + r) * 2, s);
 }
 
 // w -= sum_k V_k c_k[r] in double-float (c from k_mdot_final_df): P sums
 // (cr vr, cr vi) and Q sums (ci vr, -ci vi), so Re = P.x + Q.y and
-// Im = P.y + Q.x; the k loop is unrolled by 4 with the loads issued first
+// Im = P.y + Q.x; the k loop is unrolled by 4 with the loads issued first.
+// With part != NULL the squared norm of the new w is summed as well, in the
+// thread layout of k_mdot_df (a fixed grid, thread t on right-hand side
+// t % R), and written as k_mdot_df's partials of one dot with B = 0: one
+// pass over w instead of two.
 __global__ void __launch_bounds__(256) k_maxpy_df(const zdf *__restrict__ V, long vstride, int kc,
                                                   const float4 *__restrict__ coef, zdf *__restrict__ w, long E,
-                                                  int R) {
+                                                  int R, float4 *__restrict__ part) {
+  __shared__ float4 sm[256];
+  int t = threadIdx.x, nt = blockDim.x;
+  DF2 N2{make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+  long stride = (long)gridDim.x * nt;
+  for (long e = (long)blockIdx.x * nt + t; e < E; e += stride) {
+    int r = (int)(e % R);
+    DF2 P{make_float2(0.f, 0.f), make_float2(0.f, 0.f)}, Q = P;
+    auto step = [&](float4 v, float4 c0, float4 c1) {
+      float2 vh = make_float2(v.x, v.y), vl = make_float2(v.z, v.w);
+      df_acc(P, make_float2(c0.x, c0.y), make_float2(c0.z, c0.w), vh, vl);
+      df_acc(Q, make_float2(c1.x, c1.y), make_float2(c1.z, c1.w), vh, vl);
+    };
+    int k = 0;
+    for (; k + 4 <= kc; k += 4) {
+      float4 v[4], c[4][2];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) v[u] = ld4(V + (k + u) * vstride + e);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float4 *cp = coef + ((long)(k + u) * R + r) * 2;
+        c[u][0] = cp[0];
+        c[u][1] = cp[1];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) step(v[u], c[u][0], c[u][1]);
+    }
+    for (; k < kc; ++k) {
+      const float4 *cp = coef + ((long)k * R + r) * 2;
+      step(ld4(V + k * vstride + e), cp[0], cp[1]);
+    }
+    df_add(P, DF2{swap2(Q.s), swap2(Q.c)});
+    float4 wv = ld4(w + e);
+    DF2 Wn{make_float2(wv.x, wv.y), make_float2(wv.z, wv.w)};
+    df_add(Wn, DF2{neg2(P.s), neg2(P.c)});
+    st4(w + e, Wn.s, Wn.c);
+    if (part) df_acc(N2, Wn.s, Wn.c, Wn.s, Wn.c);
+  }
+  if (!part) return;
+  int G = nt / R, q = t / R;
+  sm[t] = make_float4(N2.s.x, N2.s.y, N2.c.x, N2.c.y);
+  __syncthreads();
+  for (int s = G >> 1; s > 0; s >>= 1) {
+    if (q < s) {
+      float4 x = sm[t], y = sm[t + s * R];
+      DF2 a{make_float2(x.x, x.y), make_float2(x.z, x.w)};
+      df_add(a, DF2{make_float2(y.x, y.y), make_float2(y.z, y.w)});
+      sm[t] = make_float4(a.s.x, a.s.y, a.c.x, a.c.y);
+    }
+    __syncthreads();
+  }
+  if (q == 0) {
+    float4 *o = part + ((long)blockIdx.x * R + t) * 2;
+    o[0] = sm[t];
+    o[1] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+}
+
+// acc += x * y componentwise, x = xh + xl a double-float, y a float
+__device__ __forceinline__ void df_acc1(DF2 &acc, float2 xh, float2 xl, float2 y) {
+  float2 p = __fmul2_rn(xh, y);
+  float2 e = __ffma2_rn(xh, y, neg2(p));
+  e = __ffma2_rn(xl, y, e);
+  float2 s, t;
+  two_sum2(acc.s, p, s, t);
+  renorm2(s, add2(t, add2(acc.c, e)), acc);
+}
+
+// the restart update x += sum_k Z_k y_k[r] (x FP64, Z the FP32 cycle
+// outputs, y as pre-broadcast double-floats from k_trisolve): the sum in
+// double-float, added to x in FP64 (the float parts widened exactly on the
+// integer pipes)
+__global__ void __launch_bounds__(256) k_xupd_df(const zf *__restrict__ Z, long zstride, int kc,
+                                                 const float4 *__restrict__ coef, zd *__restrict__ x, long E, int R) {
   long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= E) return;
   int r = (int)(e % R);
   DF2 P{make_float2(0.f, 0.f), make_float2(0.f, 0.f)}, Q = P;
-  auto step = [&](float4 v, float4 c0, float4 c1) {
-    float2 vh = make_float2(v.x, v.y), vl = make_float2(v.z, v.w);
-    df_acc(P, make_float2(c0.x, c0.y), make_float2(c0.z, c0.w), vh, vl);
-    df_acc(Q, make_float2(c1.x, c1.y), make_float2(c1.z, c1.w), vh, vl);
+  auto step = [&](zf z, float4 c0, float4 c1) {
+    float2 zv = make_float2(z.re, z.im);
+    df_acc1(P, make_float2(c0.x, c0.y), make_float2(c0.z, c0.w), zv);
+    df_acc1(Q, make_float2(c1.x, c1.y), make_float2(c1.z, c1.w), zv);
   };
   int k = 0;
   for (; k + 4 <= kc; k += 4) {
-    float4 v[4], c[4][2];
+    zf v[4];
+    float4 c[4][2];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) v[u] = ld4(V + (k + u) * vstride + e);
+    for (int u = 0; u < 4; ++u) v[u] = Z[(k + u) * zstride + e];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const float4 *cp = coef + ((long)(k + u) * R + r) * 2;
@@ -466,13 +516,13 @@ __global__ void __launch_bounds__(256) k_maxpy_df(const zdf *__restrict__ V, lon
   }
   for (; k < kc; ++k) {
     const float4 *cp = coef + ((long)k * R + r) * 2;
-    step(ld4(V + k * vstride + e), cp[0], cp[1]);
+    step(Z[k * zstride + e], cp[0], cp[1]);
   }
   df_add(P, DF2{swap2(Q.s), swap2(Q.c)});
-  float4 wv = ld4(w + e);
-  DF2 W{make_float2(wv.x, wv.y), make_float2(wv.z, wv.w)};
-  df_add(W, DF2{neg2(P.s), neg2(P.c)});
-  st4(w + e, W.s, W.c);
+  zd xv = x[e];
+  xv.re += f2d(P.s.x) + f2d(P.c.x);
+  xv.im += f2d(P.s.y) + f2d(P.c.y);
+  x[e] = xv;
 }
 
 // v_{j+1} = f[rhs] w in double-float and its FP32 copy (the next cycle's
@@ -567,7 +617,8 @@ __global__ void k_givens(KS k, int j, double tol) {
 }
 
 // y = H^-1 g (upper triangular, jend columns), zero beyond jend / inactive
-__global__ void k_trisolve(KS k) {
+// (with df, y also as double-float coefficients for k_xupd_df, in hpd)
+__global__ void k_trisolve(KS k, int df) {
   int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= k.nrhs) return;
   int m = k.m, je = k.active[r] ? k.jend[r] : 0;
@@ -586,6 +637,8 @@ __global__ void k_trisolve(KS k) {
     y[i] = (dn > 0) ? mk((s.re * d.re + s.im * d.im) / dn, (s.im * d.re - s.re * d.im) / dn) : mk(0.0, 0.0);
   }
   for (int i = 0; i < m; ++i) k.yT[(long)i * k.nrhs + r] = y[i];
+  if (df)
+    for (int i = 0; i < m; ++i) put_coef_df(k.hpd + ((long)i * k.nrhs + r) * 2, y[i]);
 }
 
 // start of a cycle: beta = ||r||, inv = active ? 1/beta : 0, g = (beta, 0..)
@@ -676,9 +729,12 @@ static int mdots_df(wl_amg *a, const zdf *V, long vstride, int kc, const zdf *w,
   return WL_OK;
 }
 
-static int norms2_df(wl_amg *a, const zdf *w, long E, int R, zd *tmp, double *out, cudaStream_t s) {
+
+// w -= sum_k V_k coef_k and out[r] = |w_r|^2 in one pass (double-float)
+static int maxpy_norm_df(wl_amg *a, const zdf *V, long vstride, int kc, const float4 *coef, zdf *w, long E, int R,
+                         zd *tmp, double *out, cudaStream_t s) {
   RedCfg c = red_cfg(E, R);
-  k_norm2_df<<<c.nblk, c.nt, 0, s>>>(w, E, R, a->red.as<float4>());
+  k_maxpy_df<<<c.nblk, c.nt, 0, s>>>(V, vstride, kc, coef, w, E, R, a->red.as<float4>());
   k_mdot_final_df<<<WL_GRID(R * 32, 256), 256, 0, s>>>(a->red.as<float4>(), c.nblk, 1, R, tmp, 1, 0, 0, nullptr);
   k_re_of<<<WL_GRID(R, 128), 128, 0, s>>>(tmp, out, R);
   wl_count_launches(3);
@@ -803,19 +859,23 @@ int fg_cycle(wl_amg *a, const zd *bnorm_h, zd *xh, int nrhs, double tol, const i
     // Gram-Schmidt against v_0 .. v_j
     k_zero_hcol<<<WL_GRID(nrhs, 128), 128, 0, s>>>(k);
     wl_count_launches(1);
+    zd *tmpc = a->small.as<zd>() + (a->small.bytes / sizeof(zd)) - 2 * (size_t)nrhs - 8;
     for (int pass = 0; pass < a->prm.gs_passes; ++pass) {
       if (df) {
         WL_TRY(mdots_df(a, Vd, vs, j + 1, wd, E, nrhs, k.hcol, m + 1, 1, k.hpd, s));
-        k_maxpy_df<<<gE, 256, 0, s>>>(Vd, vs, j + 1, k.hpd, wd, E, nrhs);
+        if (pass + 1 == a->prm.gs_passes) {  // the last pass also forms |w|^2
+          WL_TRY(maxpy_norm_df(a, Vd, vs, j + 1, k.hpd, wd, E, nrhs, tmpc, k.nrm2, s));
+        } else {
+          k_maxpy_df<<<gE, 256, 0, s>>>(Vd, vs, j + 1, k.hpd, wd, E, nrhs, nullptr);
+          wl_count_launches(1);
+        }
       } else {
         WL_TRY(mdots<double>(a, V, vs, j + 1, w, E, nrhs, k.hcol, m + 1, 1, k.hpass, s));
         k_maxpy<double, 1><<<gE, 256, 0, s>>>(V, vs, j + 1, k.hpass, nrhs, w, E, nrhs);
+        wl_count_launches(1);
       }
-      wl_count_launches(1);
     }
-    zd *tmpc = a->small.as<zd>() + (a->small.bytes / sizeof(zd)) - 2 * (size_t)nrhs - 8;
-    if (df) WL_TRY(norms2_df(a, wd, E, nrhs, tmpc, k.nrm2, s));
-    else WL_TRY(norms2(a, w, E, nrhs, tmpc, k.nrm2, s));
+    if (!df) WL_TRY(norms2(a, w, E, nrhs, tmpc, k.nrm2, s));
     WL_CUDA(cudaMemsetAsync(k.running, 0, sizeof(int) * 2, s));
     k_givens<<<WL_GRID(nrhs, 128), 128, 0, s>>>(k, j, tol);
     wl_count_launches(1);
@@ -835,8 +895,9 @@ int fg_cycle(wl_amg *a, const zd *bnorm_h, zd *xh, int nrhs, double tol, const i
     jdone = j + 1;
     if (run[0] == 0) break;
   }
-  k_trisolve<<<WL_GRID(nrhs, 128), 128, 0, s>>>(k);
-  if (prec == WL_FP64) k_maxpy<double, 0><<<gE, 256, 0, s>>>(a->Z.as<zd>(), vs, jdone, k.yT, nrhs, xh, E, nrhs);
+  k_trisolve<<<WL_GRID(nrhs, 128), 128, 0, s>>>(k, df ? 1 : 0);
+  if (df) k_xupd_df<<<gE, 256, 0, s>>>(a->Z.as<zf>(), vs, jdone, k.hpd, xh, E, nrhs);
+  else if (prec == WL_FP64) k_maxpy<double, 0><<<gE, 256, 0, s>>>(a->Z.as<zd>(), vs, jdone, k.yT, nrhs, xh, E, nrhs);
   else k_maxpy<float, 0><<<gE, 256, 0, s>>>(a->Z.as<zf>(), vs, jdone, k.yT, nrhs, xh, E, nrhs);
   wl_count_launches(2);
   WL_CUDA(cudaGetLastError());
@@ -1183,7 +1244,7 @@ extern "C" int wl_time_kernel(wl_amg *a, int kind, int level, int nrhs, int prec
       }
       default:
         if (a->prm.gs_arith == 1)
-          k_maxpy_df<<<WL_GRID(E, 256), 256, 0, s>>>(a->V.as<zdf>(), E, kc, k.hpd, a->w.as<zdf>(), E, nrhs);
+          k_maxpy_df<<<WL_GRID(E, 256), 256, 0, s>>>(a->V.as<zdf>(), E, kc, k.hpd, a->w.as<zdf>(), E, nrhs, nullptr);
         else
           k_maxpy<double, 1><<<WL_GRID(E, 256), 256, 0, s>>>(a->V.as<zd>(), E, kc, k.hpass, nrhs, a->w.as<zd>(), E,
                                                               nrhs);
