@@ -518,6 +518,109 @@ __device__ __forceinline__ void tile_relax(const S *__restrict__ A, cx<T> *__res
   }
 }
 
+// The colour steps of tile_relax with each (site, right-hand side) item split
+// over a pair of adjacent lanes (FP32, paired FMAs): lane p of the pair holds
+// spin component p of r at the site's nine neighbours, forms that spin's
+// partial row products P_p, Q_p (the chains row_dot forms per spin, in the
+// same order), takes the partner's by one shuffle, and both lanes combine
+// them in row_dot's order, so every value matches tile_relax bit for bit.
+// Lane p then updates its component of r and x component p.  Half the
+// instructions per thread and twice the warps per tile: for levels where a
+// launch has few tiles and each step's latency, not issue, sets the time.
+// Thread (k, q, p) = (tid / 2R, (tid % 2R) / 2, tid % 2).  Every lane runs
+// the arithmetic (lanes past the chunk on stale shared memory, results
+// discarded) so that the shuffles see full warps.  Ends with a barrier.
+template <typename S, int R>
+__device__ __forceinline__ void tile_relax_split(const S *__restrict__ A, zf *__restrict__ x, zf *rs,
+                                                 const float *ds, S *Ar, const int *hs, int nrhs, int r0,
+                                                 int Rc) {
+  constexpr int NT = 8 * R;
+  constexpr int ROWC = 36 * (int)sizeof(S) / 16;
+  const int tid = threadIdx.x;
+  auto issue_rows = [&](int c) {
+    S *dst = Ar + (c % 3) * 4 * 36;
+    for (int e = tid; e < 4 * ROWC; e += NT) {
+      int kk = e / ROWC, c16 = e - kk * ROWC;
+      int i = (c >> 2) + 4 * (kk >> 1), j = (c & 3) + 4 * (kk & 1);
+      long h = hs[(i + 1) * KTH + j + 1];
+      cp_async((char *)(dst + kk * 36) + 16 * c16, (const char *)(A + h * 36) + 16 * c16, 16);
+    }
+  };
+  issue_rows(0);
+  cp_async_commit();
+  issue_rows(1);
+  cp_async_commit();
+  const int k = tid / (2 * R), q0 = (tid % (2 * R)) >> 1, p = tid & 1;
+  const bool act = q0 < Rc;
+  auto x_at = [&](int c) -> long {
+    int i = (c >> 2) + 4 * (k >> 1), j = (c & 3) + 4 * (k & 1);
+    return (long)hs[(i + 1) * KTH + j + 1] * 2 * nrhs + (long)p * nrhs + r0 + q0;
+  };
+  zf xp[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+    if (act) xp[u] = x[x_at(u)];
+  for (int c0 = 0; c0 < 16; c0 += 4) {
+    zf rv[9];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int c = c0 + u;
+      if (c + 2 < 16) issue_rows(c + 2);
+      cp_async_commit();
+      cp_async_wait_group<2>();
+      __syncthreads();
+      int i = (c >> 2) + 4 * (k >> 1), j = (c & 3) + 4 * (k & 1);
+      int ks = i * KT + j;
+      const S *Ah = Ar + ((c % 3) * 4 + k) * 36;
+#pragma unroll
+      for (int d = 0; d < 9; ++d) {
+        int ls = (i + d / 3) * KTH + (j + d % 3);
+        if (u > 0 && d % 3 < 2) rv[d] = rv[d + 1];
+        else rv[d] = rs[(ls * 2 + p) * R + q0];
+      }
+      zf sv[2];
+#pragma unroll
+      for (int t = 0; t < 2; ++t) {
+        zf a_[9];
+#pragma unroll
+        for (int d = 0; d < 9; ++d) a_[d] = ld<float>(Ah + d * 4 + t * 2 + p);
+        float sc = ds[2 * ks + t];
+        if (t) sc = -sc;
+        // this lane's spin: the chains of row_dot for sp = p
+        float2 pp = make_float2(0.f, 0.f), qq = pp;
+#pragma unroll
+        for (int d = 0; d < 9; ++d) {
+          float2 v = make_float2(rv[d].re, rv[d].im);
+          pp = __ffma2_rn(make_float2(a_[d].re, a_[d].re), v, pp);
+          qq = __ffma2_rn(make_float2(a_[d].im, a_[d].im), v, qq);
+        }
+        float2 po = make_float2(__shfl_xor_sync(0xffffffffu, pp.x, 1), __shfl_xor_sync(0xffffffffu, pp.y, 1));
+        float2 qo = make_float2(__shfl_xor_sync(0xffffffffu, qq.x, 1), __shfl_xor_sync(0xffffffffu, qq.y, 1));
+        float2 P0 = p ? po : pp, Q0 = p ? qo : qq, P1 = p ? pp : po, Q1 = p ? qq : qo;
+        zf num = mk((P0.x - Q0.y) - (P1.x - Q1.y), (P0.y + Q0.x) - (P1.y + Q1.x));
+        sv[t] = sc * num;
+        float sr = sv[t].re, si = sv[t].im;  // g_s g_t = +1 (s = t), -1 (s != t)
+        float2 m1 = p == t ? make_float2(-sr, -si) : make_float2(sr, si);
+        float2 m2 = p == t ? make_float2(-si, sr) : make_float2(si, -sr);
+#pragma unroll
+        for (int d = 0; d < 9; ++d) r_sub_paired(rv[d], m1, m2, a_[d]);
+      }
+      if (act) {
+        long xo = x_at(c);
+        x[xo] = xp[u] + (p ? sv[1] : sv[0]);
+        if (c + 4 < 16) xp[u] = x[x_at(c + 4)];
+      }
+#pragma unroll
+      for (int d = 0; d < 9; ++d) {
+        if (u < 3 && d % 3) continue;  // kept for the next step
+        int ls = (i + d / 3) * KTH + (j + d % 3);
+        rs[(ls * 2 + p) * R + q0] = rv[d];
+      }
+      __syncthreads();
+    }
+  }
+}
+
 // Several right-hand sides: a block of 4 R / RPT threads, thread (k, q) owns
 // site k of the current colour step and right-hand sides r0 + q + j R / RPT
 // (j < RPT), which share the stencil coefficients and the index arithmetic.
@@ -529,16 +632,17 @@ __device__ __forceinline__ void tile_relax(const S *__restrict__ A, cx<T> *__res
 // Every right-hand side sees the same operations in the same order for any
 // R, RPT and PAIRED (paired FP32 FMAs in row_dot and r_sub_paired), so the
 // variants agree bit for bit.
-template <typename T, typename S, int R, int RPT, bool PAIRED>
-__global__ void __launch_bounds__(4 * R / RPT) k_kacz_tile(Geo g, int tc, const S *__restrict__ A,
-                                                           const T *__restrict__ den, cx<T> *__restrict__ x,
-                                                           cx<T> *__restrict__ r, int nrhs, int vec, T omega) {
+// SPLIT: each item over a pair of lanes (tile_relax_split), 8 R threads.
+template <typename T, typename S, int R, int RPT, bool PAIRED, bool SPLIT = false>
+__global__ void __launch_bounds__(SPLIT ? 8 * R : 4 * R / RPT, SPLIT ? 1024 / (8 * R) : 1)
+    k_kacz_tile(Geo g, int tc, const S *__restrict__ A, const T *__restrict__ den, cx<T> *__restrict__ x,
+                cx<T> *__restrict__ r, int nrhs, int vec, T omega) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   cx<T> *rs = (cx<T> *)sm_raw;
   T *ds = (T *)(rs + KTH * KTH * 2 * R);
   S *Ar = (S *)(ds + KT * KT * 2);
   int *hs = (int *)(Ar + 3 * 4 * 36);  // site index of tile + halo site ls = KTH (i + 1) + (j + 1)
-  constexpr int NT = 4 * R / RPT;
+  constexpr int NT = SPLIT ? 8 * R : 4 * R / RPT;
   constexpr int E = 16 / (int)sizeof(cx<T>);  // complex numbers per 16-byte copy
   constexpr int CPR = R / E;                   // 16-byte pieces per staged row
   int A0, B0;
@@ -573,7 +677,12 @@ __global__ void __launch_bounds__(4 * R / RPT) k_kacz_tile(Geo g, int tc, const 
     ds[e] = omega / den[2 * h + (e & 1)];  // the step scale, once per site and spin
   }
   cp_async_commit();
-  tile_relax<T, S, R, RPT, PAIRED>(A, x, rs, ds, Ar, hs, nrhs, r0, Rc);
+  if constexpr (SPLIT) {
+    static_assert(std::is_same<T, float>::value && PAIRED && RPT == 1, "the split form is FP32 with paired FMAs");
+    tile_relax_split<S, R>(A, x, rs, ds, Ar, hs, nrhs, r0, Rc);
+  } else {
+    tile_relax<T, S, R, RPT, PAIRED>(A, x, rs, ds, Ar, hs, nrhs, r0, Rc);
+  }
   // write r back (tile and halo)
   if (vec) {
     for (int e = tid; e < KTH * KTH * 2 * CPR; e += NT) {
@@ -1190,26 +1299,33 @@ static bool tile_p_ok(const void *r, int nrhs, int R) {
          (nrhs * sizeof(cx<T>)) % 16 == 0;
 }
 
-template <typename T, typename S, int R, int RPT, bool PAIRED = false>
+template <typename T, typename S, int R, int RPT, bool PAIRED = false, bool SPLIT = false>
 static int launch_tile_r(const Level &L, const LevelOps &o, int tc, void *x, void *r, int nrhs, double omega,
                          cudaStream_t s, bool persist = false) {
-  if (persist && tile_p_ok<T>(r, nrhs, R))
-    return launch_tile_p<T, S, R, RPT, PAIRED>(L, o, tc, x, r, nrhs, omega, s);
+  if constexpr (!SPLIT) {
+    if (persist && tile_p_ok<T>(r, nrhs, R))
+      return launch_tile_p<T, S, R, RPT, PAIRED>(L, o, tc, x, r, nrhs, omega, s);
+  }
   size_t smem = tile_smem<T, S>(R);
   static std::atomic<unsigned long long> limit_set{0};  // devices whose limit is raised
-  WL_TRY(set_smem_limit((const void *)k_kacz_tile<T, S, R, RPT, PAIRED>, smem, limit_set));
+  WL_TRY(set_smem_limit((const void *)k_kacz_tile<T, S, R, RPT, PAIRED, SPLIT>, smem, limit_set));
   int vec = ((uintptr_t)r % 16 == 0) && (sizeof(T) == 8 || nrhs % 2 == 0);
   dim3 grid((L.N / (2 * KT)) * (L.N / (4 * KT)), (nrhs + R - 1) / R);
-  k_kacz_tile<T, S, R, RPT, PAIRED><<<grid, 4 * R / RPT, smem, s>>>(L.geo, tc, o.A.as<S>(), o.den.as<T>(), (cx<T> *)x,
-                                                            (cx<T> *)r, nrhs, vec, (T)omega);
+  constexpr int NT = SPLIT ? 8 * R : 4 * R / RPT;
+  k_kacz_tile<T, S, R, RPT, PAIRED, SPLIT><<<grid, NT, smem, s>>>(L.geo, tc, o.A.as<S>(), o.den.as<T>(),
+                                                                  (cx<T> *)x, (cx<T> *)r, nrhs, vec, (T)omega);
   return WL_OK;
 }
 
-// launch parameter of the tile kernel: R | RPT << 8 | P << 12 (right-hand-side
-// chunk R, right-hand sides per thread RPT, 0 reading as 1, and 8 meaning one
-// with paired FP32 FMAs; P = 1: the persistent form with double-buffered r,
-// where the chunks are full and aligned, else the one-tile-per-block form)
-static inline int tile_param(int R, int rpt, int persist = 0) { return R | (rpt << 8) | (persist << 12); }
+// launch parameter of the tile kernel: R | RPT << 8 | P << 12 | Q << 13
+// (right-hand-side chunk R, right-hand sides per thread RPT, 0 reading as 1,
+// and 8 meaning one with paired FP32 FMAs; P = 1: the persistent form with
+// double-buffered r, where the chunks are full and aligned, else the
+// one-tile-per-block form; Q = 1 (FP32, RPT 8, P 0): each item split over a
+// pair of lanes, tile_relax_split)
+static inline int tile_param(int R, int rpt, int persist = 0, int split = 0) {
+  return R | (rpt << 8) | (persist << 12) | (split << 13);
+}
 
 // default chunk: the smallest of 8, 16, 32 (FP64: 8, 16) that covers nrhs,
 // so that few lanes idle and shared memory stays below 64 KB (FP32) or
@@ -1230,12 +1346,17 @@ static int launch_tile(const Level &L, const LevelOps &o, int tc, void *x, void 
     return WL_OK;
   }
   int R = param & 255, rpt = std::max(1, (param >> 8) & 15);
-  bool pe = (param >> 12) & 1;
+  bool pe = (param >> 12) & 1, sp = (param >> 13) & 1;
   if constexpr (sizeof(T) == 8) {  // FP64: chunks up to 16, one right-hand side per thread
     if (R == 8) return launch_tile_r<T, S, 8, 1>(L, o, tc, x, r, nrhs, omega, s, pe);
     return launch_tile_r<T, S, 16, 1>(L, o, tc, x, r, nrhs, omega, s, pe);
   } else {  // rpt 8: one right-hand side per thread with paired FMAs
     bool pr = rpt == 8;
+    if (sp) {  // each item over a pair of lanes
+      if (R == 8) return launch_tile_r<T, S, 8, 1, true, true>(L, o, tc, x, r, nrhs, omega, s);
+      if (R == 16) return launch_tile_r<T, S, 16, 1, true, true>(L, o, tc, x, r, nrhs, omega, s);
+      return launch_tile_r<T, S, 32, 1, true, true>(L, o, tc, x, r, nrhs, omega, s);
+    }
     if (R == 8)
       return pr ? launch_tile_r<T, S, 8, 1, true>(L, o, tc, x, r, nrhs, omega, s, pe)
                 : launch_tile_r<T, S, 8, 1>(L, o, tc, x, r, nrhs, omega, s, pe);
@@ -1368,6 +1489,7 @@ int autotune_sweeps(wl_amg *a, int nrhs, int prec, cudaStream_t s) {
             cand.push_back(KTune{nrhs, prec, 2, tile_param(R, 1, 1), 0.f});
             if (prec != WL_FP64) cand.push_back(KTune{nrhs, prec, 2, tile_param(R, 8, 1), 0.f});
           }
+          if (prec != WL_FP64) cand.push_back(KTune{nrhs, prec, 2, tile_param(R, 8, 0, 1), 0.f});  // split pairs
         }
     } else {
       cand.push_back(KTune{nrhs, prec, 0, 0, 0.f});
@@ -1603,7 +1725,10 @@ static bool form_exists(const wl_amg *a, int level, int nrhs, int prec, int form
   const Level &L = a->lev[level];
   bool tile = a->prm.kacz_order == 1 && wl::tile_ok(L.N);
   int R = param & 255, rpt = std::max(1, (param >> 8) & 15);
-  if (param >> 13) return false;
+  if (param >> 14) return false;
+  if ((param >> 13) & 1)  // split pairs: FP32, paired FMAs, one tile per block
+    return tile && form == 2 && nrhs > 1 && prec != WL_FP64 && rpt == 8 && !((param >> 12) & 1) &&
+           (R == 8 || R == 16 || R == 32);
   return tile ? (form == 2 &&
                  (nrhs == 1 || (R == 8 && (rpt == 1 || rpt == 8)) ||
                   ((R == 16 || R == 32) && (rpt <= 2 || rpt == 8))) &&
