@@ -182,6 +182,18 @@ int amg_setup(wl_op *op, const amg_params *params, wl_amg **out);
  * are errors of the whole call. */
 int amg_solve(wl_amg *amg, const void *b, void *x, int nrhs, double tol, wl_info *info);
 
+/* amg_solve with b and x in host memory (same layout, same results bit for
+ * bit).  Each batch of up to 256 right-hand sides is copied into device
+ * staging buffers held with the hierarchy (2 x batch x L x L x 2 complex
+ * doubles, allocated on first use, freed by amg_free), solved, and copied
+ * back; with params.overlap the two lanes copy their own halves on their
+ * own streams, so one lane's copies run beside the other lane's solve.
+ * Page-locked host memory (cudaHostAlloc, cudaHostRegister) lets the copies
+ * run asynchronously; pageable memory works, with synchronous copies.  The
+ * call returns when x is written.  Errors and statuses as amg_solve, plus
+ * WL_OOM for the staging buffers. */
+int amg_solve_host(wl_amg *amg, const void *b, void *x, int nrhs, double tol, wl_info *info);
+
 /* Hierarchy file: header "WLAMGH01", version, levels, N_l, B_l, m, gauge
  * checksum, interpolation weights of every non-coarsest level and coarse
  * stencils of levels >= 1 (complex128, layouts above), FNV-1a 64 checksum.

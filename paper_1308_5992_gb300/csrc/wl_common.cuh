@@ -283,6 +283,7 @@ struct wl_amg {
   int cap;        // right-hand sides the workspace holds
   int cap_prec;   // precision the cycle buffers were sized for
   DBuf V, Z, w, bh, xh, rr;
+  DBuf sb, sx;    // device staging of amg_solve_host's b and x (one batch)
   DBuf red;       // reduction partials
   DBuf small;     // per-rhs scalars (Hessenberg, Givens, flags)
   DBuf pinned_small;  // host-pinned mirror of flags

@@ -400,6 +400,8 @@ void amg_free(wl_amg *a) {
   a->bh.release();
   a->xh.release();
   a->rr.release();
+  a->sb.release();
+  a->sx.release();
   a->red.release();
   a->small.release();
   if (a->h_small) cudaFreeHost(a->h_small);

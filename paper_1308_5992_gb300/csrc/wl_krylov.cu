@@ -1092,12 +1092,29 @@ static int combine(int a, int b) {
   return (a || b) ? WL_NOT_CONVERGED : WL_OK;
 }
 
-// two halves of the batch at the same time: the first on a's stream in this
-// thread, the second on the twin's stream in a second host thread (both
-// drive their own FGMRES, with their own host synchronisations), so one
-// half's FP64 Gram-Schmidt kernels can share the GPU with the other half's
-// FP32 cycle
-static int solve_two_lanes(wl_amg *a, const zd *bb, zd *xx, int nb, double tol, wl_info *info) {
+// the host-buffer form of solve_lane: b (and x, unless zero_guess) copied to
+// the device staging db / dx on the lane's stream, solved there, x copied
+// back on the same stream, so one lane's copies overlap the other lane's
+// solve
+static int solve_lane_host(wl_amg *L, const zd *hb, zd *hx, zd *db, zd *dx, int n, double tol, wl_info *info) {
+  cudaStream_t s = L->op->stream;
+  size_t bytes = sizeof(zd) * (size_t)L->op->N * L->op->N * 2 * n;
+  WL_CUDA(cudaMemcpyAsync(db, hb, bytes, cudaMemcpyHostToDevice, s));
+  if (!L->prm.zero_guess) WL_CUDA(cudaMemcpyAsync(dx, hx, bytes, cudaMemcpyHostToDevice, s));
+  int rc = solve_lane(L, db, dx, n, tol, info);
+  if (rc < 0 && rc != WL_NAN) return rc;
+  WL_CUDA(cudaMemcpyAsync(hx, dx, bytes, cudaMemcpyDeviceToHost, s));
+  WL_CUDA(cudaStreamSynchronize(s));
+  return rc;
+}
+
+// two halves of the batch at the same time: lane(L, r0, n, info) for the
+// first half on a's stream in this thread, for the second on the twin's
+// stream in a second host thread (both drive their own FGMRES, with their
+// own host synchronisations), so one half's Gram-Schmidt kernels can share
+// the GPU with the other half's cycle
+template <class Lane>
+static int run_two_lanes(wl_amg *a, int nb, wl_info *info, Lane lane) {
   if (!a->twin) {
     a->twin = wl::make_twin(a);
     if (!a->twin) return WL_ECUDA;
@@ -1108,7 +1125,6 @@ static int solve_two_lanes(wl_amg *a, const zd *bb, zd *xx, int nb, double tol, 
   t->prm.overlap = 0;
   t->cap = keep_cap;
   const int h0 = (nb + 1) / 2, h1 = nb - h0, prec = a->prm.precision;
-  const size_t fs = (size_t)a->op->N * a->op->N * 2;
   // Workspaces, launch forms and cycle graphs of both lanes are made here,
   // before the second thread starts, so that neither lane times kernels or
   // captures a graph while the other one runs.  The twin takes a's launch
@@ -1144,10 +1160,10 @@ static int solve_two_lanes(wl_amg *a, const zd *bb, zd *xx, int nb, double tol, 
       err1 = "second solve lane: cudaSetDevice failed";
       return;
     }
-    rc1 = solve_lane(t, bb + h0 * fs, xx + h0 * fs, h1, tol, info ? info + h0 : nullptr);
+    rc1 = lane(t, h0, h1, info ? info + h0 : nullptr);
     if (rc1 < 0 && rc1 != WL_NAN) err1 = wl_last_error();
   });
-  int rc0 = solve_lane(a, bb, xx, h0, tol, info);
+  int rc0 = lane(a, 0, h0, info);
   th.join();
   if (rc1 < 0 && rc1 != WL_NAN) {
     wl_set_error("%s", err1.c_str());
@@ -1157,6 +1173,13 @@ static int solve_two_lanes(wl_amg *a, const zd *bb, zd *xx, int nb, double tol, 
   if (rc0 == WL_NAN || rc1 == WL_NAN)
     wl_set_error("non-finite residual for some right-hand sides");
   return combine(rc0, rc1);
+}
+
+static int solve_two_lanes(wl_amg *a, const zd *bb, zd *xx, int nb, double tol, wl_info *info) {
+  const size_t fs = (size_t)a->op->N * a->op->N * 2;
+  return run_two_lanes(a, nb, info, [&](wl_amg *L, int r0, int n, wl_info *inf) {
+    return solve_lane(L, bb + r0 * fs, xx + r0 * fs, n, tol, inf);
+  });
 }
 
 extern "C" int amg_solve(wl_amg *a, const void *b, void *x, int nrhs, double tol, wl_info *info) {
@@ -1175,6 +1198,37 @@ extern "C" int amg_solve(wl_amg *a, const void *b, void *x, int nrhs, double tol
     zd *xx = (zd *)x + (size_t)r0 * N * N * 2;
     int rc = (a->prm.overlap && nb >= 32) ? solve_two_lanes(a, bb, xx, nb, tol, info ? info + r0 : nullptr)
                                           : solve_lane(a, bb, xx, nb, tol, info ? info + r0 : nullptr);
+    if (rc < 0 && rc != WL_NAN) return rc;
+    status = combine(status, rc);
+  }
+  WL_CUDA(cudaStreamSynchronize(s));
+  if (wl::tile_timeout_take(s)) return WL_TIMEOUT;
+  return status;
+}
+
+extern "C" int amg_solve_host(wl_amg *a, const void *b, void *x, int nrhs, double tol, wl_info *info) {
+  if (!a || !b || !x || nrhs < 1 || !(tol > 0)) {
+    wl_set_error("amg_solve_host: invalid argument");
+    return WL_EINVAL;
+  }
+  wl_op *op = a->op;
+  WL_TRY(wl::enter(op));
+  cudaStream_t s = op->stream;
+  const size_t fs = (size_t)op->N * op->N * 2;
+  const int nbmax = std::min(MAX_BATCH, nrhs);
+  WL_TRY(a->sb.alloc(sizeof(zd) * fs * nbmax));
+  WL_TRY(a->sx.alloc(sizeof(zd) * fs * nbmax));
+  zd *db = a->sb.as<zd>(), *dx = a->sx.as<zd>();
+  int status = WL_OK;
+  for (int r0 = 0; r0 < nrhs; r0 += MAX_BATCH) {
+    int nb = std::min(MAX_BATCH, nrhs - r0);
+    const zd *hb = (const zd *)b + (size_t)r0 * fs;
+    zd *hx = (zd *)x + (size_t)r0 * fs;
+    auto lane = [&](wl_amg *L, int q0, int n, wl_info *inf) {
+      return solve_lane_host(L, hb + q0 * fs, hx + q0 * fs, db + q0 * fs, dx + q0 * fs, n, tol, inf);
+    };
+    wl_info *ib = info ? info + r0 : nullptr;
+    int rc = (a->prm.overlap && nb >= 32) ? run_two_lanes(a, nb, ib, lane) : lane(a, 0, nb, ib);
     if (rc < 0 && rc != WL_NAN) return rc;
     status = combine(status, rc);
   }

@@ -77,6 +77,7 @@ def lib():
             "wl_eo_reconstruct": (i, [P, P, P, P, i]),
             "amg_setup": (i, [P, C.POINTER(amg_params), C.POINTER(P)]),
             "amg_solve": (i, [P, P, P, i, d, C.POINTER(wl_info)]),
+            "amg_solve_host": (i, [P, P, P, i, d, C.POINTER(wl_info)]),
             "amg_export": (i, [P, C.c_char_p]),
             "amg_import": (i, [P, C.c_char_p, C.POINTER(amg_params), C.POINTER(P)]),
             "amg_destroy": (None, [P]),
@@ -331,6 +332,31 @@ def amg_solve(amg, b, x, nrhs, tol):
     info = (wl_info * nrhs)()
     rc = _chk(lib().amg_solve(amg.handle, _buf(b, need, op.device, "b"), _buf(x, need, op.device, "x"), nrhs,
                               tol, info), "amg_solve", ok=(WL_OK, WL_NOT_CONVERGED, WL_NAN))
+    return rc, [i.as_dict() for i in info]
+
+
+def _host_buf(t, need, what):
+    """Host pointer of t after checking that t is a contiguous complex128 CPU
+    tensor with at least `need` elements (page-locked memory lets the
+    library's copies run asynchronously)."""
+    import torch
+    if not isinstance(t, torch.Tensor) or t.is_cuda:
+        raise TypeError("%s: expected a CPU tensor" % what)
+    if t.dtype != torch.complex128 or not t.is_contiguous():
+        raise TypeError("%s: expected a contiguous complex128 tensor" % what)
+    if t.numel() < need:
+        raise ValueError("%s holds %d complex values, the call needs %d" % (what, t.numel(), need))
+    return C.c_void_p(t.data_ptr())
+
+
+def amg_solve_host(amg, b, x, nrhs, tol):
+    """amg_solve with b and x in host memory (CPU tensors, ideally pinned):
+    the library copies them in and out, overlapping one solve lane's copies
+    with the other lane's solve."""
+    need = _full(amg.op, nrhs)
+    info = (wl_info * nrhs)()
+    rc = _chk(lib().amg_solve_host(amg.handle, _host_buf(b, need, "b"), _host_buf(x, need, "x"), nrhs, tol, info),
+              "amg_solve_host", ok=(WL_OK, WL_NOT_CONVERGED, WL_NAN))
     return rc, [i.as_dict() for i in info]
 
 

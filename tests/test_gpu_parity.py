@@ -519,6 +519,32 @@ def test_two_lane_solve(O, shared, name, nb, order):
         assert np.linalg.norm(H(x1[q]) - ref) / np.linalg.norm(ref) <= 1e-10, q
 
 
+@pytest.mark.parametrize("overlap,nb,pinned,zero", [(0, 3, True, 1), (1, 40, True, 1), (1, 33, False, 0)])
+def test_solve_with_host_buffers(shared, overlap, nb, pinned, zero):
+    """amg_solve_host (b and x in host memory, copied by the library, one
+    lane's copies beside the other lane's solve) gives the device call's
+    solution bit for bit, from pinned or pageable memory, with a zero or a
+    given initial guess."""
+    w, op, h, _, path = shared("T64")
+    N = w["N"]
+    p = W.amg_params_default(zero_guess=zero, precision=W.WL_FP32, overlap=overlap, arnoldi_matvec=1, gs_arith=1)
+    amg = W.amg_import(op, path, p)
+    b = rhs_batch(N, nb, 41)
+    x0 = 0.01 * rhs_batch(N, nb, 42)
+    xd = T(x0)
+    rcd, infd = W.amg_solve(amg, T(b), xd, nb, 1e-12)
+    bh = torch.from_numpy(np.ascontiguousarray(b))
+    xh = torch.from_numpy(np.ascontiguousarray(x0))
+    if pinned:
+        bh, xh = bh.pin_memory(), xh.pin_memory()
+    rch, infh = W.amg_solve_host(amg, bh, xh, nb, 1e-12)
+    assert rcd == rch == W.WL_OK
+    assert [i["iters"] for i in infh] == [i["iters"] for i in infd]
+    assert np.array_equal(xh.numpy(), H(xd))
+    with pytest.raises(TypeError):
+        W.amg_solve_host(amg, T(b), xh, nb, 1e-12)  # a device tensor
+
+
 def test_fp64_fma_probe(shared):
     """wl_time_kernel's FP64 FMA probe (the check on the derived FP64 peak
     that the Gram-Schmidt roofline uses) runs and reports a rate below the
