@@ -774,7 +774,11 @@ static void kaczmarz_update(const or_csr *AT, int i, cplx *x, cplx *r, double om
  * tile (ta, tb) = (a / T, b / T) of the fundamental domain a in [0, N),
  * b in [0, N/2), with tile colour (ta mod 2) + 2 (tb mod 2).  The sweep takes
  * tile colours 0..3 in turn; inside a tile it takes the 16 site colours
- * 0..15 in turn (sites in increasing (a, b), spin 0 then 1).  Variables of a
+ * 4 (a mod 4) + (b mod 4) along the 4 x 4 colour grid row by row, even rows
+ * left to right and odd rows right to left (serpentine: 0 1 2 3 7 6 5 4
+ * 8 9 10 11 15 14 13 12), sites of a colour in increasing (a, b), spin 0
+ * then 1.  Any order of the colours is a multicolour ordering; in this one
+ * the sites of consecutive colours are neighbours in a row or a column.  Variables of a
  * site touch only its 3x3 (a, b) box, so tiles of one colour (one tile
  * apart) are independent.  T = 8 when N >= 64 (then 4T divides N, which
  * keeps the tile colouring consistent across the seam b = N/2 ~ 0);
@@ -788,7 +792,8 @@ static void tile_sweep(const or_csr *AT, int N, cplx *x, cplx *r, double omega) 
     for (int ta = 0; ta < N / T; ++ta)
       for (int tb = 0; tb < N / (2 * T); ++tb) {
         if ((ta & 1) + 2 * (tb & 1) != tc) continue;
-        for (int c = 0; c < 16; ++c)
+        for (int s = 0; s < 16; ++s) {
+          int row = s / 4, col = (row % 2) ? 3 - s % 4 : s % 4, c = 4 * row + col;
           for (int i = 0; i < T; ++i)
             for (int j = 0; j < T; ++j) {
               int a = ta * T + i, b = tb * T + j;
@@ -797,6 +802,7 @@ static void tile_sweep(const or_csr *AT, int N, cplx *x, cplx *r, double omega) 
               kaczmarz_update(AT, 2 * site, x, r, omega);
               kaczmarz_update(AT, 2 * site + 1, x, r, omega);
             }
+        }
       }
 }
 

@@ -298,6 +298,34 @@ __device__ __forceinline__ void ld2(const zb *p, cx<T> &a0, cx<T> &a1) {
   a1 = ld<T>(p + 1);
 }
 
+// Colour of step s of a tile sweep: the 4 x 4 grid of site colours
+// 4 (a mod 4) + (b mod 4) row by row, rows alternately left to right and
+// right to left (serpentine), so that the sites of consecutive steps of a
+// quadrant are neighbours in a row or a column.
+__host__ __device__ constexpr int tile_step_colour(int s) {
+  return 4 * (s >> 2) + (((s >> 2) & 1) ? 3 - (s & 3) : (s & 3));
+}
+// how the site of step s > 0 lies from the site of step s - 1: 1 one column
+// right, 2 one column left, 3 one row down
+__host__ __device__ constexpr int tile_step_move(int s) {
+  return (s & 3) == 0 ? 3 : (((s >> 2) & 1) ? 2 : 1);
+}
+// window cell d = 3 da + db of step s - 1 that holds cell d of step s after
+// the move (-1: a cell new to the window, read from shared memory)
+__host__ __device__ constexpr int tile_window_src(int s, int d) {
+  return tile_step_move(s) == 1 ? (d % 3 < 2 ? d + 1 : -1)
+         : tile_step_move(s) == 2 ? (d % 3 > 0 ? d - 1 : -1)
+                                  : (d / 3 < 2 ? d + 3 : -1);
+}
+// whether window cell d of step s leaves the window at the next move (all
+// cells after the last step)
+__host__ __device__ constexpr bool tile_window_leaves(int s, int d) {
+  return s == 15 ? true
+         : tile_step_move(s + 1) == 1 ? d % 3 == 0
+         : tile_step_move(s + 1) == 2 ? d % 3 == 2
+                                      : d / 3 == 0;
+}
+
 // origin of tile `t` of tile colour tc
 __device__ __forceinline__ void tile_origin(const Geo &g, int tc, int t, int &A0, int &B0) {
   int nb4 = g.N / (4 * KT);  // tiles of one colour along b
@@ -376,7 +404,8 @@ __device__ __forceinline__ void r_sub_paired(cx<float> &rv, float2 m1, float2 m2
   rv = mk(v.x, v.y);
 }
 
-// The 16 colour steps of one tile (thread (k, q): quadrant k, right-hand
+// The 16 colour steps of one tile, in the order tile_step_colour gives
+// (thread (k, q): quadrant k, right-hand
 // sides r0 + q + j R / RPT), on r of tile + halo staged in rs ([100][2][R],
 // visible to every thread after the first barrier below), the step scales
 // ds [64][2] and the site-index table hs [100] of the tile; the stencil rows
@@ -390,9 +419,10 @@ __device__ __forceinline__ void tile_relax(const S *__restrict__ A, cx<T> *__res
   constexpr int RQ = R / RPT;                     // threads per site
   constexpr int ROWC = 36 * (int)sizeof(S) / 16;  // 16-byte pieces of a stencil row
   const int tid = threadIdx.x;
-  // stencil rows of colour step c (its four sites, quadrant order) -> ring slot c % 3
-  auto issue_rows = [&](int c) {
-    S *dst = Ar + (c % 3) * 4 * 36;
+  // stencil rows of step st (its four sites, quadrant order) -> ring slot st % 3
+  auto issue_rows = [&](int st) {
+    S *dst = Ar + (st % 3) * 4 * 36;
+    const int c = tile_step_colour(st);
     for (int e = tid; e < 4 * ROWC; e += NT) {
       int kk = e / ROWC, c16 = e - kk * ROWC;
       int i = (c >> 2) + 4 * (kk >> 1), j = (c & 3) + 4 * (kk & 1);
@@ -408,10 +438,11 @@ __device__ __forceinline__ void tile_relax(const S *__restrict__ A, cx<T> *__res
   bool act[RPT];
 #pragma unroll
   for (int m = 0; m < RPT; ++m) act[m] = q0 + m * RQ < Rc;
-  // thread (k, q) visits quadrant k of the tile, one site per colour step;
-  // x of the site four steps ahead is loaded while the current step runs
-  // (a ring of four), so the HBM latency of x is off the step's critical path
-  auto x_at = [&](int c) -> long {
+  // thread (k, q) visits quadrant k of the tile, one site per step; x of the
+  // site four steps ahead is loaded while the current step runs (a ring of
+  // four), so the HBM latency of x is off the step's critical path
+  auto x_at = [&](int st) -> long {
+    const int c = tile_step_colour(st);
     int i = (c >> 2) + 4 * (k >> 1), j = (c & 3) + 4 * (k & 1);
     return (long)hs[(i + 1) * KTH + j + 1] * 2 * nrhs + r0 + q0;
   };
@@ -426,95 +457,102 @@ __device__ __forceinline__ void tile_relax(const S *__restrict__ A, cx<T> *__res
         xp[u][m][1] = x[xo + m * RQ + nrhs];
       }
   }
-  // Steps 4 i' .. 4 i' + 3 walk row i' of every quadrant.  Along a row the
-  // 3x3 window of r around the site (rows da, columns db) slides by one
-  // column: the columns that stay are kept in registers, one new column is
-  // read and the column that leaves is written back (the whole window at
-  // the row's end).  No other thread touches a kept cell meanwhile: at every
-  // step the four quadrants' windows are disjoint, and the kept cells lie in
-  // this thread's windows of both steps.  Two thirds of the shared-memory
-  // traffic of r go away; the arithmetic and its order are unchanged.
-  for (int c0 = 0; c0 < 16; c0 += 4) {
-    cx<T> rv[RPT][9][2];
+  // The 3x3 window of r around the site (rows da, columns db) follows the
+  // serpentine path: at every step it moves by one row or one column, the
+  // six cells that stay are kept in registers, three new ones are read and
+  // the three that leave are written back (the whole window after the last
+  // step).  No other thread touches a kept cell meanwhile: at every step the
+  // four quadrants' windows are disjoint, and the kept cells lie in this
+  // thread's windows of both steps.  Two thirds of the shared-memory traffic
+  // of r go away; the arithmetic and its order are unchanged.
+  cx<T> rv[RPT][9][2];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int c = c0 + u;
-      // the slot of step c + 2 was last read in step c - 1, which ended with a barrier
-      if (c + 2 < 16) issue_rows(c + 2);
-      cp_async_commit();
-      cp_async_wait_group<2>();  // everything but the two newest groups: r, rows of step c
-      __syncthreads();
-      int i = (c >> 2) + 4 * (k >> 1), j = (c & 3) + 4 * (k & 1);
-      if (act[0]) {
-        int ks = i * KT + j;
-        const S *Ah = Ar + ((c % 3) * 4 + k) * 36;
+  for (int st = 0; st < 16; ++st) {
+    const int c = tile_step_colour(st), u = st & 3;
+    // the slot of step st + 2 was last read in step st - 1, which ended with a barrier
+    if (st + 2 < 16) issue_rows(st + 2);
+    cp_async_commit();
+    cp_async_wait_group<2>();  // everything but the two newest groups: r, rows of step st
+    __syncthreads();
+    int i = (c >> 2) + 4 * (k >> 1), j = (c & 3) + 4 * (k & 1);
+    if (act[0]) {
+      int ks = i * KT + j;
+      const S *Ah = Ar + ((st % 3) * 4 + k) * 36;
+      cx<T> ov[RPT][9][2];
+#pragma unroll
+      for (int m = 0; m < RPT; ++m)
 #pragma unroll
         for (int d = 0; d < 9; ++d) {
-          int ls = (i + d / 3) * KTH + (j + d % 3);  // (i + da + 1, j + db + 1)
-#pragma unroll
-          for (int m = 0; m < RPT; ++m) {
-            if (u > 0 && d % 3 < 2) {  // column db + 1 of the previous step
-              rv[m][d][0] = rv[m][d + 1][0];
-              rv[m][d][1] = rv[m][d + 1][1];
-            } else {
-              rv[m][d][0] = rs[(ls * 2) * R + q0 + m * RQ];
-              rv[m][d][1] = rs[(ls * 2 + 1) * R + q0 + m * RQ];
-            }
-          }
+          ov[m][d][0] = rv[m][d][0];
+          ov[m][d][1] = rv[m][d][1];
         }
-        cx<T> sv[RPT][2];
 #pragma unroll
-        for (int t = 0; t < 2; ++t) {
-          cx<T> a_[9][2];
-#pragma unroll
-          for (int d = 0; d < 9; ++d) ld2<T>(Ah + d * 4 + t * 2, a_[d][0], a_[d][1]);
-          T sc = ds[2 * ks + t];
-          if (t) sc = -sc;
-#pragma unroll
-          for (int m = 0; m < RPT; ++m) {
-            sv[m][t] = sc * row_dot<T, PAIRED>(a_, rv[m]);
-            if constexpr (PAIRED) {
-              float sr = sv[m][t].re, si = sv[m][t].im;  // g_s g_t = +1 (s = t), -1 (s != t)
-              float2 m1p = make_float2(-sr, -si), m2p = make_float2(-si, sr);
-              float2 m1n = make_float2(sr, si), m2n = make_float2(si, -sr);
-#pragma unroll
-              for (int d = 0; d < 9; ++d)
-#pragma unroll
-                for (int sp = 0; sp < 2; ++sp)
-                  r_sub_paired(rv[m][d][sp], sp == t ? m1p : m1n, sp == t ? m2p : m2n, a_[d][sp]);
-            } else {
-#pragma unroll
-              for (int d = 0; d < 9; ++d)
-#pragma unroll
-                for (int sp = 0; sp < 2; ++sp) r_sub(rv[m][d][sp], (sp == t) ? (T)1 : (T)-1, sv[m][t], a_[d][sp]);
-            }
-          }
-        }
-        long xo = x_at(c), xn = c + 4 < 16 ? x_at(c + 4) : 0;
+      for (int d = 0; d < 9; ++d) {
+        int ls = (i + d / 3) * KTH + (j + d % 3);  // (i + da + 1, j + db + 1)
+        const int src = st > 0 ? tile_window_src(st, d) : -1;
 #pragma unroll
         for (int m = 0; m < RPT; ++m) {
-          if (!act[m]) continue;
-          x[xo + m * RQ] = xp[u][m][0] + sv[m][0];
-          x[xo + m * RQ + nrhs] = xp[u][m][1] + sv[m][1];
-          if (c + 4 < 16) {
-            xp[u][m][0] = x[xn + m * RQ];
-            xp[u][m][1] = x[xn + m * RQ + nrhs];
+          if (src >= 0) {  // kept from the previous step's window
+            rv[m][d][0] = ov[m][src][0];
+            rv[m][d][1] = ov[m][src][1];
+          } else {
+            rv[m][d][0] = rs[(ls * 2) * R + q0 + m * RQ];
+            rv[m][d][1] = rs[(ls * 2 + 1) * R + q0 + m * RQ];
           }
         }
+      }
+      cx<T> sv[RPT][2];
 #pragma unroll
-        for (int d = 0; d < 9; ++d) {
-          if (u < 3 && d % 3) continue;  // kept for the next step
-          int ls = (i + d / 3) * KTH + (j + d % 3);
+      for (int t = 0; t < 2; ++t) {
+        cx<T> a_[9][2];
 #pragma unroll
-          for (int m = 0; m < RPT; ++m)
-            if (act[m]) {
-              rs[(ls * 2) * R + q0 + m * RQ] = rv[m][d][0];
-              rs[(ls * 2 + 1) * R + q0 + m * RQ] = rv[m][d][1];
-            }
+        for (int d = 0; d < 9; ++d) ld2<T>(Ah + d * 4 + t * 2, a_[d][0], a_[d][1]);
+        T sc = ds[2 * ks + t];
+        if (t) sc = -sc;
+#pragma unroll
+        for (int m = 0; m < RPT; ++m) {
+          sv[m][t] = sc * row_dot<T, PAIRED>(a_, rv[m]);
+          if constexpr (PAIRED) {
+            float sr = sv[m][t].re, si = sv[m][t].im;  // g_s g_t = +1 (s = t), -1 (s != t)
+            float2 m1p = make_float2(-sr, -si), m2p = make_float2(-si, sr);
+            float2 m1n = make_float2(sr, si), m2n = make_float2(si, -sr);
+#pragma unroll
+            for (int d = 0; d < 9; ++d)
+#pragma unroll
+              for (int sp = 0; sp < 2; ++sp)
+                r_sub_paired(rv[m][d][sp], sp == t ? m1p : m1n, sp == t ? m2p : m2n, a_[d][sp]);
+          } else {
+#pragma unroll
+            for (int d = 0; d < 9; ++d)
+#pragma unroll
+              for (int sp = 0; sp < 2; ++sp) r_sub(rv[m][d][sp], (sp == t) ? (T)1 : (T)-1, sv[m][t], a_[d][sp]);
+          }
         }
       }
-      __syncthreads();
+      long xo = x_at(st), xn = st + 4 < 16 ? x_at(st + 4) : 0;
+#pragma unroll
+      for (int m = 0; m < RPT; ++m) {
+        if (!act[m]) continue;
+        x[xo + m * RQ] = xp[u][m][0] + sv[m][0];
+        x[xo + m * RQ + nrhs] = xp[u][m][1] + sv[m][1];
+        if (st + 4 < 16) {
+          xp[u][m][0] = x[xn + m * RQ];
+          xp[u][m][1] = x[xn + m * RQ + nrhs];
+        }
+      }
+#pragma unroll
+      for (int d = 0; d < 9; ++d) {
+        if (!tile_window_leaves(st, d)) continue;  // kept for the next step
+        int ls = (i + d / 3) * KTH + (j + d % 3);
+#pragma unroll
+        for (int m = 0; m < RPT; ++m)
+          if (act[m]) {
+            rs[(ls * 2) * R + q0 + m * RQ] = rv[m][d][0];
+            rs[(ls * 2 + 1) * R + q0 + m * RQ] = rv[m][d][1];
+          }
+      }
     }
+    __syncthreads();
   }
 }
 
@@ -537,8 +575,9 @@ __device__ __forceinline__ void tile_relax_split(const S *__restrict__ A, zf *__
   constexpr int NT = 8 * R;
   constexpr int ROWC = 36 * (int)sizeof(S) / 16;
   const int tid = threadIdx.x;
-  auto issue_rows = [&](int c) {
-    S *dst = Ar + (c % 3) * 4 * 36;
+  auto issue_rows = [&](int st) {
+    S *dst = Ar + (st % 3) * 4 * 36;
+    const int c = tile_step_colour(st);
     for (int e = tid; e < 4 * ROWC; e += NT) {
       int kk = e / ROWC, c16 = e - kk * ROWC;
       int i = (c >> 2) + 4 * (kk >> 1), j = (c & 3) + 4 * (kk & 1);
@@ -552,7 +591,8 @@ __device__ __forceinline__ void tile_relax_split(const S *__restrict__ A, zf *__
   cp_async_commit();
   const int k = tid / (2 * R), q0 = (tid % (2 * R)) >> 1, p = tid & 1;
   const bool act = q0 < Rc;
-  auto x_at = [&](int c) -> long {
+  auto x_at = [&](int st) -> long {
+    const int c = tile_step_colour(st);
     int i = (c >> 2) + 4 * (k >> 1), j = (c & 3) + 4 * (k & 1);
     return (long)hs[(i + 1) * KTH + j + 1] * 2 * nrhs + (long)p * nrhs + r0 + q0;
   };
@@ -560,22 +600,26 @@ __device__ __forceinline__ void tile_relax_split(const S *__restrict__ A, zf *__
 #pragma unroll
   for (int u = 0; u < 4; ++u)
     if (act) xp[u] = x[x_at(u)];
-  for (int c0 = 0; c0 < 16; c0 += 4) {
-    zf rv[9];
+  zf rv[9];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int c = c0 + u;
-      if (c + 2 < 16) issue_rows(c + 2);
+  for (int st = 0; st < 16; ++st) {
+    {
+      const int c = tile_step_colour(st), u = st & 3;
+      if (st + 2 < 16) issue_rows(st + 2);
       cp_async_commit();
       cp_async_wait_group<2>();
       __syncthreads();
       int i = (c >> 2) + 4 * (k >> 1), j = (c & 3) + 4 * (k & 1);
       int ks = i * KT + j;
-      const S *Ah = Ar + ((c % 3) * 4 + k) * 36;
+      const S *Ah = Ar + ((st % 3) * 4 + k) * 36;
+      zf ov[9];
+#pragma unroll
+      for (int d = 0; d < 9; ++d) ov[d] = rv[d];
 #pragma unroll
       for (int d = 0; d < 9; ++d) {
         int ls = (i + d / 3) * KTH + (j + d % 3);
-        if (u > 0 && d % 3 < 2) rv[d] = rv[d + 1];
+        const int src = st > 0 ? tile_window_src(st, d) : -1;
+        if (src >= 0) rv[d] = ov[src];
         else rv[d] = rs[(ls * 2 + p) * R + q0];
       }
       zf sv[2];
@@ -606,13 +650,13 @@ __device__ __forceinline__ void tile_relax_split(const S *__restrict__ A, zf *__
         for (int d = 0; d < 9; ++d) r_sub_paired(rv[d], m1, m2, a_[d]);
       }
       if (act) {
-        long xo = x_at(c);
+        long xo = x_at(st);
         x[xo] = xp[u] + (p ? sv[1] : sv[0]);
-        if (c + 4 < 16) xp[u] = x[x_at(c + 4)];
+        if (st + 4 < 16) xp[u] = x[x_at(st + 4)];
       }
 #pragma unroll
       for (int d = 0; d < 9; ++d) {
-        if (u < 3 && d % 3) continue;  // kept for the next step
+        if (!tile_window_leaves(st, d)) continue;  // kept for the next step
         int ls = (i + d / 3) * KTH + (j + d % 3);
         rs[(ls * 2 + p) * R + q0] = rv[d];
       }
@@ -633,8 +677,11 @@ __device__ __forceinline__ void tile_relax_split(const S *__restrict__ A, zf *__
 // R, RPT and PAIRED (paired FP32 FMAs in row_dot and r_sub_paired), so the
 // variants agree bit for bit.
 // SPLIT: each item over a pair of lanes (tile_relax_split), 8 R threads.
+// Launch bounds: one right-hand side per thread keeps 128 registers (512
+// threads per SM, four blocks of 128 at R = 32, as shared memory allows);
+// the split form keeps 85 (768 threads per SM).
 template <typename T, typename S, int R, int RPT, bool PAIRED, bool SPLIT = false>
-__global__ void __launch_bounds__(SPLIT ? 8 * R : 4 * R / RPT, SPLIT ? 1024 / (8 * R) : 1)
+__global__ void __launch_bounds__(SPLIT ? 8 * R : 4 * R / RPT, SPLIT ? 768 / (8 * R) : (RPT == 1 ? R / 8 : 1))
     k_kacz_tile(Geo g, int tc, const S *__restrict__ A, const T *__restrict__ den, cx<T> *__restrict__ x,
                 cx<T> *__restrict__ r, int nrhs, int vec, T omega) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
@@ -813,8 +860,9 @@ __global__ void __launch_bounds__(128) k_kacz_tile1(Geo g, int tc, const S *__re
   cp_async_wait_all();
   __syncthreads();
   const int k = tid >> 5, lane = tid & 31;
-  // lane 0 of warp k holds x of its quadrant's sites four colour steps ahead
-  auto x_at = [&](int c) -> long {
+  // lane 0 of warp k holds x of its quadrant's sites four steps ahead
+  auto x_at = [&](int st) -> long {
+    const int c = tile_step_colour(st);
     int i = (c >> 2) + 4 * (k >> 1), j = (c & 3) + 4 * (k & 1);
     return (long)g.idx(A0 + i + B0 + j, A0 + i - B0 - j) * 2;
   };
@@ -828,7 +876,7 @@ __global__ void __launch_bounds__(128) k_kacz_tile1(Geo g, int tc, const S *__re
   for (int c0 = 0; c0 < 16; c0 += 4) {
 #pragma unroll
    for (int u = 0; u < 4; ++u) {
-    const int c = c0 + u;
+    const int st = c0 + u, c = tile_step_colour(st);
     if (k < 4) {
       int i = (c >> 2) + 4 * (k >> 1), j = (c & 3) + 4 * (k & 1);
       int ks = i * KT + j;
@@ -852,11 +900,11 @@ __global__ void __launch_bounds__(128) k_kacz_tile1(Geo g, int tc, const S *__re
         if (t) sc = -sc;
         cx<T> sv = sc * num;
         r_sub(rv, (sp == t) ? (T)1 : (T)-1, sv, a_);
-        if (lane == 0) x[x_at(c) + t] = xp[u][t] + sv;
+        if (lane == 0) x[x_at(st) + t] = xp[u][t] + sv;
       }
-      if (lane == 0 && c + 4 < 16) {
-        xp[u][0] = x[x_at(c + 4)];
-        xp[u][1] = x[x_at(c + 4) + 1];
+      if (lane == 0 && st + 4 < 16) {
+        xp[u][0] = x[x_at(st + 4)];
+        xp[u][1] = x[x_at(st + 4) + 1];
       }
       if (act) rs[ls * 2 + sp] = rv;
     }

@@ -375,15 +375,26 @@ def _tile_order(O, N):
             for tb in range(N // (2 * T)):
                 if (ta & 1) + 2 * (tb & 1) != tc:
                     continue
-                for c in range(16):
-                    for i in range(T):
-                        for j in range(T):
-                            a, b = ta * T + i, tb * T + j
-                            if 4 * (a % 4) + (b % 4) != c:
-                                continue
-                            x, y = (a + b) % N, (a - b) % N
-                            order.append(y * (N // 2) + x // 2)
+                # site colours 4 (a mod 4) + (b mod 4), the 4 x 4 colour grid taken
+                # row by row, even rows left to right, odd rows right to left
+                for row in range(4):
+                    for col in (range(4) if row % 2 == 0 else range(3, -1, -1)):
+                        c = 4 * row + col
+                        order += _tile_colour_sites(N, T, ta, tb, c)
     return order
+
+
+def _tile_colour_sites(N, T, ta, tb, c):
+    """sites of colour c in tile (ta, tb), increasing (a, b)"""
+    out = []
+    for i in range(T):
+        for j in range(T):
+            a, b = ta * T + i, tb * T + j
+            if 4 * (a % 4) + (b % 4) != c:
+                continue
+            x, y = (a + b) % N, (a - b) % N
+            out.append(y * (N // 2) + x // 2)
+    return out
 
 
 def test_tile_order_covers_every_site_and_tiles_are_independent(O):

@@ -89,7 +89,8 @@ def tile_order(N, T=8):
             for tb in range(N // (2 * T)):
                 if (ta & 1) + 2 * (tb & 1) != tc:
                     continue
-                for c in range(16):
+                # the 4 x 4 colour grid row by row, odd rows right to left
+                for c in (0, 1, 2, 3, 7, 6, 5, 4, 8, 9, 10, 11, 15, 14, 13, 12):
                     for i in range(T):
                         for j in range(T):
                             a, b = ta * T + i, tb * T + j
