@@ -382,8 +382,9 @@ int wl_time_kernel(wl_amg *amg, int kind, int level, int nrhs, int prec, int rep
  * ((*param >> 8) & 15: 1 or 2; 8 = one per thread with paired FP32 FMAs);
  * bit 0x1000: the persistent form (r double-buffered by bulk copies); bit
  * 0x2000: each (site, right-hand side) split over a pair of lanes, one per
- * spin component (FP32, paired FMAs); 3 = one launch for all colours with a block per *param
- * right-hand sides (small levels, x and r in shared memory); *us = the autotuner's measured time of one
+ * spin component (FP32, paired FMAs); 3 = one launch for all colours with a block per
+ * (*param & 255) right-hand sides (small levels, x and r in shared memory; bit 0x100: the stencil
+ * rows and denominators in shared memory too); *us = the autotuner's measured time of one
  * sweep in microseconds, 0 when the form was not measured (explicit
  * sweep_kernel, or no cycle of that width yet).  Errors: WL_EINVAL. */
 int amg_sweep_form(wl_amg *amg, int level, int nrhs, int prec, int *form, int *param, float *us);

@@ -82,6 +82,49 @@ __device__ __forceinline__ void r_sub(cx<T> &rv, T g, cx<T> sv, cx<T> a) {
   rv.im = fma(sr, a.im, rv.im);
 }
 
+// Row inner product of a Kaczmarz step, num = sum_d a_0 r_0 - a_1 r_1
+// (complex, a_s = A[h][d][t][s], r_s of neighbour d), as eight independent
+// chains: per spin s, P_s = sum_d Re(a_s) (Re r_s, Im r_s) and
+// Q_s = sum_d Im(a_s) (Re r_s, Im r_s), then a_s r_s summed is
+// (P.re - Q.im, P.im + Q.re).  PAIRED (FP32 only) runs each (re, im) pair of
+// chains as one paired FMA (__ffma2_rn), lane for lane the same operation,
+// so both forms give the same bits.
+template <typename T, bool PAIRED>
+__device__ __forceinline__ cx<T> row_dot(const cx<T> (&a)[9][2], const cx<T> (&rv)[9][2]) {
+  cx<T> P[2], Q[2];
+  if constexpr (PAIRED) {
+    static_assert(std::is_same<T, float>::value, "paired FMAs are FP32");
+    float2 p2[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)}, q2[2] = {p2[0], p2[0]};
+#pragma unroll
+    for (int d = 0; d < 9; ++d)
+#pragma unroll
+      for (int sp = 0; sp < 2; ++sp) {
+        float2 v = make_float2(rv[d][sp].re, rv[d][sp].im);
+        p2[sp] = __ffma2_rn(make_float2(a[d][sp].re, a[d][sp].re), v, p2[sp]);
+        q2[sp] = __ffma2_rn(make_float2(a[d][sp].im, a[d][sp].im), v, q2[sp]);
+      }
+#pragma unroll
+    for (int sp = 0; sp < 2; ++sp) {
+      P[sp] = mk(p2[sp].x, p2[sp].y);
+      Q[sp] = mk(q2[sp].x, q2[sp].y);
+    }
+  } else {
+#pragma unroll
+    for (int sp = 0; sp < 2; ++sp) P[sp] = Q[sp] = mk<T>(0, 0);
+#pragma unroll
+    for (int d = 0; d < 9; ++d)
+#pragma unroll
+      for (int sp = 0; sp < 2; ++sp) {
+        cx<T> v = rv[d][sp], c = a[d][sp];
+        P[sp].re = fma(c.re, v.re, P[sp].re);
+        P[sp].im = fma(c.re, v.im, P[sp].im);
+        Q[sp].re = fma(c.im, v.re, Q[sp].re);
+        Q[sp].im = fma(c.im, v.im, Q[sp].im);
+      }
+  }
+  return mk((P[0].re - Q[0].im) - (P[1].re - Q[1].im), (P[0].im + Q[0].re) - (P[1].im + Q[1].re));
+}
+
 // one (site, right-hand side) item, one thread
 template <typename T, typename S>
 __device__ __forceinline__ void kacz_item(const Geo &g, int colour, int q, int rh, const S *__restrict__ A,
@@ -104,13 +147,15 @@ __device__ __forceinline__ void kacz_item(const Geo &g, int colour, int q, int r
   xs[1] = x[xo + nrhs];
 #pragma unroll
   for (int t = 0; t < 2; ++t) {
-    cx<T> num = mk<T>(0, 0);
+    cx<T> a_[9][2];
 #pragma unroll
     for (int d = 0; d < 9; ++d) {
-      cfma(num, ld<T>(Ah + d * 4 + t * 2 + 0), rv[d][0]);
-      cx<T> m1 = ld<T>(Ah + d * 4 + t * 2 + 1);
-      cfma(num, mk<T>(-m1.re, -m1.im), rv[d][1]);
+      a_[d][0] = ld<T>(Ah + d * 4 + t * 2 + 0);
+      a_[d][1] = ld<T>(Ah + d * 4 + t * 2 + 1);
     }
+    // the row inner product as eight independent chains (row_dot), so
+    // a thread's step is not one long chain of dependent FMAs
+    cx<T> num = row_dot<T, false>(a_, rv);
     T sc = omega / den[2 * h + t];
     if (t) sc = -sc;
     cx<T> sv = sc * num;
@@ -118,10 +163,7 @@ __device__ __forceinline__ void kacz_item(const Geo &g, int colour, int q, int r
 #pragma unroll
     for (int d = 0; d < 9; ++d) {
 #pragma unroll
-      for (int s = 0; s < 2; ++s) {
-        cx<T> a_ = ld<T>(Ah + d * 4 + t * 2 + s);
-        r_sub(rv[d][s], (s == t) ? (T)1 : (T)-1, sv, a_);  // g_s g_t
-      }
+      for (int s = 0; s < 2; ++s) r_sub(rv[d][s], (s == t) ? (T)1 : (T)-1, sv, a_[d][s]);  // g_s g_t
     }
   }
   x[xo] = xs[0];
@@ -189,34 +231,60 @@ __global__ void __launch_bounds__(128) k_kacz_warp(Geo g, int colour, const S *_
   kacz_site_warp<T, S>(g, colour, q, threadIdx.x & 31, A, den, x, r, omega);
 }
 
+// asynchronous global -> shared copies (cp.async): the staging loads of a
+// block are all in flight at once and waited for together
+__device__ __forceinline__ void cp_async(void *smem, const void *gmem, int bytes) {
+  unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  if (bytes == 16) asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem));
+  else if (bytes == 8) asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem));
+  else asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::); }
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
 // Small levels: all colours of `sweeps` sweeps in one launch, a block per
 // chunk of RC right-hand sides.  Right-hand sides do not interact, so a block
 // owning whole right-hand sides needs only block barriers between colours;
-// x and r of its chunk live in shared memory ([n][2][RC] each), the stencil
-// rows come through the cache.  The per-item arithmetic is kacz_item's, so
-// the result equals the other launch forms bit for bit.
-template <typename T, typename S>
+// x and r of its chunk live in shared memory ([n][2][RC] each).  The stencil
+// rows and denominators come through the cache, or (STAGE) are staged in
+// shared memory as well, so no colour step waits on L2.  The per-item
+// arithmetic is kacz_item's, so the result equals the other launch forms
+// bit for bit.
+template <typename T, typename S, bool STAGE>
 __global__ void __launch_bounds__(256) k_kacz_block(Geo g, int sweeps, int RC, const S *__restrict__ A,
                                                     const T *__restrict__ den, cx<T> *__restrict__ x,
                                                     cx<T> *__restrict__ r, int nrhs, T omega) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   int n = g.nsites();
   cx<T> *xs = (cx<T> *)sm_raw, *rs = xs + (long)n * 2 * RC;
+  S *As = (S *)(rs + (long)n * 2 * RC);  // [n][36] with STAGE
+  T *dsm = (T *)(As + (STAGE ? (long)n * 36 : 0));
   int r0 = blockIdx.x * RC, rc = min(RC, nrhs - r0);
   int tid = threadIdx.x, nt = blockDim.x;
+  if constexpr (STAGE) {
+    const int rowc = n * 36 * (int)sizeof(S) / 16;  // whole rows, 16-byte pieces
+    for (int e = tid; e < rowc; e += nt) cp_async((char *)As + 16 * e, (const char *)A + 16 * (long)e, 16);
+    cp_async_commit();
+    for (int e = tid; e < 2 * n; e += nt) dsm[e] = den[e];
+  }
   for (int e = tid; e < n * 2 * RC; e += nt) {
     int j = e % RC, row = e / RC;
     bool in = j < rc;
     xs[e] = in ? x[(long)row * nrhs + r0 + j] : mk<T>(0, 0);
     rs[e] = in ? r[(long)row * nrhs + r0 + j] : mk<T>(0, 0);
   }
+  if constexpr (STAGE) cp_async_wait_all();
   __syncthreads();
+  const S *Au = STAGE ? As : A;
+  const T *du = STAGE ? dsm : den;
   int n16 = n >> 4;
   for (int sw = 0; sw < sweeps; ++sw)
     for (int c = 0; c < 16; ++c) {
       for (int it = tid; it < n16 * RC; it += nt) {
         int q = it / RC, j = it - q * RC;
-        if (j < rc) kacz_item<T, S>(g, c, q, j, A, den, xs, rs, RC, omega);
+        if (j < rc) kacz_item<T, S>(g, c, q, j, Au, du, xs, rs, RC, omega);
       }
       __syncthreads();
     }
@@ -265,18 +333,6 @@ __global__ void __launch_bounds__(128) k_kacz_coop(Geo g, int sweeps, int wpi, c
 // (tile + halo) regions, so the write-back does not race.
 #define KT 8            // tile side
 #define KTH (KT + 2)    // with halo
-// asynchronous global -> shared copies (cp.async): the staging loads of a
-// block are all in flight at once and waited for together
-__device__ __forceinline__ void cp_async(void *smem, const void *gmem, int bytes) {
-  unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-  if (bytes == 16) asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem));
-  else if (bytes == 8) asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem));
-  else asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem));
-}
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::); }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait_group() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
 // two adjacent stored coefficients in one shared-memory load (16 bytes for
 // complex float, 8 for a bf16 pair; 2 x 16 for complex double)
@@ -350,49 +406,6 @@ __device__ __forceinline__ void tile_stage_rows(const Geo &g, int A0, int B0, co
     long h = g.idx(a + b, a - b);
     cp_async(ds + e, den + 2 * h + (e & 1), (int)sizeof(T));
   }
-}
-
-// Row inner product of a Kaczmarz step, num = sum_d a_0 r_0 - a_1 r_1
-// (complex, a_s = A[h][d][t][s], r_s of neighbour d), as eight independent
-// chains: per spin s, P_s = sum_d Re(a_s) (Re r_s, Im r_s) and
-// Q_s = sum_d Im(a_s) (Re r_s, Im r_s), then a_s r_s summed is
-// (P.re - Q.im, P.im + Q.re).  PAIRED (FP32 only) runs each (re, im) pair of
-// chains as one paired FMA (__ffma2_rn), lane for lane the same operation,
-// so both forms give the same bits.
-template <typename T, bool PAIRED>
-__device__ __forceinline__ cx<T> row_dot(const cx<T> (&a)[9][2], const cx<T> (&rv)[9][2]) {
-  cx<T> P[2], Q[2];
-  if constexpr (PAIRED) {
-    static_assert(std::is_same<T, float>::value, "paired FMAs are FP32");
-    float2 p2[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)}, q2[2] = {p2[0], p2[0]};
-#pragma unroll
-    for (int d = 0; d < 9; ++d)
-#pragma unroll
-      for (int sp = 0; sp < 2; ++sp) {
-        float2 v = make_float2(rv[d][sp].re, rv[d][sp].im);
-        p2[sp] = __ffma2_rn(make_float2(a[d][sp].re, a[d][sp].re), v, p2[sp]);
-        q2[sp] = __ffma2_rn(make_float2(a[d][sp].im, a[d][sp].im), v, q2[sp]);
-      }
-#pragma unroll
-    for (int sp = 0; sp < 2; ++sp) {
-      P[sp] = mk(p2[sp].x, p2[sp].y);
-      Q[sp] = mk(q2[sp].x, q2[sp].y);
-    }
-  } else {
-#pragma unroll
-    for (int sp = 0; sp < 2; ++sp) P[sp] = Q[sp] = mk<T>(0, 0);
-#pragma unroll
-    for (int d = 0; d < 9; ++d)
-#pragma unroll
-      for (int sp = 0; sp < 2; ++sp) {
-        cx<T> v = rv[d][sp], c = a[d][sp];
-        P[sp].re = fma(c.re, v.re, P[sp].re);
-        P[sp].im = fma(c.re, v.im, P[sp].im);
-        Q[sp].re = fma(c.im, v.re, Q[sp].re);
-        Q[sp].im = fma(c.im, v.im, Q[sp].im);
-      }
-  }
-  return mk((P[0].re - Q[0].im) - (P[1].re - Q[1].im), (P[0].im + Q[0].re) - (P[1].im + Q[1].re));
 }
 
 // r_sub as two paired FMAs: (re, im) += (-sr, -si) Re a, then += (-si, sr) Im a
@@ -1254,28 +1267,39 @@ int stencil_apply(wl_amg *a, int l, int prec, const void *x, void *y, const void
   return WL_OK;
 }
 
-// block-resident sweeps of a small level: RC right-hand sides per block
-#define WL_BLOCK_SMEM_MAX (200 * 1024)
-template <typename T>
-static size_t block_smem(const Level &L, int RC) {
-  return (size_t)L.n * 2 * RC * sizeof(cx<T>) * 2;
+// block-resident sweeps of a small level: launch parameter RC | STAGE << 8
+// (RC right-hand sides per block; STAGE = 1: stencil rows and denominators
+// in shared memory too)
+#define WL_BLOCK_SMEM_MAX (227 * 1024)
+static size_t block_smem(const Level &L, int param, int prec) {
+  int RC = param & 255;
+  bool stage = (param >> 8) & 1;
+  size_t ct = prec == WL_FP64 ? 16 : 8, t = ct / 2;
+  size_t sz = prec == WL_FP64 ? 16 : (prec == WL_FP32 ? 8 : 4);
+  return (size_t)L.n * 2 * RC * ct * 2 + (stage ? (size_t)L.n * 36 * sz + (size_t)L.n * 2 * t : 0);
 }
-static bool block_fits(const Level &L, int RC, int prec) {
-  size_t b = prec == WL_FP64 ? block_smem<double>(L, RC) : block_smem<float>(L, RC);
-  return RC >= 1 && b <= WL_BLOCK_SMEM_MAX;
+static bool block_fits(const Level &L, int param, int prec) {
+  return (param & 255) >= 1 && (param >> 9) == 0 && block_smem(L, param, prec) <= WL_BLOCK_SMEM_MAX;
 }
 
-template <typename T, typename S>
-static int launch_block(const Level &L, const LevelOps &o, int sweeps, void *x, void *r, int nrhs, double omega,
-                        cudaStream_t s, int RC) {
+template <typename T, typename S, bool STAGE>
+static int launch_block_s(const Level &L, const LevelOps &o, int sweeps, void *x, void *r, int nrhs, double omega,
+                          cudaStream_t s, int RC, size_t smem) {
   static std::atomic<unsigned long long> limit_set{0};
-  WL_TRY(set_smem_limit((const void *)k_kacz_block<T, S>, WL_BLOCK_SMEM_MAX, limit_set));
+  WL_TRY(set_smem_limit((const void *)k_kacz_block<T, S, STAGE>, WL_BLOCK_SMEM_MAX, limit_set));
   long items = (long)(L.n >> 4) * RC;
   int nt = (int)std::min<long>(256, std::max<long>(32, (items + 31) / 32 * 32));
-  k_kacz_block<T, S><<<(nrhs + RC - 1) / RC, nt, block_smem<T>(L, RC), s>>>(L.geo, sweeps, RC, o.A.as<S>(),
-                                                                          o.den.as<T>(), (cx<T> *)x, (cx<T> *)r,
-                                                                          nrhs, (T)omega);
+  k_kacz_block<T, S, STAGE><<<(nrhs + RC - 1) / RC, nt, smem, s>>>(L.geo, sweeps, RC, o.A.as<S>(), o.den.as<T>(),
+                                                                  (cx<T> *)x, (cx<T> *)r, nrhs, (T)omega);
   return WL_OK;
+}
+template <typename T, typename S>
+static int launch_block(const Level &L, const LevelOps &o, int sweeps, void *x, void *r, int nrhs, double omega,
+                        cudaStream_t s, int param, int prec) {
+  size_t smem = block_smem(L, param, prec);
+  if ((param >> 8) & 1)
+    return launch_block_s<T, S, true>(L, o, sweeps, x, r, nrhs, omega, s, param & 255, smem);
+  return launch_block_s<T, S, false>(L, o, sweeps, x, r, nrhs, omega, s, param & 255, smem);
 }
 
 // tile-coloured launch for tile colour tc (one quarter of a sweep)
@@ -1460,9 +1484,10 @@ static int run_sweeps(wl_amg *a, int l, int prec, void *x, void *r, int nrhs, in
     const LevelOps &o = ops_of(L, prec);
     wl_count_launches(1);
     int rc;
-    if (prec == WL_FP64) rc = launch_block<double, zd>(L, o, sweeps, x, r, nrhs, a->prm.omega, s, t.param);
-    else if (prec == WL_FP32) rc = launch_block<float, zf>(L, o, sweeps, x, r, nrhs, a->prm.omega, s, t.param);
-    else rc = launch_block<float, zb>(L, o, sweeps, x, r, nrhs, a->prm.omega, s, t.param);
+    if (prec == WL_FP64) rc = launch_block<double, zd>(L, o, sweeps, x, r, nrhs, a->prm.omega, s, t.param, prec);
+    else if (prec == WL_FP32)
+      rc = launch_block<float, zf>(L, o, sweeps, x, r, nrhs, a->prm.omega, s, t.param, prec);
+    else rc = launch_block<float, zb>(L, o, sweeps, x, r, nrhs, a->prm.omega, s, t.param, prec);
     WL_TRY(rc);
   } else {
     for (int sw = 0; sw < sweeps; ++sw)
@@ -1543,7 +1568,9 @@ int autotune_sweeps(wl_amg *a, int nrhs, int prec, cudaStream_t s) {
       cand.push_back(KTune{nrhs, prec, 0, 0, 0.f});
       if (nrhs > 1)  // block-resident sweeps (thread per item, as forms 0 and 1 at nrhs > 1)
         for (int RC : {1, 2, 4, 8})
-          if (RC <= nrhs && block_fits(L, RC, prec)) cand.push_back(KTune{nrhs, prec, 3, RC, 0.f});
+          for (int stage : {0, 1})  // stencil rows through the cache, or staged in shared memory
+            if (RC <= nrhs && block_fits(L, RC | stage << 8, prec))
+              cand.push_back(KTune{nrhs, prec, 3, RC | stage << 8, 0.f});
       int maxb = coop_max_blocks(prec);
       long need = colour_blocks(L, nrhs);
       if (need <= 4L * maxb)

@@ -250,6 +250,9 @@ def test_every_launch_form_agrees_bitwise(shared, order, nrhs):
             forms = [(0, 0), (1, 1), (1, 7), (1, 64)]
             # block-resident sweeps where x and r of the chunk fit 200 KB of shared memory
             forms += [(3, rc) for rc in (1, 2, 4) if rc <= nrhs and n * 2 * 8 * rc <= 200 * 1024]
+            # and with the stencil rows and denominators staged in shared memory as well
+            forms += [(3, rc | 1 << 8) for rc in (1, 2, 4)
+                      if rc <= nrhs and n * 2 * 8 * rc * 2 + n * 36 * 8 + n * 2 * 4 <= 227 * 1024]
         else:
             forms = [(2, 8), (2, 16), (2, 16 | 2 << 8), (2, 32), (2, 32 | 2 << 8), (2, 8 | 8 << 8),
                      (2, 16 | 8 << 8), (2, 32 | 8 << 8),
