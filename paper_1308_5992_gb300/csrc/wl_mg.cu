@@ -482,11 +482,15 @@ __device__ __forceinline__ void tile_relax(const S *__restrict__ A, cx<T> *__res
 #pragma unroll
   for (int st = 0; st < 16; ++st) {
     const int c = tile_step_colour(st), u = st & 3;
-    // the slot of step st + 2 was last read in step st - 1, which ended with a barrier
+    cp_async_wait_group<1>();  // everything but the newest group: r, rows of step st
+    // One barrier per step: after it every thread has finished step st - 1,
+    // so (a) the cells of r written back at the end of step st - 1 are
+    // visible, and (b) the ring slot of step st + 2, last read in step st - 1,
+    // may be refilled.  Within a step the four quadrants' windows are
+    // disjoint, so no thread reads a cell another one writes.
+    __syncthreads();
     if (st + 2 < 16) issue_rows(st + 2);
     cp_async_commit();
-    cp_async_wait_group<2>();  // everything but the two newest groups: r, rows of step st
-    __syncthreads();
     int i = (c >> 2) + 4 * (k >> 1), j = (c & 3) + 4 * (k & 1);
     if (act[0]) {
       int ks = i * KT + j;
@@ -565,8 +569,8 @@ __device__ __forceinline__ void tile_relax(const S *__restrict__ A, cx<T> *__res
           }
       }
     }
-    __syncthreads();
   }
+  __syncthreads();
 }
 
 // The colour steps of tile_relax with each (site, right-hand side) item split
@@ -618,10 +622,10 @@ __device__ __forceinline__ void tile_relax_split(const S *__restrict__ A, zf *__
   for (int st = 0; st < 16; ++st) {
     {
       const int c = tile_step_colour(st), u = st & 3;
+      cp_async_wait_group<1>();
+      __syncthreads();  // one barrier per step, as in tile_relax
       if (st + 2 < 16) issue_rows(st + 2);
       cp_async_commit();
-      cp_async_wait_group<2>();
-      __syncthreads();
       int i = (c >> 2) + 4 * (k >> 1), j = (c & 3) + 4 * (k & 1);
       int ks = i * KT + j;
       const S *Ah = Ar + ((st % 3) * 4 + k) * 36;
@@ -673,9 +677,9 @@ __device__ __forceinline__ void tile_relax_split(const S *__restrict__ A, zf *__
         int ls = (i + d / 3) * KTH + (j + d % 3);
         rs[(ls * 2 + p) * R + q0] = rv[d];
       }
-      __syncthreads();
     }
   }
+  __syncthreads();
 }
 
 // Several right-hand sides: a block of 4 R / RPT threads, thread (k, q) owns
