@@ -37,8 +37,7 @@ METRIC = "Wilson-AMG solves/s at 1e-10 rel err (mixed+batched vs plain FP64); p9
 # roofline reports, by (kernel, right-hand sides per launch), from one ncu capture each of the
 # C4 workload (ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum on bench.py
 # --kernel-only); None until captured for the current kernel
-TRAFFIC = {("k_mdot", 64): 3228150000, ("k_kacz_tile", 64): 127050496, ("k_kacz_tile", 32): 55873536,
-           ("k_mdot_df", 32): 1751391232}
+TRAFFIC = {("k_mdot", 64): 3228150000, ("k_kacz_tile", 32): 55593728, ("k_mdot_df", 32): 1751585024}
 
 
 def parse():
@@ -385,6 +384,32 @@ def run_gb300(args, rank, world, local_rank):
            "h2d_bytes_per_step": b_host.numel() * 16, "d2h_bytes_per_step": x_host.numel() * 16,
            "h2d_ms_alone": round(min(h2d_ms), 3), "d2h_ms_alone": round(min(d2h_ms), 3)}
 
+    # The same step with the Gram-Schmidt in FP64 instead of double-float (the precision
+    # split that keeps FP64 there), on the same hierarchy, timed the same way
+    gs64 = None
+    if w["gs_arith"]:
+        p_gs = params(prec)
+        p_gs.gs_arith = 0
+        amg_gs = W.amg_import(op, hier, p_gs)
+        pin_sweep_forms(W, amg_gs, args.sweep_forms, lane, prec)
+        for _ in range(args.warmup):
+            step(amg_gs, b, x, nrhs)
+        t_gs, it_gs = [], []
+        for _ in range(max(1, min(args.steps, 5))):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            inf = step(amg_gs, b, x, nrhs)
+            e1.record()
+            torch.cuda.synchronize()
+            t_gs.append(e0.elapsed_time(e1))
+            it_gs += [i["iters"] for i in inf]
+        gs64 = {"value": round(nrhs * len(t_gs) / (sum(t_gs) * 1e-3), 3), "unit": "solves/s",
+                "ms_per_step": round(sum(t_gs) / len(t_gs), 3), "iters_mean": round(sum(it_gs) / len(it_gs), 2),
+                "what": "the same step with FP64 Gram-Schmidt (gs_arith = 0), same hierarchy and lanes"}
+        W.amg_destroy(amg_gs)
+
     # plain FP64 single-RHS solve of the same lattice (the method's baseline)
     b1, x1 = b[:1].contiguous(), torch.zeros_like(b[:1])
     for _ in range(2):
@@ -510,6 +535,7 @@ def run_gb300(args, rank, world, local_rank):
         "true_relres_max": relres, "setup_s": round(setup_s, 3),
         "step_ms_p50": sorted(times)[len(times) // 2], "step_ms_p99": sorted(times)[min(len(times) - 1,
                                                                                          int(0.99 * len(times)))],
+        "gram_schmidt_fp64": gs64,
         "plain_fp64_single_rhs": {"value": round(1e3 / (sorted(p64)[1]), 3), "unit": "solves/s",
                                   "ms": sorted(p64)[1], "iters": inf64[0]["iters"]},
         "e2e": e2e, "gpu_launches": int(launches), "roofline": roof, "roofline_more": roof_more, "clocks": clk,

@@ -244,14 +244,21 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait_group() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
+// set to 1 by a launch whose bounded wait for its own bulk copies ran out
+// (persistent tile form, staged block form)
+__device__ int g_tile_timeout;
+
 // Small levels: all colours of `sweeps` sweeps in one launch, a block per
 // chunk of RC right-hand sides.  Right-hand sides do not interact, so a block
 // owning whole right-hand sides needs only block barriers between colours;
 // x and r of its chunk live in shared memory ([n][2][RC] each).  The stencil
 // rows and denominators come through the cache, or (STAGE) are staged in
-// shared memory as well, so no colour step waits on L2.  The per-item
-// arithmetic is kacz_item's, so the result equals the other launch forms
-// bit for bit.
+// shared memory as well, so no colour step waits on L2: two 1-D bulk copies
+// (the level's whole [n][36] stencil and [n][2] denominators, both contiguous)
+// that complete on one mbarrier, with the wait bounded (one second; on a
+// timeout g_tile_timeout gets 1 and the block stops without writing).  The
+// per-item arithmetic is kacz_item's, so the result equals the other launch
+// forms bit for bit.
 template <typename T, typename S, bool STAGE>
 __global__ void __launch_bounds__(256) k_kacz_block(Geo g, int sweeps, int RC, const S *__restrict__ A,
                                                     const T *__restrict__ den, cx<T> *__restrict__ x,
@@ -261,13 +268,21 @@ __global__ void __launch_bounds__(256) k_kacz_block(Geo g, int sweeps, int RC, c
   cx<T> *xs = (cx<T> *)sm_raw, *rs = xs + (long)n * 2 * RC;
   S *As = (S *)(rs + (long)n * 2 * RC);  // [n][36] with STAGE
   T *dsm = (T *)(As + (STAGE ? (long)n * 36 : 0));
+  uint64_t *mbar = (uint64_t *)(((uintptr_t)(dsm + (STAGE ? 2 * n : 0)) + 7) & ~(uintptr_t)7);
   int r0 = blockIdx.x * RC, rc = min(RC, nrhs - r0);
   int tid = threadIdx.x, nt = blockDim.x;
   if constexpr (STAGE) {
-    const int rowc = n * 36 * (int)sizeof(S) / 16;  // whole rows, 16-byte pieces
-    for (int e = tid; e < rowc; e += nt) cp_async((char *)As + 16 * e, (const char *)A + 16 * (long)e, 16);
-    cp_async_commit();
-    for (int e = tid; e < 2 * n; e += nt) dsm[e] = den[e];
+    if (tid == 0) {
+      mbar_init(smem_u32(mbar), 1);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (tid == 0) {
+      const uint32_t mb = smem_u32(mbar), ab = (uint32_t)n * 36 * sizeof(S), db = (uint32_t)n * 2 * sizeof(T);
+      mbar_arrive_expect_tx(mb, ab + db);
+      bulk_g2s(smem_u32(As), A, ab, mb);
+      bulk_g2s(smem_u32(dsm), den, db, mb);
+    }
   }
   for (int e = tid; e < n * 2 * RC; e += nt) {
     int j = e % RC, row = e / RC;
@@ -275,7 +290,12 @@ __global__ void __launch_bounds__(256) k_kacz_block(Geo g, int sweeps, int RC, c
     xs[e] = in ? x[(long)row * nrhs + r0 + j] : mk<T>(0, 0);
     rs[e] = in ? r[(long)row * nrhs + r0 + j] : mk<T>(0, 0);
   }
-  if constexpr (STAGE) cp_async_wait_all();
+  if constexpr (STAGE) {
+    if (!__syncthreads_and(mbar_wait(smem_u32(mbar), 0, 1000000000ull))) {
+      if (tid == 0) atomicExch(&g_tile_timeout, 1);
+      return;
+    }
+  }
   __syncthreads();
   const S *Au = STAGE ? As : A;
   const T *du = STAGE ? dsm : den;
@@ -778,8 +798,6 @@ __global__ void __launch_bounds__(SPLIT ? 8 * R : 4 * R / RPT, SPLIT ? 768 / (8 
 // so prefetching one while another is written back cannot race.  The wait
 // for a buffer is bounded (one second); on a timeout g_tile_timeout gets 1
 // and the block stops.
-// set to 1 by a persistent tile launch whose wait for its r buffer ran out
-__device__ int g_tile_timeout;
 
 template <typename T, typename S, int R, int RPT, bool PAIRED>
 __global__ void __launch_bounds__(4 * R / RPT) k_kacz_tile_p(Geo g, int tc, const S *__restrict__ A,
@@ -1280,7 +1298,7 @@ static size_t block_smem(const Level &L, int param, int prec) {
   bool stage = (param >> 8) & 1;
   size_t ct = prec == WL_FP64 ? 16 : 8, t = ct / 2;
   size_t sz = prec == WL_FP64 ? 16 : (prec == WL_FP32 ? 8 : 4);
-  return (size_t)L.n * 2 * RC * ct * 2 + (stage ? (size_t)L.n * 36 * sz + (size_t)L.n * 2 * t : 0);
+  return (size_t)L.n * 2 * RC * ct * 2 + (stage ? (size_t)L.n * 36 * sz + (size_t)L.n * 2 * t + 16 : 0);
 }
 static bool block_fits(const Level &L, int param, int prec) {
   return (param & 255) >= 1 && (param >> 9) == 0 && block_smem(L, param, prec) <= WL_BLOCK_SMEM_MAX;
