@@ -1,7 +1,7 @@
 """Full-size parity on the benchmark workload: C4 (512x512, beta = 10, four
 grids with 4x4, 4x4, 2x2 cells, k = 12), 64 right-hand sides in one call, in
 the launch configuration bench.py times (FP32 V(4,4) tile-coloured cycle,
-FGMRES(20) with one double-float Gram-Schmidt pass, FP32 Arnoldi matvec,
+FGMRES(16) with one double-float Gram-Schmidt pass, FP32 Arnoldi matvec,
 FP64 restarts, the batch in two concurrent lanes of 32).
 The hierarchy is the oracle's (shared file), so the solve phase is compared
 on the same operators.  Checked: every right-hand side's full-system residual
@@ -65,7 +65,7 @@ def test_c4_full_size_batch(O, c4):
 def test_c4_full_size_matches_oracle_at_1e13(O, c4):
     """The benchmark's call solved to a 1e-13 residual: sampled right-hand
     sides against the oracle's same-option solve (one Gram-Schmidt pass,
-    tile-coloured V(4,4) cycle, FGMRES(20)) at 1e-10 relative error, as a
+    tile-coloured V(4,4) cycle, FGMRES(16)) at 1e-10 relative error, as a
     norm and element by element."""
     w, h, path = c4
     N, U, m = w["N"], w["U"], w["m"]
@@ -82,7 +82,7 @@ def test_c4_full_size_matches_oracle_at_1e13(O, c4):
     assert rc == W.WL_OK and max(i["true_relres"] for i in info) <= 1e-13
     x = psi.cpu().numpy()
     for r in (0, 21, 42, 63):
-        ref, oi = h.solve(b[r], tol=1e-13, nu1=w["nu"], nu2=w["nu"], order=O.ORDER_TILE,
+        ref, oi = h.solve(b[r], tol=1e-13, m=w["fgmres_m"], nu1=w["nu"], nu2=w["nu"], order=O.ORDER_TILE,
                           gs_passes=w["gs_passes"])
         assert oi["status"] == 0
         assert np.linalg.norm(x[r] - ref) / np.linalg.norm(ref) <= 1e-10, r

@@ -100,9 +100,15 @@ WORKLOADS["C4"].update(overlap=1)
 # updates were bound by the FP64 rate (1.2 TFLOP/s), the double-float ones are bound by HBM;
 # measured 389.8 against 323.5 solves/s (two lanes), 374.2 with one lane
 WORKLOADS["C4"].update(gs_arith=1)
+# and restarts every 16 iterations: with the FP32 cycle a restart cycle's Arnoldi relation holds to
+# FP32 rounding, so restarting sooner from the FP64 true residual pays; measured (two lanes,
+# double-float Gram-Schmidt) FGMRES(10) 485, (12) 477, (14) 481, (16) 482 solves/s with 36.1
+# iterations, (20) 427 with 37.4, (24) 378, (30) 312
+WORKLOADS["C4"].update(fgmres_m=16)
 # the single right-hand-side mixed-precision workload with the same cycle; C3b
 # is its variant with BF16-stored stencils and interpolation weights
-WORKLOADS["C3"].update(nu=4, gs_passes=1, kacz_order=1, arnoldi_matvec=1, setup_mu=(10, 20), gs_arith=1)
+WORKLOADS["C3"].update(nu=4, gs_passes=1, kacz_order=1, arnoldi_matvec=1, setup_mu=(10, 20), gs_arith=1,
+                       fgmres_m=16)
 WORKLOADS["C3b"] = dict(WORKLOADS["C3"], precision="bf16")
 
 
