@@ -110,8 +110,8 @@ typedef struct {
   int overlap;            /* 1: amg_solve splits a batch of at least 32 right-hand sides
                              into two halves solved at the same time on two streams (a
                              second workspace and graph set that share the hierarchy's
-                             operators, made on first use), so that one half's FP64
-                             Gram-Schmidt runs beside the other half's FP32 cycle.  Each
+                             operators, made on first use), so that one half's
+                             Gram-Schmidt runs beside the other half's cycle.  Each
                              right-hand side computes what it computes alone (results
                              agree with overlap = 0 up to the rounding of batch-width-
                              dependent reductions). */
