@@ -1,10 +1,12 @@
-// wl_krylov.cu -- FP64 flexible GMRES(m) (Saad 1993) around the AMG cycle,
+// wl_krylov.cu -- flexible GMRES(m) (Saad 1993) around the AMG cycle,
 // batched over right-hand sides in lock step: right preconditioning
 // z_j = M(v_j) (Sec. 4 uses GMRES(32) with a W(4,4) cycle), classical
-// Gram-Schmidt with optional reorthogonalisation, per right-hand-side
-// Givens rotations, restarts that recompute the true residual in FP64
-// (iterative refinement when the cycle runs in FP32), and the two-step
-// Schur solve of Sec. 3.2 around it (amg_solve).
+// Gram-Schmidt with optional reorthogonalisation in FP64 or in double-float
+// on the FP32 pipes, per right-hand-side Givens rotations in FP64, restarts
+// that recompute the true residual in FP64 (iterative refinement when the
+// cycle runs in FP32), the two-step Schur solve of Sec. 3.2 around it
+// (amg_solve, amg_solve_host), and the batch as one or two concurrent
+// solve lanes.
 #include <math.h>
 #include <cmath>
 #include <string.h>
