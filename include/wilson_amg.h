@@ -202,6 +202,11 @@ int amg_solve_host(wl_amg *amg, const void *b, void *x, int nrhs, double tol, wl
  * is corrupt or belongs to another gauge field / mass. */
 int amg_export(wl_amg *amg, const char *path);
 int amg_import(wl_op *op, const char *path, const amg_params *params, wl_amg **out);
+/* FNV-1a 64 (offset basis 14695981039346656037, prime 1099511628211) of n
+ * host bytes at p: the hierarchy file's checksum and the gauge identity
+ * wilson_create records.  Host only (no GPU needed); 0 for p = NULL with
+ * n > 0. */
+unsigned long long wl_hash_bytes(const void *p, size_t n);
 void amg_destroy(wl_amg *amg);
 
 /* Number of levels and the lattice side of level l (host outputs). */

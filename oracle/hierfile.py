@@ -13,7 +13,7 @@ import struct
 
 import numpy as np
 
-_FNV_OFF = 1469598103934665603
+_FNV_OFF = 14695981039346656037  # FNV-1a 64 offset basis
 _FNV_PRIME = 1099511628211
 
 

@@ -436,7 +436,8 @@ int compute_den64(int N, const zd *A, double *den, cudaStream_t s) {
 }  // namespace wl
 
 // -------------------------------------------------------------- C ABI
-static uint64_t fnv1a(const void *p, size_t n, uint64_t h = 1469598103934665603ULL) {
+// FNV-1a, 64 bit: offset basis 14695981039346656037, prime 1099511628211
+static uint64_t fnv1a(const void *p, size_t n, uint64_t h = 14695981039346656037ULL) {
   const unsigned char *c = (const unsigned char *)p;
   for (size_t i = 0; i < n; ++i) h = (h ^ c[i]) * 1099511628211ULL;
   return h;
@@ -678,3 +679,5 @@ int take_even_internal(wl_op *op, const zd *psi, zd *xe, int nrhs, cudaStream_t 
 }
 uint64_t hash_bytes(const void *p, size_t n) { return fnv1a(p, n); }
 }  // namespace wl
+
+extern "C" unsigned long long wl_hash_bytes(const void *p, size_t n) { return p || !n ? fnv1a(p, n) : 0ULL; }

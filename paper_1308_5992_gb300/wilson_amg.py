@@ -105,6 +105,7 @@ def lib():
             "srv_drain": (i, [P]),
             "srv_destroy": (None, [P]),
             "wl_launch_count": (C.c_longlong, []),
+            "wl_hash_bytes": (C.c_ulonglong, [P, C.c_size_t]),
             "agg_create": (i, [P, i, i, i, P, C.POINTER(P)]),
             "agg_import": (i, [P, i, i, i, P, P, C.POINTER(P)]),
             "agg_export": (i, [P, P, P]),
@@ -466,6 +467,12 @@ def wl_time_kernel(amg, kind, level, nrhs, prec, reps):
 
 def wl_launch_count():
     return lib().wl_launch_count()
+
+
+def wl_hash_bytes(data):
+    """FNV-1a 64 of a bytes object, computed by the library (host only)"""
+    buf = C.create_string_buffer(bytes(data), len(data)) if len(data) else None
+    return int(lib().wl_hash_bytes(buf, len(data)))
 
 
 # ------------------------------------------------------------------ serving
